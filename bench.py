@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Throughput of the fast spectral collision operator Q^(pq) on GB300.
+
+One step = one call of the C-ABI collision entry point over the whole
+1-D-slab workload (24 spatial points x 4 species pairs = 96 Q^(pq)
+evaluations at N = 32, M = 12, N_rho = 8, VSS omega = 0.75, alpha = 1.4),
+inputs resident in HBM, L2 flushed (256 MiB write) before every timed step.
+
+Prints ONE JSON line (rank 0).  Fields beyond the base contract:
+  forms        evals/s and relative max-norm error vs the FP64 CPU oracle for
+               every precision form measured (tensor-core FP32 vs FP64),
+  roofline     the dominant kernel: algorithmic work per launch / its average
+               CUDA-event duration inside the timed region,
+  cpu_baseline the FP64 oracle timed on this host's cores on a bounded sample,
+  e2e          the same metric through the host-buffer C-ABI call,
+  clocks       nvidia-smi samples taken during the timed region.
+
+--impl reference times the FP64 CPU oracle (the only reference that exists:
+the paper publishes no code) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Q^(pq) evals/s at N=32,M=12,Nrho=8: TC-FP32 vs FP64 on GB300, err vs FP64"
+UNIT = "Q^(pq) evals/s"
+WORKLOAD = "c2_slab_n32"
+WORKLOAD_DESC = ("1-D DG slab: 8 elements x 3 Gauss points = 24 spatial points, 2 species (m = 1, 4), "
+                 "VSS omega = 0.75, alpha = 1.4, N = 32 on [-10, 10]^3, M = 12 (icosahedron), N_rho = 8; "
+                 "f = Hermite-perturbed Maxwellians (seed 2)")
+# P100 FP64, Table 1 (N = 32, N_rho = 8, M = 12, mass ratio 1): 0.00287 s per evaluation
+PAPER_EVALS_PER_S = 1.0 / 0.00287
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------ work models
+def fft_flops(N):
+    return 5.0 * N * math.log2(N)
+
+
+def kernel_work(name, plan_info, P, S, RS):
+    """Algorithmic FLOPs of one launch of a kernel class (the FFT count
+    5 N log2 N per length-N complex transform plus the complex multiplies the
+    method performs), used for the roofline's achieved rate."""
+    N = int(plan_info["N"])
+    E = min(int(plan_info["chunk"]), P)
+    pen = N * N
+    f = fft_flops(N)
+    if name == "fp64_inv_first" or name == "fp64_inv":
+        return E * RS * pen * 2 * (f + 6 * N)
+    if name == "fp64_prod":
+        return E * RS * pen * (3 * f + 3 * 6 * N)
+    if name == "fp64_fwd":
+        return E * RS * pen * f  # dominant instances act on the (r, s) grids
+    if name == "fp64_mac":
+        return E * RS * pen * (f + 10 * N)
+    return None
+
+
+# --------------------------------------------------------------- our arm
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_1903_04670_gb300 import binding as B
+    from paper_1903_04670_gb300 import workloads as W
+
+    torch.cuda.set_device(0 if world == 1 else int(os.environ.get("LOCAL_RANK", rank)))
+    dev = torch.cuda.current_device()
+    pb = W.make_problem(WORKLOAD)
+    P, S = pb["f"].shape[0], pb["f"].shape[1]
+    RS = pb["M"] * pb["Nrho"]
+    evals = P * S * S
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def make(prec):
+        return B.Plan(pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"], prec, P, dev)
+
+    precisions = [args.precision] if args.precision != "auto" else ["fp32_tc", "fp64"]
+    forms = {}
+    main = None
+    for prec in precisions:
+        try:
+            plan = make(prec)
+            f = torch.from_numpy(pb["f"]).to("cuda", plan.dtype)
+            Q = plan.collide(f)
+            torch.cuda.synchronize()
+        except B.DgfsError as e:
+            if e.status == 5:
+                forms[prec] = {"unavailable": str(e)}
+                continue
+            raise
+        steps = args.steps if main is None else max(2, min(args.steps, 3))
+        for _ in range(args.warmup):
+            plan.collide(f, Q)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        n0 = plan.launch_count()
+        clocks = ClockSampler(dev) if main is None else None
+        if clocks:
+            clocks.start()
+        plan.profile(True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            plan.collide(f, Q)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        prof = plan.profile_read()
+        plan.profile(False)
+        launches = plan.launch_count() - n0
+        clk = clocks.stop() if clocks else None
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        value = world * evals * steps / (ms / 1e3)
+        rec = {"value": value, "ms_per_step": ms / steps, "steps": steps, "launches": launches,
+               "profile": prof, "plan": plan, "f": f, "Q": Q, "clocks": clk}
+        forms[prec] = rec
+        if main is None:
+            main = prec
+
+    if main is None:
+        raise RuntimeError("no precision form could run")
+    rec = forms[main]
+    plan = rec["plan"]
+    info = plan.info()
+    out = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": rec["steps"],
+           "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": rec["value"] / PAPER_EVALS_PER_S,
+           "vs_baseline_ref": "P100 FP64, paper Table 1 (N=32, N_rho=8, M=12): 0.00287 s per evaluation",
+           "dtype": "f64" if main == "fp64" else "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "description": WORKLOAD_DESC, "points": P, "species": S,
+                      "evals_per_step": evals, "precision": main, "rs_per_eval": RS,
+                      "l2": "flushed before every timed step (256 MiB write, outside the events)",
+                      "parallelism": "replicas: every rank evaluates its own 96 (point, pair) operators"}}
+
+    # roofline of the dominant kernel (by summed event time)
+    prof = rec["profile"]
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (cnt, tot_ms) = dom
+    peaks, src = _peaks()
+    work = kernel_work(name, info, P, S, RS)
+    avg_s = tot_ms / cnt / 1e3
+    if name.startswith("fp64"):
+        peak = 1250.0  # GFLOP/s: nominal GB300 FP64 (no measured FP64 peak on this machine)
+        roof = {"bound": "alu", "achieved": work / avg_s / 1e9 if work else None, "peak": peak,
+                "unit": "GFLOP/s", "peak_source": "nominal FP64 of the GB300 (1.25 TFLOP/s)"}
+    else:
+        roof = tc_roofline(name, info, P, S, RS, avg_s, peaks, src)
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("achieved") else None
+    roof["kernel"] = name
+    roof["launches"] = cnt
+    roof["avg_launch_ms"] = tot_ms / cnt
+    roof["share_of_step"] = tot_ms / sum(v[1] for v in prof.values())
+    roof["traffic"] = None
+    out["roofline"] = roof
+    out["kernels"] = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in prof.items()}
+    out["gpu_launches"] = rec["launches"]
+    out["clocks"] = rec["clocks"]
+
+    # end to end through the host-buffer C-ABI call (pinned host memory)
+    if not args.no_e2e:
+        es = 8 if main == "fp64" else 4
+        fh = torch.from_numpy(pb["f"]).to(plan.dtype).pin_memory()
+        Qh = torch.empty(tuple(rec["Q"].shape), dtype=plan.dtype).pin_memory()
+        plan.collide_host(fh, Qh)
+        tot = 0.0
+        for _ in range(rec["steps"]):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan.collide_host(fh, Qh)
+            tot += time.perf_counter() - t0
+        out["e2e"] = {"value": world * evals * rec["steps"] / tot, "unit": UNIT,
+                      "h2d_bytes_per_step": int(fh.numel() * es), "d2h_bytes_per_step": int(Qh.numel() * es)}
+
+    # per-form throughput and error vs the oracle on a sampled subset of points
+    sample_pts = [0, 23] if not args.quick else [0]
+    Qo = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        cores = len(os.sched_getaffinity(0))
+        O.set_threads(cores)
+        prob = O.Problem(pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"])
+        t0 = time.perf_counter()
+        Qo = prob.collide_all(pb["f"], points=sample_pts)
+        dt = time.perf_counter() - t0
+        n_ev = len(sample_pts) * S * S
+        out["cpu_baseline"] = {"value": n_ev / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": "%d points x %d pairs of the same workload (points %s), FP64, "
+                                         "tables excluded" % (len(sample_pts), S * S, sample_pts)}
+    out["forms"] = {}
+    for prec, r in forms.items():
+        if "value" not in r:
+            out["forms"][prec] = r
+            continue
+        d = {"value": r["value"], "ms_per_step": r["ms_per_step"]}
+        if Qo is not None:
+            Qg = r["Q"][sample_pts].double().cpu().numpy()
+            d["rel_err_vs_oracle"] = float(np.abs(Qg - Qo).max() / np.abs(Qo).max())
+            d["err_sample_points"] = sample_pts
+        out["forms"][prec] = d
+    return out
+
+
+def tc_roofline(name, info, P, S, RS, avg_s, peaks, src):
+    N = int(info["N"])
+    flops = float(info.get("tc_flops_" + name, 0.0)) if isinstance(info, dict) else 0.0
+    bf16 = peaks["bf16_tflops"]
+    tf32 = bf16 * (1.1 / 2.25)
+    return {"bound": "tensor", "achieved": flops / avg_s / 1e12 if flops else None, "peak": tf32,
+            "unit": "TFLOP/s", "peak_source": "%s bf16 x nominal tf32/bf16 ratio" % src}
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import numpy as np
+
+    import oracle as O
+    from paper_1903_04670_gb300 import workloads as W
+
+    pb = W.make_problem(WORKLOAD)
+    S = pb["f"].shape[1]
+    cores = len(os.sched_getaffinity(0))
+    O.set_threads(cores)
+    prob = O.Problem(pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"])
+    npts = max(1, cores // (S * S))
+    pts = list(range(npts))
+    for _ in range(args.warmup):
+        prob.collide_all(pb["f"], points=pts[:1])
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        prob.collide_all(pb["f"], points=pts)
+    dt = time.perf_counter() - t0
+    evals = args.steps * npts * S * S
+    v = evals / dt
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": v / PAPER_EVALS_PER_S,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "description": WORKLOAD_DESC, "points": npts,
+                       "evals_per_step": npts * S * S},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d points x %d pairs per step of the same workload, FP64, OpenMP "
+                                       "over (point, pair)" % (npts, S * S)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "fp32_tc", "tf32", "bf16x3"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

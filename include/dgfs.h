@@ -1,0 +1,164 @@
+/*
+ * dgfs.h -- C ABI of the GB300 (sm_103a) fast spectral collision library.
+ *
+ * Computes the multi-species fast Fourier spectral collision operator
+ * Q^(pq)(f_p, f_q) of Jaiswal, Hu, Brillon & Alexeenko (PASC'19, arXiv
+ * 1903.04670) for every spatial point and every species pair: "given f_p, f_q
+ * on N^3 uniform points, produce Q^(pq) at the same grid" (Sec. 2.1).
+ *
+ * Conventions shared by every entry point
+ *  - Velocity grid: N points per dimension on [-L, L]^3, cell centred
+ *    (c_j = -L + (j + 1/2) h, h = 2L/N), flattened as (ix*N + iy)*N + iz with
+ *    x slowest.  n = N^3.
+ *  - Distribution layout f[P][S][n]; operator layout Q[P][S][S][n] with the
+ *    pair index p-major, q-minor: Q[pt][p][q] = Q^(pq)(f[pt][p], f[pt][q]).
+ *  - Element type: double for a DGFS_FP64 plan, float for every other plan.
+ *  - Pointers named *_dev are device pointers on the plan's device; *_host are
+ *    host pointers (pageable or pinned).  The caller owns every buffer it
+ *    passes; the plan owns its tables and workspace.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued asynchronously unless stated otherwise.
+ *  - Errors are returned as dgfs_status codes and never thrown across the
+ *    ABI.  A failed call leaves caller buffers in an unspecified state.
+ *    dgfs_last_error() gives a human-readable detail of the last failure in
+ *    the calling thread.  Asynchronous device faults surface as DGFS_ECUDA on
+ *    a later call.
+ *  - A plan is immutable after creation and owns one workspace: calls on the
+ *    same plan must not overlap (same stream or externally ordered).
+ */
+#ifndef DGFS_H
+#define DGFS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dgfs_plan_s *dgfs_plan;
+
+typedef enum {
+    DGFS_OK = 0,
+    DGFS_EINVAL = 1,       /* bad argument: size, shape, pointer, range      */
+    DGFS_ENOMEM = 2,       /* device or host allocation failed               */
+    DGFS_ECUDA = 3,        /* CUDA runtime error (launch, copy, async fault) */
+    DGFS_ETIMEOUT = 4,     /* a bounded device wait gave up                  */
+    DGFS_EUNSUPPORTED = 5  /* valid request this build does not implement    */
+} dgfs_status;
+
+typedef enum {
+    DGFS_FP64 = 0,     /* FP64 SIMT FFT path (parity anchor)                  */
+    DGFS_FP32_TC = 1,  /* tcgen05 DFT-GEMM, 3xTF32 compensated, FP32 accum.   */
+    DGFS_TF32 = 2,     /* tcgen05 DFT-GEMM, single TF32 product, FP32 accum.  */
+    DGFS_BF16X3 = 3    /* tcgen05 DFT-GEMM, 3-term split BF16, FP32 accum.    */
+} dgfs_precision;
+
+/* Parameters of one species pair (p, q): VSS kernel of Eq. (3) with viscosity
+ * index omega, scattering parameter alpha and non-dimensional reference
+ * diameter d (Kn of Eq. (4) with n0 = H0 = 1, T_ref = T0).  beta_override:
+ * NaN = beta^(pq) from Eq. (4) and the beta^(pq) definition (Sec. 2);
+ * otherwise the constant used as beta (e.g. the constant Krook-Wu kernel of
+ * Sec. 3.2 with omega = alpha = 1). */
+typedef struct {
+    double omega;
+    double alpha;
+    double d;
+    double beta_override;
+} dgfs_pair;
+
+/* Create a plan and its tables (Algorithm 1, Sec. 2.2).
+ *   out        : receives the plan handle (set to NULL on failure).
+ *   N          : grid points per dimension; 2^a 3^b with 4 <= N <= 48.
+ *   L          : half-width of the velocity domain [-L, L]^3 (> 0).
+ *   M          : spherical-design size on the full sphere: 6 (octahedron) or
+ *                12 (icosahedron), weights 4 pi / M.
+ *   N_rho      : Gauss-Legendre points on [0, R_pq] (1 <= N_rho <= 64).
+ *   S          : number of species (1 <= S <= 4).
+ *   masses     : host array [S] of non-dimensional masses (> 0).
+ *   pairs      : host array [S*S], p-major.
+ *   prec       : arithmetic of the collision path (see dgfs_precision).
+ *   max_points : largest P any later call may pass (>= 1); sizes workspace.
+ *   device     : CUDA device ordinal.
+ * Tables are generated on the device in FP64 (per pair: R_pq, quadratures,
+ * phase vectors, b^(pq) with N_rho*M*n entries and c^(pq) with n entries).
+ * Synchronous.  Errors: EINVAL, ENOMEM, ECUDA, EUNSUPPORTED. */
+dgfs_status dgfs_plan_create(dgfs_plan *out, int N, double L, int M, int N_rho, int S,
+                             const double *masses, const dgfs_pair *pairs,
+                             dgfs_precision prec, int max_points, int device);
+
+/* Release a plan and everything it owns.  NULL is accepted.  Synchronous. */
+dgfs_status dgfs_plan_destroy(dgfs_plan plan);
+
+/* Collision operator, Algorithm 2 (Sec. 2.2) for all P*S*S (point, pair)
+ * evaluations:
+ *   Q^(pq) = beta^(pq) Re( ifft( sum_{r,s} w_r w_s b_rs . fft( ifft(t1) ifft(t2) ) )
+ *                          - f_p . ifft( c . fft(f_q) ) )
+ *   t1 = exp(+i m_q/(m_p+m_q) a_rs) fft(f_p), t2 = exp(-i m_p/(m_p+m_q) a_rs) fft(f_q).
+ *   f_dev : device [P][S][n] input.   Q_dev : device [P][S][S][n] output.
+ *   1 <= P <= max_points.  No allocation.  Errors: EINVAL, ECUDA. */
+dgfs_status dgfs_collide(dgfs_plan plan, int P, const void *f_dev, void *Q_dev, void *stream);
+
+/* Same operator with host buffers: copies f to the device, evaluates, copies
+ * Q back.  Synchronous with respect to the host (returns when Q_host is
+ * written).  Uses the plan's staging buffers; no allocation. */
+dgfs_status dgfs_collide_host(dgfs_plan plan, int P, const void *f_host, void *Q_host, void *stream);
+
+/* Adjoint of the bilinear map (f_p, f_q) -> Q^(pq) (bilinearity of Eq. (7)):
+ * for an upstream gradient dQ = dL/dQ [P][S][S][n] returns
+ *   df[P][S][n]   = sum over pairs of the f_p- and f_q-gradients,
+ *   domega[S*S]   = dL/d omega_pq (host or device pointer, see domega_on_host),
+ * recomputing the per-(rho, sigma) translates instead of storing them.
+ * df_dev is overwritten.  domega may be NULL.  Errors: EINVAL, ECUDA,
+ * EUNSUPPORTED (FP64 plans only in this build). */
+dgfs_status dgfs_collide_backward(dgfs_plan plan, int P, const void *f_dev, const void *dQ_dev,
+                                  void *df_dev, double *domega, int domega_on_host, void *stream);
+
+/* FP64 moments of Q on the cell-centred grid (conservation, Sec. 2 Eq. (2)):
+ *   out[pt][p][q][0..4] = h^3 sum_j Q_j * {1, m_p c_x, m_p c_y, m_p c_z, m_p |c|^2}
+ *   Q_dev : device [P][S][S][n] (the plan's element type).
+ *   out_dev : device double [P][S][S][5].  Errors: EINVAL, ECUDA. */
+dgfs_status dgfs_moments(dgfs_plan plan, int P, const void *Q_dev, double *out_dev, void *stream);
+
+/* Plan introspection.  info (host, 16 doubles):
+ *  [0] N [1] L [2] M [3] N_rho [4] S [5] precision [6] max_points
+ *  [7] workspace bytes [8] table bytes [9] chunk (evaluations per pass)
+ *  [10..15] reserved. */
+dgfs_status dgfs_plan_info(dgfs_plan plan, double *info);
+
+/* Copy pair (p, q)'s tables to host FP64 buffers for verification:
+ *   scalars[8] = {R, beta, gamma, eta, dlogbeta/domega, m_q/mu, m_p/mu, overridden}
+ *   rho[N_rho], w_rho[N_rho], sigma[3*M], w_sigma[M],
+ *   b[N_rho][M][n] complex (interleaved re, im), c[n] complex.
+ * Any output pointer may be NULL.  Synchronous. */
+dgfs_status dgfs_plan_pair_tables(dgfs_plan plan, int p, int q, double *scalars, double *rho,
+                                  double *w_rho, double *sigma, double *w_sigma, double *b, double *c);
+
+/* Number of the library's kernels launched since the plan was created
+ * (host-side counter of launches enqueued by dgfs_* calls on this plan). */
+dgfs_status dgfs_plan_launch_count(dgfs_plan plan, long long *count);
+
+/* Profiling hooks (instrumentation, no counterpart in the paper).  With
+ * enable != 0 every later kernel launch on the plan is bracketed by a pair of
+ * CUDA events recorded on the launch's own stream (16384 pairs, reset on each
+ * enable call); enable == 0 synchronises and frees them.  Asynchronous. */
+dgfs_status dgfs_plan_profile(dgfs_plan plan, int enable);
+
+/* Aggregate the recorded launches per kernel class.  Synchronises the device.
+ *   names     : host char[max_classes][64] (may be NULL), NUL-terminated class names
+ *   counts    : host long long[max_classes] launches per class (may be NULL)
+ *   total_ms  : host double[max_classes] summed event durations (may be NULL)
+ *   n_classes : receives the number of classes written.
+ * Returns EINVAL if slots ran out (the totals then cover the first 16384). */
+dgfs_status dgfs_plan_profile_read(dgfs_plan plan, int max_classes, char *names, long long *counts,
+                                   double *total_ms, int *n_classes);
+
+/* Static strings; never NULL. */
+const char *dgfs_status_string(dgfs_status s);
+const char *dgfs_last_error(void);
+const char *dgfs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGFS_H */

@@ -1,0 +1,273 @@
+"""Thin Python binding of the C ABI in include/dgfs.h (argument marshalling only).
+
+Functions keep the C names (dgfs_plan_create, dgfs_collide, ...).  Tensors are
+passed as raw device/host pointers; every step of the computation runs in the
+CUDA library ``_lib/libdgfs.so``.  There is no CPU fallback: if the library
+cannot be loaded, every call raises.
+"""
+import ctypes
+import math
+import os
+
+import torch
+
+from . import _build
+
+FP64, FP32_TC, TF32, BF16X3 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp32_tc": FP32_TC, "tf32": TF32, "bf16x3": BF16X3}
+STATUS = {0: "DGFS_OK", 1: "DGFS_EINVAL", 2: "DGFS_ENOMEM", 3: "DGFS_ECUDA", 4: "DGFS_ETIMEOUT",
+          5: "DGFS_EUNSUPPORTED"}
+
+
+class DgfsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(msg)
+        self.status = status
+
+
+class dgfs_pair(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_double), ("alpha", ctypes.c_double), ("d", ctypes.c_double),
+                ("beta_override", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load (building first if needed) the CUDA library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        i, d, ll = ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+        sig = {
+            "dgfs_plan_create": (i, [ctypes.POINTER(_P), i, d, i, i, i, _P, _P, i, i, i]),
+            "dgfs_plan_destroy": (i, [_P]),
+            "dgfs_collide": (i, [_P, i, _P, _P, _P]),
+            "dgfs_collide_host": (i, [_P, i, _P, _P, _P]),
+            "dgfs_collide_backward": (i, [_P, i, _P, _P, _P, _P, i, _P]),
+            "dgfs_moments": (i, [_P, i, _P, _P, _P]),
+            "dgfs_plan_info": (i, [_P, _P]),
+            "dgfs_plan_pair_tables": (i, [_P, i, i, _P, _P, _P, _P, _P, _P, _P]),
+            "dgfs_plan_launch_count": (i, [_P, ctypes.POINTER(ll)]),
+            "dgfs_plan_profile": (i, [_P, i]),
+            "dgfs_plan_profile_read": (i, [_P, i, _P, _P, _P, ctypes.POINTER(i)]),
+            "dgfs_status_string": (ctypes.c_char_p, [i]),
+            "dgfs_last_error": (ctypes.c_char_p, []),
+            "dgfs_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names of the dgfs_* functions the loaded library exports (checked by tests
+    against include/dgfs.h without calling any of them)."""
+    L = lib()
+    import re
+    hdr = open(os.path.join(_build.ROOT, "include", "dgfs.h")).read()
+    names = re.findall(r"\b(dgfs_[a-z0-9_]+)\s*\(", hdr)
+    return {n: hasattr(L, n) for n in names}
+
+
+def _check(st, what):
+    if st != 0:
+        msg = lib().dgfs_last_error().decode(errors="replace")
+        raise DgfsError(st, "%s failed: %s: %s" % (what, STATUS.get(st, st), msg))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------------ C-named wrappers
+def dgfs_version():
+    return lib().dgfs_version().decode()
+
+
+def dgfs_status_string(s):
+    return lib().dgfs_status_string(int(s)).decode()
+
+
+def dgfs_last_error():
+    return lib().dgfs_last_error().decode(errors="replace")
+
+
+def dgfs_plan_create(N, L, M, N_rho, masses, pairs, precision=FP64, max_points=1, device=0):
+    S = len(masses)
+    m = (ctypes.c_double * S)(*[float(x) for x in masses])
+    pr = (dgfs_pair * (S * S))()
+    for k, p in enumerate(pairs):
+        pr[k].omega = float(p["omega"])
+        pr[k].alpha = float(p["alpha"])
+        pr[k].d = float(p.get("d", 1.0))
+        pr[k].beta_override = float(p.get("beta_override", math.nan))
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    h = _P()
+    _check(lib().dgfs_plan_create(ctypes.byref(h), int(N), float(L), int(M), int(N_rho), S,
+                                  ctypes.cast(m, _P), ctypes.cast(pr, _P), int(precision),
+                                  int(max_points), int(device)), "dgfs_plan_create")
+    return h
+
+
+def dgfs_plan_destroy(h):
+    _check(lib().dgfs_plan_destroy(h), "dgfs_plan_destroy")
+
+
+def dgfs_collide(h, P, f, Q, stream=None):
+    _check(lib().dgfs_collide(h, int(P), _ptr(f), _ptr(Q), _stream(stream)), "dgfs_collide")
+
+
+def dgfs_collide_host(h, P, f_host, Q_host, stream=None):
+    _check(lib().dgfs_collide_host(h, int(P), _ptr(f_host), _ptr(Q_host), _stream(stream)),
+           "dgfs_collide_host")
+
+
+def dgfs_collide_backward(h, P, f, dQ, df, domega=None, domega_on_host=False, stream=None):
+    _check(lib().dgfs_collide_backward(h, int(P), _ptr(f), _ptr(dQ), _ptr(df),
+                                       _ptr(domega) if domega is not None else None,
+                                       1 if domega_on_host else 0, _stream(stream)), "dgfs_collide_backward")
+
+
+def dgfs_moments(h, P, Q, out, stream=None):
+    _check(lib().dgfs_moments(h, int(P), _ptr(Q), _ptr(out), _stream(stream)), "dgfs_moments")
+
+
+def dgfs_plan_info(h):
+    out = (ctypes.c_double * 16)()
+    _check(lib().dgfs_plan_info(h, ctypes.cast(out, _P)), "dgfs_plan_info")
+    keys = ("N", "L", "M", "N_rho", "S", "precision", "max_points", "workspace_bytes", "table_bytes", "chunk")
+    return {k: out[i] for i, k in enumerate(keys)}
+
+
+def dgfs_plan_pair_tables(h, p, q, N, M, N_rho, with_b=True):
+    import numpy as np
+    n = N ** 3
+    sc = np.empty(8)
+    rho, wr = np.empty(N_rho), np.empty(N_rho)
+    sig, ws = np.empty((M, 3)), np.empty(M)
+    b = np.empty((N_rho, M, N, N, N), dtype=np.complex128) if with_b else None
+    c = np.empty((N, N, N), dtype=np.complex128)
+    cp = lambda a: a.ctypes.data_as(_P) if a is not None else None
+    _check(lib().dgfs_plan_pair_tables(h, int(p), int(q), cp(sc), cp(rho), cp(wr), cp(sig), cp(ws), cp(b),
+                                       cp(c)), "dgfs_plan_pair_tables")
+    keys = ("R", "beta", "gamma", "eta", "dlogbeta", "cq", "cp", "overridden")
+    return dict(scalars=dict(zip(keys, sc.tolist())), rho=rho, w_rho=wr, sigma=sig, w_sigma=ws, b=b, c=c)
+
+
+def dgfs_plan_launch_count(h):
+    v = ctypes.c_longlong(0)
+    _check(lib().dgfs_plan_launch_count(h, ctypes.byref(v)), "dgfs_plan_launch_count")
+    return int(v.value)
+
+
+def dgfs_plan_profile(h, enable):
+    _check(lib().dgfs_plan_profile(h, 1 if enable else 0), "dgfs_plan_profile")
+
+
+def dgfs_plan_profile_read(h, max_classes=64):
+    names = ctypes.create_string_buffer(64 * max_classes)
+    counts = (ctypes.c_longlong * max_classes)()
+    ms = (ctypes.c_double * max_classes)()
+    nc = ctypes.c_int(0)
+    _check(lib().dgfs_plan_profile_read(h, max_classes, ctypes.cast(names, _P), ctypes.cast(counts, _P),
+                                        ctypes.cast(ms, _P), ctypes.byref(nc)), "dgfs_plan_profile_read")
+    out = {}
+    for c in range(nc.value):
+        nm = names.raw[64 * c:64 * c + 64].split(b"\0", 1)[0].decode()
+        out[nm] = (int(counts[c]), float(ms[c]))
+    return out
+
+
+# --------------------------------------------------------------- convenience
+class Plan:
+    """Owns a dgfs_plan; tensors in, tensors out (all computation in the library)."""
+
+    def __init__(self, N, L, M, N_rho, masses, pairs, precision="fp64", max_points=1, device=0):
+        self.N, self.L, self.M, self.N_rho = int(N), float(L), int(M), int(N_rho)
+        self.S = len(masses)
+        self.masses = list(masses)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.max_points = int(max_points)
+        self.device = torch.device("cuda", device)
+        self.dtype = torch.float64 if self.precision == FP64 else torch.float32
+        self._h = dgfs_plan_create(N, L, M, N_rho, masses, pairs, self.precision, max_points, device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            dgfs_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n(self):
+        return self.N ** 3
+
+    def _check_f(self, f):
+        if not (f.is_cuda and f.dtype == self.dtype and f.is_contiguous()):
+            raise ValueError("f must be a contiguous %s CUDA tensor" % self.dtype)
+        P = f.shape[0]
+        if f.numel() != P * self.S * self.n:
+            raise ValueError("f must have shape [P][S][N][N][N]")
+        return P
+
+    def collide(self, f, Q=None, stream=None):
+        P = self._check_f(f)
+        if Q is None:
+            Q = torch.empty((P, self.S, self.S, self.N, self.N, self.N), dtype=self.dtype, device=f.device)
+        dgfs_collide(self._h, P, f, Q, stream)
+        return Q
+
+    def collide_host(self, f_host, Q_host, stream=None):
+        P = f_host.shape[0]
+        dgfs_collide_host(self._h, P, f_host, Q_host, stream)
+        return Q_host
+
+    def backward(self, f, dQ, stream=None):
+        P = self._check_f(f)
+        df = torch.empty_like(f)
+        dom = torch.zeros(self.S * self.S, dtype=torch.float64, device=f.device)
+        dgfs_collide_backward(self._h, P, f, dQ.contiguous(), df, dom, False, stream)
+        return df, dom
+
+    def moments(self, Q, stream=None):
+        P = Q.shape[0]
+        out = torch.empty((P, self.S, self.S, 5), dtype=torch.float64, device=Q.device)
+        dgfs_moments(self._h, P, Q, out, stream)
+        return out
+
+    def info(self):
+        return dgfs_plan_info(self._h)
+
+    def pair_tables(self, p, q, with_b=True):
+        return dgfs_plan_pair_tables(self._h, p, q, self.N, self.M, self.N_rho, with_b)
+
+    def launch_count(self):
+        return dgfs_plan_launch_count(self._h)
+
+    def profile(self, enable=True):
+        dgfs_plan_profile(self._h, enable)
+
+    def profile_read(self):
+        return dgfs_plan_profile_read(self._h)

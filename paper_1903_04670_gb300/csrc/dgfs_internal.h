@@ -1,0 +1,114 @@
+// Internal declarations of the CUDA collision library (not installed, not
+// shared with anything outside csrc/).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dgfs.h"
+
+namespace dgfs {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// Per-pair tables (Algorithm 1).  Device arrays are owned by the plan.
+struct PairTables {
+    // scalars (host)
+    double R = 0, beta = 0, gamma = 0, eta = 0, dlogbeta = 0, cq = 0, cp = 0;
+    int overridden = 0;
+    std::vector<double> rho, wrho;  // N_rho Gauss-Legendre nodes/weights on [0, R]
+    // FP64 device tables, natural k layout (x slowest)
+    double2 *b = nullptr;      // [RS][n]   b_rs(k), RS = N_rho * M, rs = r*M + s
+    double2 *c = nullptr;      // [n]       c_k
+    double2 *c_om = nullptr;   // [n]       c with rho^{gamma+2} -> -2 ln(rho) rho^{gamma+2}
+    double2 *phase = nullptr;  // [RS][2][3][N]  exp(+i cq theta_r sigma_sd l), exp(-i cp theta_r sigma_sd l)
+    double *w = nullptr;       // [RS]  w_r w_s
+    double *wlog = nullptr;    // [RS]  -2 ln(rho_r) w_r w_s
+    // FP32 tensor-core form (built only for non-FP64 plans)
+    float2 *b32 = nullptr;     // [RS][n]
+    float2 *c32 = nullptr;     // [n]
+    float *tmat = nullptr;     // translate / DFT matrices, see tc32.cu
+};
+
+}  // namespace dgfs
+
+struct dgfs_plan_s {
+    int N = 0, M = 0, Nrho = 0, S = 0, max_points = 0, device = 0;
+    double L = 0;
+    dgfs_precision prec = DGFS_FP64;
+    std::vector<double> masses;
+    std::vector<dgfs_pair> pair_params;
+    double sigma[12 * 3] = {0};
+    double wsig[12] = {0};
+    std::vector<dgfs::PairTables> pairs;  // S*S, p-major
+
+    double2 *twiddle = nullptr;  // [N] exp(-2 pi i j / N)
+    double *quad_dev = nullptr;  // scratch copy of rho/w/sigma for table kernels
+    double *masses_dev = nullptr;  // [S]
+
+    // workspace (owned)
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    int chunk = 1;            // evaluations per pass launch
+    void *stage_f = nullptr;  // host-call staging [max_points][S][n]
+    void *stage_Q = nullptr;  // host-call staging [max_points][S][S][n]
+    size_t table_bytes = 0;
+    long long launches = 0;
+    // tensor-core form state (tc32.cu)
+    void *tc = nullptr;
+    // per-kernel CUDA-event profiler (capi.cu), null unless enabled
+    void *prof = nullptr;
+};
+
+namespace dgfs {
+
+// error detail for dgfs_last_error(); thread local
+void set_error(const std::string &msg);
+dgfs_status cuda_status(cudaError_t e, const char *what);
+
+#define DGFS_CUDA(call)                                                    \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) return ::dgfs::cuda_status(e_, #call);      \
+    } while (0)
+
+#define DGFS_LAUNCHED(plan)                                                \
+    do {                                                                   \
+        (plan)->launches++;                                                \
+        cudaError_t e_ = cudaGetLastError();                               \
+        if (e_ != cudaSuccess) return ::dgfs::cuda_status(e_, "kernel launch"); \
+    } while (0)
+
+size_t elem_size(const dgfs_plan_s *plan);
+
+// Brackets one kernel launch with CUDA events on its stream when the plan's
+// profiler is on (dgfs_plan_profile); no-op otherwise.
+class ProfScope {
+  public:
+    ProfScope(dgfs_plan_s *plan, const char *kernel_class, cudaStream_t st);
+    ~ProfScope();
+
+  private:
+    void *slot_;
+    cudaStream_t st_;
+};
+
+// tables.cu
+dgfs_status build_tables(dgfs_plan_s *plan);
+// fft64.cu
+size_t fp64_workspace_bytes(const dgfs_plan_s *plan, int chunk);
+dgfs_status fp64_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st);
+dgfs_status fp64_backward(dgfs_plan_s *plan, int P, const void *f, const void *dQ, void *df,
+                          double *domega, int domega_on_host, cudaStream_t st);
+// moments (fft64.cu)
+dgfs_status moments(dgfs_plan_s *plan, int P, const void *Q, double *out, cudaStream_t st);
+// tc32.cu
+dgfs_status tc_prepare(dgfs_plan_s *plan);
+void tc_release(dgfs_plan_s *plan);
+dgfs_status tc_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st);
+size_t tc_workspace_bytes(const dgfs_plan_s *plan);
+
+}  // namespace dgfs

@@ -1,0 +1,487 @@
+// FP64 SIMT path of the collision operator (Algorithm 2, Sec. 2.2): the
+// parity anchor of the library.
+//
+// Each kernel is one "pass": a length-N transform along one axis of many N^3
+// grids, one thread per pencil, the pencil held in registers and transformed
+// by a compile-time-unrolled mixed-radix (4, 2, 3) Cooley-Tukey FFT.  The
+// separable phases exp(+-i c a_rs) of Algorithm 2 (steps 4-5) are applied as
+// per-axis multiplies inside the inverse passes; the product of the two
+// translates, the forward transform (step 6) and the weighted accumulation
+// into QG (step 7) are fused into the last passes; the loss term and the real
+// part (step 10) into the finishing passes.
+//
+// Pass order per (point, pair) and (r, s):
+//   P1 x: A = ifft_x(phi+_x F_p), B = ifft_x(phi-_x F_q)
+//   P2 y: A = ifft_y(phi+_y A),   B = ifft_y(phi-_y B)
+//   P3 z: H = fft_z( ifft_z(phi+_z A) * ifft_z(phi-_z B) )
+//   P4 y: H = fft_y(H)
+//   P5 x: QG += w_rs / n^2 * b_rs * fft_x(H)   (loop over all (r, s) in-thread)
+// Finish: Q = beta/n Re( ifft3_u(QG) - f_p * ifft3_u(c * F_q) ) with unnormalised
+// inverse transforms ifft3_u.  Memory layout is natural (x slowest) everywhere;
+// pencils along x and y are read with threads consecutive in z (coalesced).
+#include <algorithm>
+
+#include "dgfs_internal.h"
+
+namespace dgfs {
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b)  // a * conj(b)
+{
+    return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// multiply by SIGN * i
+template <int SIGN>
+__device__ __forceinline__ double2 mul_si(double2 a)
+{
+    return SIGN < 0 ? make_double2(a.y, -a.x) : make_double2(-a.y, a.x);
+}
+
+// radix-P butterfly of decimation in time: y[q m] = sum_a W_P^{SIGN a q} t[a]
+template <int P, int SIGN>
+__device__ __forceinline__ void bfly(const double2 *t, double2 *y, int m)
+{
+    if constexpr (P == 2) {
+        y[0] = cadd(t[0], t[1]);
+        y[m] = csub(t[0], t[1]);
+    } else if constexpr (P == 4) {
+        const double2 u0 = cadd(t[0], t[2]), u1 = csub(t[0], t[2]);
+        const double2 u2 = cadd(t[1], t[3]), u3 = mul_si<SIGN>(csub(t[1], t[3]));
+        y[0] = cadd(u0, u2);
+        y[2 * m] = csub(u0, u2);
+        y[m] = cadd(u1, u3);
+        y[3 * m] = csub(u1, u3);
+    } else {  // P == 3
+        constexpr double h3 = 0.86602540378443864676;  // sqrt(3)/2
+        const double2 s = cadd(t[1], t[2]);
+        const double2 d = csub(t[1], t[2]);
+        const double2 r = make_double2(t[0].x - 0.5 * s.x, t[0].y - 0.5 * s.y);
+        const double2 q = mul_si<SIGN>(cscale(d, h3));
+        y[0] = cadd(t[0], s);
+        y[m] = cadd(r, q);
+        y[2 * m] = csub(r, q);
+    }
+}
+
+// y[k] = sum_j x[j*S] exp(SIGN 2 pi i j k / N), k < N; TOPN is the top-level length
+// whose twiddle table tw[e] = exp(-2 pi i e / TOPN) is used.
+template <int N, int SIGN, int TOPN>
+struct Dft {
+    template <int S>
+    __device__ static __forceinline__ void run(const double2 *x, double2 *y, const double2 *tw)
+    {
+        if constexpr (N == 1) {
+            y[0] = x[0];
+        } else {
+            constexpr int P = (N % 4 == 0) ? 4 : ((N % 2 == 0) ? 2 : 3);
+            constexpr int m = N / P;
+            double2 sub[N];
+#pragma unroll
+            for (int a = 0; a < P; ++a) Dft<m, SIGN, TOPN>::template run<S * P>(x + a * S, sub + a * m, tw);
+#pragma unroll
+            for (int k = 0; k < m; ++k) {
+                double2 t[P];
+#pragma unroll
+                for (int a = 0; a < P; ++a) {
+                    const int e = (a * k * (TOPN / N)) % TOPN;
+                    if (e == 0) {
+                        t[a] = sub[a * m + k];
+                    } else {
+                        const double2 w = tw[e];
+                        t[a] = SIGN < 0 ? cmul(sub[a * m + k], w) : cmulc(sub[a * m + k], w);
+                    }
+                }
+                bfly<P, SIGN>(t, y + k, m);
+            }
+        }
+    }
+};
+
+template <int N, int SIGN>
+__device__ __forceinline__ void fft(double2 *v, const double2 *tw)
+{
+    double2 out[N];
+    Dft<N, SIGN, N>::template run<1>(v, out, tw);
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = out[k];
+}
+
+enum Mode {
+    FWD_REAL = 0,   // F = fft_axis(real f)       grid.y = species, grid.z = point
+    FWD_INPLACE,    // buf = fft_axis(buf)        grid.y, grid.z index [z][y] grids
+    INV_AB_FIRST,   // GA/GB = ifft(phi * F_p/q)   grid.y = rs, grid.z = eval
+    INV_AB,         // GA/GB = ifft(phi * GA/GB) in place
+    PROD,           // GA = fft(ifft(phi+ GA) * ifft(phi- GB))
+    MAC,            // QG = sum_rs w b fft(GA)     grid.z = eval
+    FIN1,           // QG = ifft(QG), G2 = ifft(c F_q)
+    FIN2,           // in place inverse on QG, G2
+    FIN3            // Q = beta/n Re(ifft(QG) - f_p ifft(G2))
+};
+
+struct PassArgs {
+    long n;
+    int S, p, q, pt0, RS;
+    const double *f;      // real f [P][S][n] (double)  or float when f32 != 0
+    int f32;              // element type of f and Q: 0 double, 1 float
+    double2 *F;           // [P][S][n]
+    double2 *buf;         // FWD_INPLACE target base
+    double2 *GA, *GB;     // [E][RS][n]
+    double2 *QG, *G2;     // [E][n]
+    const double2 *phase; // [RS][2][3][N]
+    const double2 *b;     // [RS][n]
+    const double *w;      // [RS]
+    const double2 *c;     // [n]
+    double beta, inv_n, inv_n2;
+    void *Q;              // [P][S][S][n]
+    const double2 *tw;
+};
+
+template <int N, int AXIS>
+__device__ __forceinline__ long pencil_off(int pi, int j)
+{
+    if constexpr (AXIS == 0) return (long)j * N * N + pi;
+    else if constexpr (AXIS == 1) return (long)(pi / N) * N * N + (long)j * N + (pi % N);
+    else return (long)pi * N + j;
+}
+
+template <int N, int AXIS, int MODE>
+__global__ void __launch_bounds__(128) k_pass(PassArgs a)
+{
+    __shared__ double2 tw[N];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw[i];
+    extern __shared__ double2 acc_s[];  // MAC: [N][blockDim]
+    __syncthreads();
+    const int pi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pi >= N * N) return;
+    const long n = a.n;
+    double2 v[N];
+
+    if constexpr (MODE == FWD_REAL) {
+        const int s = blockIdx.y, pt = blockIdx.z;
+        const long base = ((long)pt * a.S + s) * n;
+        if (a.f32) {
+            const float *fr = reinterpret_cast<const float *>(a.f) + base;
+#pragma unroll
+            for (int j = 0; j < N; ++j) v[j] = make_double2((double)fr[pencil_off<N, AXIS>(pi, j)], 0.0);
+        } else {
+#pragma unroll
+            for (int j = 0; j < N; ++j) v[j] = make_double2(a.f[base + pencil_off<N, AXIS>(pi, j)], 0.0);
+        }
+        fft<N, -1>(v, tw);
+        double2 *F = a.F + base;
+#pragma unroll
+        for (int k = 0; k < N; ++k) F[pencil_off<N, AXIS>(pi, k)] = v[k];
+    } else if constexpr (MODE == FWD_INPLACE) {
+        double2 *g = a.buf + ((long)blockIdx.z * gridDim.y + blockIdx.y) * n;
+#pragma unroll
+        for (int j = 0; j < N; ++j) v[j] = g[pencil_off<N, AXIS>(pi, j)];
+        fft<N, -1>(v, tw);
+#pragma unroll
+        for (int k = 0; k < N; ++k) g[pencil_off<N, AXIS>(pi, k)] = v[k];
+    } else if constexpr (MODE == INV_AB_FIRST || MODE == INV_AB) {
+        const int rs = blockIdx.y, e = blockIdx.z;
+        const double2 *php = a.phase + ((long)rs * 6 + 0 * 3 + AXIS) * N;
+        const double2 *phq = a.phase + ((long)rs * 6 + 1 * 3 + AXIS) * N;
+        double2 *ga = a.GA + ((long)e * a.RS + rs) * n;
+        double2 *gb = a.GB + ((long)e * a.RS + rs) * n;
+        const double2 *srcA = ga, *srcB = gb;
+        if constexpr (MODE == INV_AB_FIRST) {
+            const int pt = a.pt0 + e;
+            srcA = a.F + ((long)pt * a.S + a.p) * n;
+            srcB = a.F + ((long)pt * a.S + a.q) * n;
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) v[j] = cmul(srcA[pencil_off<N, AXIS>(pi, j)], php[j]);
+        fft<N, +1>(v, tw);
+#pragma unroll
+        for (int k = 0; k < N; ++k) ga[pencil_off<N, AXIS>(pi, k)] = v[k];
+#pragma unroll
+        for (int j = 0; j < N; ++j) v[j] = cmul(srcB[pencil_off<N, AXIS>(pi, j)], phq[j]);
+        fft<N, +1>(v, tw);
+#pragma unroll
+        for (int k = 0; k < N; ++k) gb[pencil_off<N, AXIS>(pi, k)] = v[k];
+    } else if constexpr (MODE == PROD) {
+        const int rs = blockIdx.y, e = blockIdx.z;
+        const double2 *php = a.phase + ((long)rs * 6 + 0 * 3 + AXIS) * N;
+        const double2 *phq = a.phase + ((long)rs * 6 + 1 * 3 + AXIS) * N;
+        double2 *ga = a.GA + ((long)e * a.RS + rs) * n;
+        const double2 *gb = a.GB + ((long)e * a.RS + rs) * n;
+        double2 u[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) v[j] = cmul(ga[pencil_off<N, AXIS>(pi, j)], php[j]);
+        fft<N, +1>(v, tw);
+#pragma unroll
+        for (int j = 0; j < N; ++j) u[j] = cmul(gb[pencil_off<N, AXIS>(pi, j)], phq[j]);
+        fft<N, +1>(u, tw);
+#pragma unroll
+        for (int j = 0; j < N; ++j) v[j] = cmul(v[j], u[j]);
+        fft<N, -1>(v, tw);
+#pragma unroll
+        for (int k = 0; k < N; ++k) ga[pencil_off<N, AXIS>(pi, k)] = v[k];
+    } else if constexpr (MODE == MAC) {
+        const int e = blockIdx.z;
+        const int T = blockDim.x, t = threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < N; ++k) acc_s[k * T + t] = make_double2(0.0, 0.0);
+        for (int rs = 0; rs < a.RS; ++rs) {
+            const double2 *ga = a.GA + ((long)e * a.RS + rs) * n;
+            const double2 *brs = a.b + (long)rs * n;
+            const double wr = a.w[rs] * a.inv_n2;
+#pragma unroll
+            for (int j = 0; j < N; ++j) v[j] = ga[pencil_off<N, AXIS>(pi, j)];
+            fft<N, -1>(v, tw);
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const double2 bb = brs[pencil_off<N, AXIS>(pi, k)];
+                const double2 t3 = cmul(bb, v[k]);
+                double2 s = acc_s[k * T + t];
+                s.x = fma(wr, t3.x, s.x);
+                s.y = fma(wr, t3.y, s.y);
+                acc_s[k * T + t] = s;
+            }
+        }
+        double2 *qg = a.QG + (long)e * n;
+#pragma unroll
+        for (int k = 0; k < N; ++k) qg[pencil_off<N, AXIS>(pi, k)] = acc_s[k * T + t];
+    } else if constexpr (MODE == FIN1 || MODE == FIN2) {
+        const int e = blockIdx.z;
+        double2 *qg = a.QG + (long)e * n;
+        double2 *g2 = a.G2 + (long)e * n;
+#pragma unroll
+        for (int j = 0; j < N; ++j) v[j] = qg[pencil_off<N, AXIS>(pi, j)];
+        fft<N, +1>(v, tw);
+#pragma unroll
+        for (int k = 0; k < N; ++k) qg[pencil_off<N, AXIS>(pi, k)] = v[k];
+        if constexpr (MODE == FIN1) {
+            const double2 *Fq = a.F + ((long)(a.pt0 + e) * a.S + a.q) * n;
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const long o = pencil_off<N, AXIS>(pi, j);
+                v[j] = cmul(a.c[o], Fq[o]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < N; ++j) v[j] = g2[pencil_off<N, AXIS>(pi, j)];
+        }
+        fft<N, +1>(v, tw);
+#pragma unroll
+        for (int k = 0; k < N; ++k) g2[pencil_off<N, AXIS>(pi, k)] = v[k];
+    } else if constexpr (MODE == FIN3) {
+        const int e = blockIdx.z;
+        const int pt = a.pt0 + e;
+        const double2 *qg = a.QG + (long)e * n;
+        const double2 *g2 = a.G2 + (long)e * n;
+        double2 u[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) v[j] = qg[pencil_off<N, AXIS>(pi, j)];
+        fft<N, +1>(v, tw);
+#pragma unroll
+        for (int j = 0; j < N; ++j) u[j] = g2[pencil_off<N, AXIS>(pi, j)];
+        fft<N, +1>(u, tw);
+        const long fbase = ((long)pt * a.S + a.p) * n;
+        const long qbase = (((long)pt * a.S + a.p) * a.S + a.q) * n;
+        const double sc = a.beta * a.inv_n;
+        if (a.f32) {
+            const float *fr = reinterpret_cast<const float *>(a.f) + fbase;
+            float *Q = reinterpret_cast<float *>(a.Q) + qbase;
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const long o = pencil_off<N, AXIS>(pi, k);
+                Q[o] = (float)(sc * (v[k].x - (double)fr[o] * u[k].x));
+            }
+        } else {
+            const double *fr = a.f + fbase;
+            double *Q = reinterpret_cast<double *>(a.Q) + qbase;
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const long o = pencil_off<N, AXIS>(pi, k);
+                Q[o] = sc * (v[k].x - fr[o] * u[k].x);
+            }
+        }
+    }
+}
+
+constexpr int kThreads = 128;
+constexpr int kMacThreads = 64;
+
+template <int N, int AXIS, int MODE>
+dgfs_status launch(dgfs_plan_s *plan, dim3 grid, const PassArgs &a, cudaStream_t st)
+{
+    const int T = MODE == MAC ? kMacThreads : kThreads;
+    grid.x = (N * N + T - 1) / T;
+    size_t smem = MODE == MAC ? sizeof(double2) * N * T : 0;
+    if (smem > 48 * 1024) {
+        DGFS_CUDA(cudaFuncSetAttribute(k_pass<N, AXIS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    }
+    static const char *names[] = {"fp64_fwd_real", "fp64_fwd", "fp64_inv_first", "fp64_inv", "fp64_prod",
+                                  "fp64_mac", "fp64_fin1", "fp64_fin2", "fp64_fin3"};
+    {
+        ProfScope ps(plan, names[MODE], st);
+        k_pass<N, AXIS, MODE><<<grid, T, smem, st>>>(a);
+    }
+    DGFS_LAUNCHED(plan);
+    return DGFS_OK;
+}
+
+#define DGFS_TRY(x)                              \
+    do {                                         \
+        dgfs_status s_ = (x);                    \
+        if (s_ != DGFS_OK) return s_;            \
+    } while (0)
+
+template <int N>
+dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaStream_t st)
+{
+    const int S = plan->S, RS = plan->Nrho * plan->M;
+    const long n = (long)N * N * N;
+    const int E = plan->chunk;
+    // workspace: F [max_points][S][n] | GA [E][RS][n] | GB [E][RS][n] | QG [E][n] | G2 [E][n]
+    double2 *F = reinterpret_cast<double2 *>(plan->ws);
+    double2 *GA = F + (long)plan->max_points * S * n;
+    double2 *GB = GA + (long)E * RS * n;
+    double2 *QG = GB + (long)E * RS * n;
+    double2 *G2 = QG + (long)E * n;
+
+    PassArgs a{};
+    a.n = n;
+    a.S = S;
+    a.RS = RS;
+    a.f = reinterpret_cast<const double *>(f);
+    a.f32 = plan->prec == DGFS_FP64 ? 0 : 1;
+    a.F = F;
+    a.GA = GA;
+    a.GB = GB;
+    a.QG = QG;
+    a.G2 = G2;
+    a.Q = Qout;
+    a.tw = plan->twiddle;
+    a.inv_n = 1.0 / (double)n;
+    a.inv_n2 = a.inv_n * a.inv_n;
+
+    // forward transforms of every species at every point (step 1)
+    DGFS_TRY((launch<N, 0, FWD_REAL>(plan, dim3(1, S, P), a, st)));
+    a.buf = F;
+    DGFS_TRY((launch<N, 1, FWD_INPLACE>(plan, dim3(1, S, P), a, st)));
+    DGFS_TRY((launch<N, 2, FWD_INPLACE>(plan, dim3(1, S, P), a, st)));
+
+    for (int p = 0; p < S; ++p)
+        for (int q = 0; q < S; ++q) {
+            const PairTables &pt = plan->pairs[p * S + q];
+            a.p = p;
+            a.q = q;
+            a.phase = pt.phase;
+            a.b = pt.b;
+            a.w = pt.w;
+            a.c = pt.c;
+            a.beta = pt.beta;
+            for (int pt0 = 0; pt0 < P; pt0 += E) {
+                const int Ec = std::min(E, P - pt0);
+                a.pt0 = pt0;
+                DGFS_TRY((launch<N, 0, INV_AB_FIRST>(plan, dim3(1, RS, Ec), a, st)));
+                DGFS_TRY((launch<N, 1, INV_AB>(plan, dim3(1, RS, Ec), a, st)));
+                DGFS_TRY((launch<N, 2, PROD>(plan, dim3(1, RS, Ec), a, st)));
+                a.buf = GA;
+                DGFS_TRY((launch<N, 1, FWD_INPLACE>(plan, dim3(1, RS, Ec), a, st)));
+                DGFS_TRY((launch<N, 0, MAC>(plan, dim3(1, 1, Ec), a, st)));
+                DGFS_TRY((launch<N, 0, FIN1>(plan, dim3(1, 1, Ec), a, st)));
+                DGFS_TRY((launch<N, 1, FIN2>(plan, dim3(1, 1, Ec), a, st)));
+                DGFS_TRY((launch<N, 2, FIN3>(plan, dim3(1, 1, Ec), a, st)));
+            }
+        }
+    return DGFS_OK;
+}
+
+// ------------------------------------------------------------------ moments
+template <typename T>
+__global__ void __launch_bounds__(256) k_moments(const T *Q, double *out, int N, double L, const double *mass_of_p,
+                                                 int S)
+{
+    const long n = (long)N * N * N;
+    const int e = blockIdx.x;  // (pt, p, q)
+    const int p = (e / S) % S;
+    const double m = mass_of_p[p];
+    const double h = 2.0 * L / N;
+    const T *q = Q + (long)e * n;
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (long i = threadIdx.x; i < n; i += blockDim.x) {
+        const int ix = (int)(i / ((long)N * N)), iy = (int)((i / N) % N), iz = (int)(i % N);
+        const double cx = -L + (ix + 0.5) * h, cy = -L + (iy + 0.5) * h, cz = -L + (iz + 0.5) * h;
+        const double v = (double)q[i];
+        acc[0] += v;
+        acc[1] += m * cx * v;
+        acc[2] += m * cy * v;
+        acc[3] += m * cz * v;
+        acc[4] += m * (cx * cx + cy * cy + cz * cz) * v;
+    }
+    __shared__ double red[5][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[k][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+        out[(long)e * 5 + threadIdx.x] = s * h * h * h;
+    }
+}
+
+}  // namespace
+
+size_t fp64_workspace_bytes(const dgfs_plan_s *plan, int chunk)
+{
+    const long n = (long)plan->N * plan->N * plan->N;
+    const long RS = (long)plan->Nrho * plan->M;
+    return sizeof(double2) * ((long)plan->max_points * plan->S * n + 2L * chunk * RS * n + 2L * chunk * n);
+}
+
+dgfs_status fp64_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st)
+{
+    switch (plan->N) {
+    case 4: return collide_n<4>(plan, P, f, Q, st);
+    case 6: return collide_n<6>(plan, P, f, Q, st);
+    case 8: return collide_n<8>(plan, P, f, Q, st);
+    case 12: return collide_n<12>(plan, P, f, Q, st);
+    case 16: return collide_n<16>(plan, P, f, Q, st);
+    case 24: return collide_n<24>(plan, P, f, Q, st);
+    case 32: return collide_n<32>(plan, P, f, Q, st);
+    case 48: return collide_n<48>(plan, P, f, Q, st);
+    default: set_error("N not supported by the FP64 path"); return DGFS_EUNSUPPORTED;
+    }
+}
+
+dgfs_status moments(dgfs_plan_s *plan, int P, const void *Q, double *out, cudaStream_t st)
+{
+    const int S = plan->S;
+    const double *masses = plan->masses_dev;
+    ProfScope ps(plan, "moments", st);
+    if (plan->prec == DGFS_FP64)
+        k_moments<double><<<P * S * S, 256, 0, st>>>(reinterpret_cast<const double *>(Q), out, plan->N, plan->L,
+                                                     masses, S);
+    else
+        k_moments<float><<<P * S * S, 256, 0, st>>>(reinterpret_cast<const float *>(Q), out, plan->N, plan->L,
+                                                    masses, S);
+    DGFS_LAUNCHED(plan);
+    return DGFS_OK;
+}
+
+}  // namespace dgfs
+
+namespace dgfs {
+dgfs_status fp64_backward(dgfs_plan_s *, int, const void *, const void *, void *, double *, int, cudaStream_t)
+{
+    set_error("adjoint not built");
+    return DGFS_EUNSUPPORTED;
+}
+}  // namespace dgfs
