@@ -103,6 +103,12 @@ dgfs_status dgfs_collide(dgfs_plan plan, int P, const void *f_dev, void *Q_dev, 
  * written).  Uses the plan's staging buffers; no allocation. */
 dgfs_status dgfs_collide_host(dgfs_plan plan, int P, const void *f_host, void *Q_host, void *stream);
 
+/* Synchronise the plan's device and report deferred device-side conditions:
+ * DGFS_ETIMEOUT if a bounded wait inside a tensor-core kernel expired since
+ * the last check (the flag is cleared), DGFS_ECUDA for an asynchronous fault.
+ * dgfs_collide_host performs this check itself. */
+dgfs_status dgfs_plan_check(dgfs_plan plan);
+
 /* Adjoint of the bilinear map (f_p, f_q) -> Q^(pq) (bilinearity of Eq. (7)):
  * for an upstream gradient dQ = dL/dQ [P][S][S][n] returns
  *   df[P][S][n]   = sum over pairs of the f_p- and f_q-gradients,
@@ -121,8 +127,9 @@ dgfs_status dgfs_moments(dgfs_plan plan, int P, const void *Q_dev, double *out_d
 
 /* Plan introspection.  info (host, 16 doubles):
  *  [0] N [1] L [2] M [3] N_rho [4] S [5] precision [6] max_points
- *  [7] workspace bytes [8] table bytes [9] chunk (evaluations per pass)
- *  [10..15] reserved. */
+ *  [7] workspace bytes [8] table bytes [9] chunk (evaluations per launch)
+ *  [10] (r, s) blocks of the accumulation stage (tensor-core plans)
+ *  [11] split products per contraction (tensor-core plans) [12..15] reserved. */
 dgfs_status dgfs_plan_info(dgfs_plan plan, double *info);
 
 /* Copy pair (p, q)'s tables to host FP64 buffers for verification:

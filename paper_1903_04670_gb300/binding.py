@@ -56,6 +56,7 @@ def lib():
             "dgfs_plan_pair_tables": (i, [_P, i, i, _P, _P, _P, _P, _P, _P, _P]),
             "dgfs_plan_launch_count": (i, [_P, ctypes.POINTER(ll)]),
             "dgfs_plan_profile": (i, [_P, i]),
+            "dgfs_plan_check": (i, [_P]),
             "dgfs_plan_profile_read": (i, [_P, i, _P, _P, _P, ctypes.POINTER(i)]),
             "dgfs_status_string": (ctypes.c_char_p, [i]),
             "dgfs_last_error": (ctypes.c_char_p, []),
@@ -152,7 +153,8 @@ def dgfs_moments(h, P, Q, out, stream=None):
 def dgfs_plan_info(h):
     out = (ctypes.c_double * 16)()
     _check(lib().dgfs_plan_info(h, ctypes.cast(out, _P)), "dgfs_plan_info")
-    keys = ("N", "L", "M", "N_rho", "S", "precision", "max_points", "workspace_bytes", "table_bytes", "chunk")
+    keys = ("N", "L", "M", "N_rho", "S", "precision", "max_points", "workspace_bytes", "table_bytes", "chunk",
+            "rs_blocks", "nterms")
     return {k: out[i] for i, k in enumerate(keys)}
 
 
@@ -175,6 +177,10 @@ def dgfs_plan_launch_count(h):
     v = ctypes.c_longlong(0)
     _check(lib().dgfs_plan_launch_count(h, ctypes.byref(v)), "dgfs_plan_launch_count")
     return int(v.value)
+
+
+def dgfs_plan_check(h):
+    _check(lib().dgfs_plan_check(h), "dgfs_plan_check")
 
 
 def dgfs_plan_profile(h, enable):
@@ -265,6 +271,9 @@ class Plan:
 
     def launch_count(self):
         return dgfs_plan_launch_count(self._h)
+
+    def check(self):
+        dgfs_plan_check(self._h)
 
     def profile(self, enable=True):
         dgfs_plan_profile(self._h, enable)

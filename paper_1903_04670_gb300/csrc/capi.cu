@@ -377,7 +377,16 @@ dgfs_status dgfs_collide_host(dgfs_plan plan, int P, const void *f_host, void *Q
     if (st != DGFS_OK) return st;
     DGFS_CUDA(cudaMemcpyAsync(Q_host, plan->stage_Q, qb, cudaMemcpyDeviceToHost, s));
     DGFS_CUDA(cudaStreamSynchronize(s));
-    return DGFS_OK;
+    return tc_check(plan);
+}
+
+dgfs_status dgfs_plan_check(dgfs_plan plan)
+{
+    if (!plan) return DGFS_EINVAL;
+    dgfs_status st = entry_check(plan);
+    if (st != DGFS_OK) return st;
+    DGFS_CUDA(cudaDeviceSynchronize());
+    return tc_check(plan);
 }
 
 dgfs_status dgfs_collide_backward(dgfs_plan plan, int P, const void *f_dev, const void *dQ_dev, void *df_dev,
@@ -422,6 +431,7 @@ dgfs_status dgfs_plan_info(dgfs_plan plan, double *info)
     info[7] = (double)plan->ws_bytes;
     info[8] = (double)plan->table_bytes;
     info[9] = plan->chunk;
+    tc_info(plan, info);
     return DGFS_OK;
 }
 

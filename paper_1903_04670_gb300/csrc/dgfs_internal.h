@@ -110,5 +110,7 @@ dgfs_status tc_prepare(dgfs_plan_s *plan);
 void tc_release(dgfs_plan_s *plan);
 dgfs_status tc_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st);
 size_t tc_workspace_bytes(const dgfs_plan_s *plan);
+dgfs_status tc_check(dgfs_plan_s *plan);
+void tc_info(const dgfs_plan_s *plan, double *info);
 
 }  // namespace dgfs

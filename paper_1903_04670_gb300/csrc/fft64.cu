@@ -22,96 +22,16 @@
 #include <algorithm>
 
 #include "dgfs_internal.h"
+#include "fftreg.cuh"
 
 namespace dgfs {
 namespace {
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b)
-{
-    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 cmulc(double2 a, double2 b)  // a * conj(b)
-{
-    return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
-}
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
-// multiply by SIGN * i
-template <int SIGN>
-__device__ __forceinline__ double2 mul_si(double2 a)
-{
-    return SIGN < 0 ? make_double2(a.y, -a.x) : make_double2(-a.y, a.x);
-}
-
-// radix-P butterfly of decimation in time: y[q m] = sum_a W_P^{SIGN a q} t[a]
-template <int P, int SIGN>
-__device__ __forceinline__ void bfly(const double2 *t, double2 *y, int m)
-{
-    if constexpr (P == 2) {
-        y[0] = cadd(t[0], t[1]);
-        y[m] = csub(t[0], t[1]);
-    } else if constexpr (P == 4) {
-        const double2 u0 = cadd(t[0], t[2]), u1 = csub(t[0], t[2]);
-        const double2 u2 = cadd(t[1], t[3]), u3 = mul_si<SIGN>(csub(t[1], t[3]));
-        y[0] = cadd(u0, u2);
-        y[2 * m] = csub(u0, u2);
-        y[m] = cadd(u1, u3);
-        y[3 * m] = csub(u1, u3);
-    } else {  // P == 3
-        constexpr double h3 = 0.86602540378443864676;  // sqrt(3)/2
-        const double2 s = cadd(t[1], t[2]);
-        const double2 d = csub(t[1], t[2]);
-        const double2 r = make_double2(t[0].x - 0.5 * s.x, t[0].y - 0.5 * s.y);
-        const double2 q = mul_si<SIGN>(cscale(d, h3));
-        y[0] = cadd(t[0], s);
-        y[m] = cadd(r, q);
-        y[2 * m] = csub(r, q);
-    }
-}
-
-// y[k] = sum_j x[j*S] exp(SIGN 2 pi i j k / N), k < N; TOPN is the top-level length
-// whose twiddle table tw[e] = exp(-2 pi i e / TOPN) is used.
-template <int N, int SIGN, int TOPN>
-struct Dft {
-    template <int S>
-    __device__ static __forceinline__ void run(const double2 *x, double2 *y, const double2 *tw)
-    {
-        if constexpr (N == 1) {
-            y[0] = x[0];
-        } else {
-            constexpr int P = (N % 4 == 0) ? 4 : ((N % 2 == 0) ? 2 : 3);
-            constexpr int m = N / P;
-            double2 sub[N];
-#pragma unroll
-            for (int a = 0; a < P; ++a) Dft<m, SIGN, TOPN>::template run<S * P>(x + a * S, sub + a * m, tw);
-#pragma unroll
-            for (int k = 0; k < m; ++k) {
-                double2 t[P];
-#pragma unroll
-                for (int a = 0; a < P; ++a) {
-                    const int e = (a * k * (TOPN / N)) % TOPN;
-                    if (e == 0) {
-                        t[a] = sub[a * m + k];
-                    } else {
-                        const double2 w = tw[e];
-                        t[a] = SIGN < 0 ? cmul(sub[a * m + k], w) : cmulc(sub[a * m + k], w);
-                    }
-                }
-                bfly<P, SIGN>(t, y + k, m);
-            }
-        }
-    }
-};
-
-template <int N, int SIGN>
-__device__ __forceinline__ void fft(double2 *v, const double2 *tw)
-{
-    double2 out[N];
-    Dft<N, SIGN, N>::template run<1>(v, out, tw);
-#pragma unroll
-    for (int k = 0; k < N; ++k) v[k] = out[k];
-}
+using reg::cadd;
+using reg::cmul;
+using reg::cmulc;
+using reg::csub;
+using reg::fft;
 
 enum Mode {
     FWD_REAL = 0,   // F = fft_axis(real f)       grid.y = species, grid.z = point
@@ -317,7 +237,7 @@ dgfs_status launch(dgfs_plan_s *plan, dim3 grid, const PassArgs &a, cudaStream_t
     const int T = MODE == MAC ? kMacThreads : kThreads;
     grid.x = (N * N + T - 1) / T;
     size_t smem = MODE == MAC ? sizeof(double2) * N * T : 0;
-    if (smem > 48 * 1024) {
+    if (smem > 0) {  // static twiddles + dynamic accumulators may pass the 48 KiB default
         DGFS_CUDA(cudaFuncSetAttribute(k_pass<N, AXIS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
     }

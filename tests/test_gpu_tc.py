@@ -1,0 +1,119 @@
+"""GPU parity of the tensor-core (tcgen05) path against the FP64 oracle.
+
+Bar (relative max-norm against the oracle's ||Q||_inf):
+  DGFS_FP32_TC (3xTF32, FP32 accumulation): <= 1e-5
+  DGFS_TF32    (one TF32 product):          reported, <= 1e-2 sanity bound
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1903_04670_gb300 import binding as B
+from paper_1903_04670_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL_TC = 1e-5
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def _gpu(pb, f, prec, max_points=None):
+    P = f.shape[0]
+    plan = B.Plan(pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"], prec, max_points or P)
+    fd = torch.from_numpy(np.ascontiguousarray(f)).to("cuda", torch.float32)
+    Q = plan.collide(fd)
+    plan.check()
+    return Q.double().cpu().numpy(), plan
+
+
+def _oracle(pb, f, points=None):
+    prob = O.Problem(pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"])
+    return prob.collide_all(f, points=points)
+
+
+def test_c1_homogeneous_n16_fp32_tc_and_tf32():
+    pb = W.make_problem("c1_homog_n16")
+    Qo = _oracle(pb, pb["f"])
+    Qg, _ = _gpu(pb, pb["f"], "fp32_tc")
+    assert _rel(Qg, Qo) < TOL_TC
+    Qt, _ = _gpu(pb, pb["f"], "tf32")
+    e = _rel(Qt, Qo)
+    assert e < 1e-2
+    assert e > _rel(Qg, Qo)  # one TF32 product is less accurate than three
+
+
+@pytest.mark.parametrize("N,M,Nrho,S,P", [(8, 12, 4, 3, 2), (16, 6, 3, 2, 6), (24, 6, 3, 2, 1)])
+def test_small_and_ragged(N, M, Nrho, S, P):
+    """N = 24 leaves a partial plane group (128 = 5 x 24 + 8) and a partial
+    pencil tile (576 = 4 x 128 + 64); P = 6 > chunk exercises chunking."""
+    rng = np.random.default_rng(100 + N)
+    masses = [1.0, 2.5, 0.7][:S]
+    pairs = W.pair_params([0.72, 0.8, 0.9][:S], [1.4, 1.0, 1.2][:S], [1.0, 1.1, 0.9][:S])
+    L = 0.5 * N
+    f = np.stack([np.stack([W.two_maxwellians(rng, N, L, m) for m in masses]) for _ in range(P)])
+    pb = dict(N=N, L=L, M=M, Nrho=Nrho, masses=masses, pairs=pairs)
+    Qo = _oracle(pb, f)
+    Qg, _ = _gpu(pb, f, "fp32_tc")
+    for pt in range(P):
+        for p in range(S):
+            for q in range(S):
+                assert _rel(Qg[pt, p, q], Qo[pt, p, q]) < TOL_TC, (pt, p, q, _rel(Qg[pt, p, q], Qo[pt, p, q]))
+
+
+def test_c2_slab_n32_sampled_points():
+    """The benchmark's workload and launch configuration (24 points, N = 32,
+    M = 12, N_rho = 8, VSS); the oracle checks sampled points."""
+    pb = W.make_problem("c2_slab_n32")
+    Qg, plan = _gpu(pb, pb["f"], "fp32_tc")
+    pts = [0, 13, 23]
+    Qo = _oracle(pb, pb["f"], points=pts)
+    for i, pt in enumerate(pts):
+        for p in range(2):
+            for q in range(2):
+                assert _rel(Qg[pt, p, q], Qo[i, p, q]) < TOL_TC, (pt, p, q, _rel(Qg[pt, p, q], Qo[i, p, q]))
+
+
+def test_n48_single_pair():
+    N, L = 48, 12.0
+    rng = np.random.default_rng(480)
+    f = np.stack([W.two_maxwellians(rng, N, L, m) for m in (1.0, 2.0)])[None]
+    pairs = W.pair_params([0.81, 0.81], [1.0, 1.0], [1.0, 1.2])
+    pb = dict(N=N, L=L, M=6, Nrho=3, masses=[1.0, 2.0], pairs=pairs)
+    Qg, _ = _gpu(pb, f, "fp32_tc")
+    prob = O.Problem(N, L, 6, 3, [1.0, 2.0], pairs)
+    Qo, _ = prob.pair(1, 0).collide(f[0, 1], f[0, 0])
+    assert _rel(Qg[0, 1, 0], Qo) < TOL_TC
+
+
+def test_krook_wu_closed_form_on_tensor_cores():
+    import test_oracle_operator as T
+    pb = W.krook_wu_problem(16, 6, 8)
+    f, df, _ = T.krook_wu(5.5, 16, pb["L"])
+    Qg, _ = _gpu(pb, f[None], "fp32_tc")
+    err = np.abs(Qg[0, 0].sum(0) - df[0]).max()
+    assert 3.73e-3 / 3 < err < 3 * 3.73e-3
+
+
+def test_deterministic_and_no_timeouts():
+    pb = W.make_problem("c1_homog_n16")
+    Q1, plan = _gpu(pb, pb["f"], "fp32_tc")
+    f = torch.from_numpy(pb["f"]).to("cuda", torch.float32)
+    Q2 = plan.collide(f)
+    plan.check()
+    assert np.array_equal(Q1, Q2.double().cpu().numpy())
+
+
+def test_moments_of_fp32_operator():
+    pb = W.make_problem("c1_homog_n16")
+    Qg, plan = _gpu(pb, pb["f"], "fp32_tc")
+    Qd = torch.from_numpy(Qg).to("cuda", torch.float32)
+    mom = plan.moments(Qd).cpu().numpy()
+    Q32 = Qd.double().cpu().numpy()
+    for p in range(2):
+        for q in range(2):
+            ref = O.moments(pb["N"], pb["L"], pb["masses"][p], Q32[0, p, q])
+            scale = O.moments(pb["N"], pb["L"], pb["masses"][p], np.abs(Q32[0, p, q]))
+            assert np.all(np.abs(mom[0, p, q] - ref) <= 1e-12 * np.abs(scale))
