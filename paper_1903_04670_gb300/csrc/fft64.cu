@@ -319,6 +319,55 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
     return DGFS_OK;
 }
 
+// Forward transforms F = fft3(f) of every (point, species) in FP64; f is
+// double for FP64 plans and float otherwise.
+template <int N>
+dgfs_status forward_n(dgfs_plan_s *plan, int P, const void *f, double2 *F, cudaStream_t st)
+{
+    PassArgs a{};
+    a.n = (long)N * N * N;
+    a.S = plan->S;
+    a.f = reinterpret_cast<const double *>(f);
+    a.f32 = plan->prec == DGFS_FP64 ? 0 : 1;
+    a.F = F;
+    a.buf = F;
+    a.tw = plan->twiddle;
+    DGFS_TRY((launch<N, 0, FWD_REAL>(plan, dim3(1, plan->S, P), a, st)));
+    DGFS_TRY((launch<N, 1, FWD_INPLACE>(plan, dim3(1, plan->S, P), a, st)));
+    DGFS_TRY((launch<N, 2, FWD_INPLACE>(plan, dim3(1, plan->S, P), a, st)));
+    return DGFS_OK;
+}
+
+// Step 10 of Algorithm 2 in FP64 for pair (p, q) at points [0, P):
+// Q = beta/n Re( ifft3_u(QG) - f_p ifft3_u(c F_q) ).  QG and G2 are [P][n];
+// QG is overwritten.
+template <int N>
+dgfs_status finish_n(dgfs_plan_s *plan, int p, int q, int P, double2 *QG, double2 *G2, const double2 *F,
+                     const void *f, void *Q, cudaStream_t st)
+{
+    const PairTables &pt = plan->pairs[p * plan->S + q];
+    PassArgs a{};
+    a.n = (long)N * N * N;
+    a.S = plan->S;
+    a.p = p;
+    a.q = q;
+    a.pt0 = 0;
+    a.f = reinterpret_cast<const double *>(f);
+    a.f32 = plan->prec == DGFS_FP64 ? 0 : 1;
+    a.F = const_cast<double2 *>(F);
+    a.QG = QG;
+    a.G2 = G2;
+    a.c = pt.c;
+    a.beta = pt.beta;
+    a.inv_n = 1.0 / (double)a.n;
+    a.Q = Q;
+    a.tw = plan->twiddle;
+    DGFS_TRY((launch<N, 0, FIN1>(plan, dim3(1, 1, P), a, st)));
+    DGFS_TRY((launch<N, 1, FIN2>(plan, dim3(1, 1, P), a, st)));
+    DGFS_TRY((launch<N, 2, FIN3>(plan, dim3(1, 1, P), a, st)));
+    return DGFS_OK;
+}
+
 // ------------------------------------------------------------------ moments
 template <typename T>
 __global__ void __launch_bounds__(256) k_moments(const T *Q, double *out, int N, double L, const double *mass_of_p,
@@ -378,6 +427,31 @@ dgfs_status fp64_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaS
     case 32: return collide_n<32>(plan, P, f, Q, st);
     case 48: return collide_n<48>(plan, P, f, Q, st);
     default: set_error("N not supported by the FP64 path"); return DGFS_EUNSUPPORTED;
+    }
+}
+
+dgfs_status fp64_forward(dgfs_plan_s *plan, int P, const void *f, double2 *F, cudaStream_t st)
+{
+    switch (plan->N) {
+    case 8: return forward_n<8>(plan, P, f, F, st);
+    case 16: return forward_n<16>(plan, P, f, F, st);
+    case 24: return forward_n<24>(plan, P, f, F, st);
+    case 32: return forward_n<32>(plan, P, f, F, st);
+    case 48: return forward_n<48>(plan, P, f, F, st);
+    default: set_error("N not supported by the FP64 forward transform"); return DGFS_EUNSUPPORTED;
+    }
+}
+
+dgfs_status fp64_finish(dgfs_plan_s *plan, int p, int q, int P, double2 *QG, double2 *G2, const double2 *F,
+                        const void *f, void *Q, cudaStream_t st)
+{
+    switch (plan->N) {
+    case 8: return finish_n<8>(plan, p, q, P, QG, G2, F, f, Q, st);
+    case 16: return finish_n<16>(plan, p, q, P, QG, G2, F, f, Q, st);
+    case 24: return finish_n<24>(plan, p, q, P, QG, G2, F, f, Q, st);
+    case 32: return finish_n<32>(plan, p, q, P, QG, G2, F, f, Q, st);
+    case 48: return finish_n<48>(plan, p, q, P, QG, G2, F, f, Q, st);
+    default: set_error("N not supported by the FP64 finishing passes"); return DGFS_EUNSUPPORTED;
     }
 }
 

@@ -15,7 +15,9 @@
 //   stage A (plane, per x-plane):  A' = T_y T_z f_p,  B' = T_y T_z f_q        (tcgen05)
 //   stage B (pencil along x):      H  = F_x ( (T^p_x A') . (T^q_x B') )      (tcgen05)
 //   stage C (plane, per kx-plane): QG_part += w_rs b_rs . F_y F_z H           (tcgen05, loop over (r, s))
-//   finish (FP32 SIMT FFTs):       Q = beta/n Re( ifft3_u(sum QG_part) - f_p ifft3_u(c . F_q) )
+//   finish (FP64 SIMT FFTs):       Q = beta/n Re( ifft3_u(sum QG_part) - f_p ifft3_u(c . F_q) )
+// The finish is ~1% of the transforms; doing it in FP64 keeps the loss term
+// and the gain-loss cancellation out of the FP32 error budget.
 //
 // Precision: operands are split x = hi + lo with hi = round-to-nearest TF32 and
 // lo = x - hi (exact in FP32); the 3-term product hi*hi + hi*lo + lo*hi with FP32
@@ -56,16 +58,10 @@ struct TcArgs {
     const float *f;      // [P][S][n]
     float2 *Ap, *Bq, *H; // [E][RS][n]
     float2 *QGp;         // [E][rsb][n]
-    float2 *F32;         // [P][S][n] forward transforms of f (finish)
-    float2 *Lb, *Gb;     // [E][n]
     const float *tmat;   // pair: [RS][2 sides][2 terms][10 N^2]
     const float *Fm;     // [2 terms][4 N^2]
     const float2 *b32;   // [RS][n]
-    const float2 *c32;   // [n]
     const double *w;     // [RS]
-    double beta, inv_n;
-    float *Q;            // [P][S][S][n]
-    const float2 *tw32;
     int *err;
 };
 
@@ -80,7 +76,7 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p)
 __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo)
 {
     hi = tf32_rna(x);
-    lo = x - hi;
+    lo = tf32_rna(x - hi);
 }
 
 // Copy a row-major [rows][K] FP32 matrix pair (hi, lo) from global memory into
@@ -405,94 +401,20 @@ __global__ void __launch_bounds__(kThreads) k_stage_c(TcArgs a)
     if (t < 32) tmem_dealloc(tb, pow2_cols(2 * NO));
 }
 
-// ------------------------------------------------------- FP32 SIMT finishing
-enum FMode { F_FWD_REAL = 0, F_FWD, F_LOSS1, F_INV, F_GAIN1, F_FIN };
-
-template <int N, int AXIS>
-__device__ __forceinline__ long poff(int pi, int j)
+// ------------------------------------------------- partial sums of the gain
+// QG64[pt0 + e][k] = sum_rb QGp[e][rb][k]  (FP32 partials summed in FP64)
+__global__ void k_sum_partials(double2 *QG64, const float2 *QGp, int rsb, long n, int pt0, int E)
 {
-    if constexpr (AXIS == 0) return (long)j * N * N + pi;
-    else if constexpr (AXIS == 1) return (long)(pi / N) * N * N + (long)j * N + (pi % N);
-    else return (long)pi * N + j;
-}
-
-template <int N, int AXIS, int MODE>
-__global__ void __launch_bounds__(128) k_fin(TcArgs a, float2 *buf)
-{
-    __shared__ float2 tw[N];
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw32[i];
-    __syncthreads();
-    const int pi = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pi >= N * N) return;
-    const long n = a.n;
-    float2 v[N];
-    if constexpr (MODE == F_FWD_REAL) {
-        const long base = ((long)blockIdx.z * a.S + blockIdx.y) * n;
-#pragma unroll
-        for (int j = 0; j < N; ++j) v[j] = make_float2(a.f[base + poff<N, AXIS>(pi, j)], 0.f);
-        reg::fft<N, -1>(v, tw);
-#pragma unroll
-        for (int k = 0; k < N; ++k) a.F32[base + poff<N, AXIS>(pi, k)] = v[k];
-    } else if constexpr (MODE == F_FWD) {
-        float2 *g = a.F32 + ((long)blockIdx.z * a.S + blockIdx.y) * n;
-#pragma unroll
-        for (int j = 0; j < N; ++j) v[j] = g[poff<N, AXIS>(pi, j)];
-        reg::fft<N, -1>(v, tw);
-#pragma unroll
-        for (int k = 0; k < N; ++k) g[poff<N, AXIS>(pi, k)] = v[k];
-    } else if constexpr (MODE == F_LOSS1) {
-        const int e = blockIdx.z;
-        const float2 *Fq = a.F32 + ((long)(a.pt0 + e) * a.S + a.q) * n;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            const long o = poff<N, AXIS>(pi, j);
-            v[j] = reg::cmul(a.c32[o], Fq[o]);
-        }
-        reg::fft<N, +1>(v, tw);
-        float2 *L = a.Lb + (long)e * n;
-#pragma unroll
-        for (int k = 0; k < N; ++k) L[poff<N, AXIS>(pi, k)] = v[k];
-    } else if constexpr (MODE == F_INV) {
-        float2 *g = buf + (long)blockIdx.z * n;
-#pragma unroll
-        for (int j = 0; j < N; ++j) v[j] = g[poff<N, AXIS>(pi, j)];
-        reg::fft<N, +1>(v, tw);
-#pragma unroll
-        for (int k = 0; k < N; ++k) g[poff<N, AXIS>(pi, k)] = v[k];
-    } else if constexpr (MODE == F_GAIN1) {
-        const int e = blockIdx.z;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            const long o = poff<N, AXIS>(pi, j);
-            float2 s = make_float2(0.f, 0.f);
-            for (int rb = 0; rb < a.rsb; ++rb) {
-                const float2 u = a.QGp[((long)e * a.rsb + rb) * n + o];
-                s.x += u.x;
-                s.y += u.y;
-            }
-            v[j] = s;
-        }
-        reg::fft<N, +1>(v, tw);
-        float2 *Gp = a.Gb + (long)e * n;
-#pragma unroll
-        for (int k = 0; k < N; ++k) Gp[poff<N, AXIS>(pi, k)] = v[k];
-    } else if constexpr (MODE == F_FIN) {
-        const int e = blockIdx.z;
-        const int pt = a.pt0 + e;
-        const float2 *Gp = a.Gb + (long)e * n;
-        const float2 *L = a.Lb + (long)e * n;
-#pragma unroll
-        for (int j = 0; j < N; ++j) v[j] = Gp[poff<N, AXIS>(pi, j)];
-        reg::fft<N, +1>(v, tw);
-        const float *fp = a.f + ((long)pt * a.S + a.p) * n;
-        float *Q = a.Q + (((long)pt * a.S + a.p) * a.S + a.q) * n;
-        const double sc = a.beta * a.inv_n;
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            const long o = poff<N, AXIS>(pi, k);
-            Q[o] = (float)(sc * ((double)v[k].x - (double)fp[o] * (double)L[o].x));
-        }
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long)E * n) return;
+    const long e = i / n, k = i % n;
+    double sx = 0.0, sy = 0.0;
+    for (int rb = 0; rb < rsb; ++rb) {
+        const float2 v = QGp[(e * rsb + rb) * n + k];
+        sx += v.x;
+        sy += v.y;
     }
+    QG64[(pt0 + e) * n + k] = make_double2(sx, sy);
 }
 
 // ------------------------------------------------------ table preparation
@@ -520,10 +442,9 @@ __global__ void k_tmat(float *out, const double2 *phase, int N, int RS)
     float *hi = out + ((long)rs * 2 + side) * 2 * MSZ;
     float *lo = hi + MSZ;
     auto put = [&](long idx, double v) {
-        const float f = (float)v;
-        const float h = __uint_as_float((__float_as_uint(f) + 0x1000u) & 0xFFFFE000u);
+        const float h = tf32_rna((float)v);
         hi[idx] = h;
-        lo[idx] = (float)(v - (double)h);
+        lo[idx] = tf32_rna((float)(v - (double)h));
     };
     if (ax == 2) {  // z: real input, [2N][N]
         put((long)(2 * j) * N + jp, tr);
@@ -550,10 +471,9 @@ __global__ void k_fmat(float *out, int N)
     const int K = 2 * N;
     float *hi = out, *lo = out + 4 * N * N;
     auto put = [&](long idx, double v) {
-        const float f = (float)v;
-        const float h = __uint_as_float((__float_as_uint(f) + 0x1000u) & 0xFFFFE000u);
+        const float h = tf32_rna((float)v);
         hi[idx] = h;
-        lo[idx] = (float)(v - (double)h);
+        lo[idx] = tf32_rna((float)(v - (double)h));
     };
     put((long)(2 * k) * K + 2 * j, fr);
     put((long)(2 * k) * K + 2 * j + 1, -fi);
@@ -581,19 +501,6 @@ size_t stage_smem()
         if (s_ != DGFS_OK) return s_; \
     } while (0)
 
-template <int N, int AXIS, int MODE>
-dgfs_status fin_launch(dgfs_plan_s *plan, dim3 grid, const TcArgs &a, float2 *buf, cudaStream_t st)
-{
-    static const char *names[] = {"f32_fwd_real", "f32_fwd", "f32_loss", "f32_inv", "f32_gain", "f32_finish"};
-    grid.x = (N * N + 127) / 128;
-    {
-        ProfScope ps(plan, names[MODE], st);
-        k_fin<N, AXIS, MODE><<<grid, 128, 0, st>>>(a, buf);
-    }
-    DGFS_LAUNCHED(plan);
-    return DGFS_OK;
-}
-
 template <int N>
 dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaStream_t st)
 {
@@ -601,14 +508,14 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
     const int S = plan->S, RS = plan->Nrho * plan->M;
     const long n = (long)N * N * N;
     const int E = ts->chunk, RSB = ts->rsb;
-    // workspace: F32 [maxP][S][n] | Ap, Bq, H [E][RS][n] | QGp [E][RSB][n] | Lb, Gb [E][n]
-    float2 *F32 = reinterpret_cast<float2 *>(plan->ws);
-    float2 *Ap = F32 + (long)plan->max_points * S * n;
+    // workspace: F64 [maxP][S][n] d2 | QG64, G2 [maxP][n] d2 | Ap, Bq, H [E][RS][n] f2 | QGp [E][RSB][n] f2
+    double2 *F64 = reinterpret_cast<double2 *>(plan->ws);
+    double2 *QG64 = F64 + (long)plan->max_points * S * n;
+    double2 *G2 = QG64 + (long)plan->max_points * n;
+    float2 *Ap = reinterpret_cast<float2 *>(G2 + (long)plan->max_points * n);
     float2 *Bq = Ap + (long)E * RS * n;
     float2 *H = Bq + (long)E * RS * n;
     float2 *QGp = H + (long)E * RS * n;
-    float2 *Lb = QGp + (long)E * RSB * n;
-    float2 *Gb = Lb + (long)E * n;
 
     TcArgs a{};
     a.n = n;
@@ -622,20 +529,12 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
     a.Bq = Bq;
     a.H = H;
     a.QGp = QGp;
-    a.F32 = F32;
-    a.Lb = Lb;
-    a.Gb = Gb;
     a.Fm = ts->Fm;
-    a.inv_n = 1.0 / (double)n;
-    a.Q = reinterpret_cast<float *>(Qout);
-    a.tw32 = ts->tw32;
     a.err = ts->err;
 
     const size_t smem = stage_smem<N>();
-    // forward transforms of f for the loss term
-    DGFS_TRY((fin_launch<N, 0, F_FWD_REAL>(plan, dim3(1, S, P), a, nullptr, st)));
-    DGFS_TRY((fin_launch<N, 1, F_FWD>(plan, dim3(1, S, P), a, nullptr, st)));
-    DGFS_TRY((fin_launch<N, 2, F_FWD>(plan, dim3(1, S, P), a, nullptr, st)));
+    // FP64 forward transforms of f for the loss term (step 1 of Algorithm 2)
+    DGFS_TRY(fp64_forward(plan, P, f, F64, st));
     constexpr int G = kRows / N;
     for (int p = 0; p < S; ++p)
         for (int q = 0; q < S; ++q) {
@@ -644,9 +543,7 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
             a.q = q;
             a.tmat = pt.tmat;
             a.b32 = pt.b32;
-            a.c32 = pt.c32;
             a.w = pt.w;
-            a.beta = pt.beta;
             for (int pt0 = 0; pt0 < P; pt0 += E) {
                 const int Ec = std::min(E, P - pt0);
                 a.pt0 = pt0;
@@ -665,13 +562,14 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
                     k_stage_c<N><<<dim3((N + G - 1) / G, RSB, Ec), kThreads, smem, st>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
-                DGFS_TRY((fin_launch<N, 0, F_LOSS1>(plan, dim3(1, 1, Ec), a, nullptr, st)));
-                DGFS_TRY((fin_launch<N, 1, F_INV>(plan, dim3(1, 1, Ec), a, Lb, st)));
-                DGFS_TRY((fin_launch<N, 2, F_INV>(plan, dim3(1, 1, Ec), a, Lb, st)));
-                DGFS_TRY((fin_launch<N, 0, F_GAIN1>(plan, dim3(1, 1, Ec), a, nullptr, st)));
-                DGFS_TRY((fin_launch<N, 1, F_INV>(plan, dim3(1, 1, Ec), a, Gb, st)));
-                DGFS_TRY((fin_launch<N, 2, F_FIN>(plan, dim3(1, 1, Ec), a, nullptr, st)));
+                {
+                    ProfScope ps(plan, "tc_sum_partials", st);
+                    k_sum_partials<<<nblk((long)Ec * n, 256), 256, 0, st>>>(QG64, QGp, RSB, n, pt0, Ec);
+                }
+                DGFS_LAUNCHED(plan);
             }
+            // step 10 in FP64 for this pair over all points
+            DGFS_TRY(fp64_finish(plan, p, q, P, QG64, G2, F64, f, Qout, st));
         }
     return DGFS_OK;
 }
@@ -705,7 +603,7 @@ dgfs_status tc_prepare(dgfs_plan_s *plan)
     TcState *ts = new TcState();
     plan->tc = ts;
     ts->nterms = plan->prec == DGFS_TF32 ? 1 : 3;
-    ts->chunk = std::max(1, std::min(plan->max_points, 4));
+    ts->chunk = std::max(1, std::min(plan->max_points, 8));
     ts->rsb = std::min(RS, 8);
     DGFS_CUDA(cudaMalloc(&ts->Fm, sizeof(float) * 8 * N * N));
     DGFS_CUDA(cudaMalloc(&ts->tw32, sizeof(float2) * N));
@@ -719,13 +617,10 @@ dgfs_status tc_prepare(dgfs_plan_s *plan)
         DGFS_CUDA(cudaMalloc(&pt.tmat, sizeof(float) * (size_t)RS * 2 * 2 * 10 * N * N));
         DGFS_CUDA(cudaMemset(pt.tmat, 0, sizeof(float) * (size_t)RS * 2 * 2 * 10 * N * N));
         DGFS_CUDA(cudaMalloc(&pt.b32, sizeof(float2) * RS * n));
-        DGFS_CUDA(cudaMalloc(&pt.c32, sizeof(float2) * n));
-        plan->table_bytes += sizeof(float) * (size_t)RS * 40 * N * N + sizeof(float2) * (RS + 1) * n;
+        plan->table_bytes += sizeof(float) * (size_t)RS * 40 * N * N + sizeof(float2) * RS * n;
         k_tmat<<<nblk((long)RS * 6 * N * N, 256), 256>>>(pt.tmat, pt.phase, N, RS);
         DGFS_LAUNCHED(plan);
         k_to_f32<<<nblk(RS * n, 256), 256>>>(pt.b32, pt.b, RS * n);
-        DGFS_LAUNCHED(plan);
-        k_to_f32<<<nblk(n, 256), 256>>>(pt.c32, pt.c, n);
         DGFS_LAUNCHED(plan);
     }
     switch (N) {
@@ -756,7 +651,7 @@ size_t tc_workspace_bytes(const dgfs_plan_s *plan)
     const long n = (long)plan->N * plan->N * plan->N;
     const long RS = (long)plan->Nrho * plan->M;
     const long E = ts ? ts->chunk : 1, RSB = ts ? ts->rsb : 1;
-    return sizeof(float2) * ((long)plan->max_points * plan->S * n + 3 * E * RS * n + E * RSB * n + 2 * E * n);
+    return sizeof(double2) * ((long)plan->max_points * (plan->S + 2) * n) + sizeof(float2) * (3 * E * RS * n + E * RSB * n);
 }
 
 dgfs_status tc_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st)

@@ -1,8 +1,14 @@
 """GPU parity of the tensor-core (tcgen05) path against the FP64 oracle.
 
-Bar (relative max-norm against the oracle's ||Q||_inf):
-  DGFS_FP32_TC (3xTF32, FP32 accumulation): <= 1e-5
-  DGFS_TF32    (one TF32 product):          reported, <= 1e-2 sanity bound
+Bar for DGFS_FP32_TC (3xTF32 contractions, FP32 accumulation):
+  * over a compared batch of (point, pair) operators:
+        ||Q_gpu - Q_orc||_inf <= 1e-5 ||Q_orc||_inf
+  * per (point, pair):
+        ||Q_gpu - Q_orc||_inf <= 1e-5 ||Q^pq_orc||_inf + 1e-6 ||gain^pq||_inf
+    The second term is FP32 rounding at the scale of the gain (about 17 ulp):
+    near equilibrium Q = gain - loss cancels, so an error bound relative to
+    ||Q^pq|| alone cannot hold for any FP32 evaluation.
+DGFS_TF32 (one TF32 product) is reported with a 1e-2 sanity bound.
 """
 import numpy as np
 import pytest
@@ -34,11 +40,29 @@ def _oracle(pb, f, points=None):
     return prob.collide_all(f, points=points)
 
 
+def _check_pairs(pb, f, Qg, points, tol=TOL_TC):
+    """Per-(point, pair) check against the oracle with the gain-scaled floor;
+    returns the batch relative error."""
+    prob = O.Problem(pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"])
+    S = len(pb["masses"])
+    num, den = 0.0, 0.0
+    for pt in points:
+        for p in range(S):
+            for q in range(S):
+                Qo, d = prob.pair(p, q).collide(f[pt, p], f[pt, q])
+                err = np.abs(Qg[pt, p, q] - Qo).max()
+                bound = tol * np.abs(Qo).max() + 0.1 * tol * d["gain_max"]
+                assert err <= bound, (pt, p, q, err, np.abs(Qo).max(), d["gain_max"])
+                num, den = max(num, err), max(den, np.abs(Qo).max())
+    return num / den
+
+
 def test_c1_homogeneous_n16_fp32_tc_and_tf32():
     pb = W.make_problem("c1_homog_n16")
     Qo = _oracle(pb, pb["f"])
     Qg, _ = _gpu(pb, pb["f"], "fp32_tc")
     assert _rel(Qg, Qo) < TOL_TC
+    _check_pairs(pb, pb["f"], Qg, [0])
     Qt, _ = _gpu(pb, pb["f"], "tf32")
     e = _rel(Qt, Qo)
     assert e < 1e-2
@@ -55,12 +79,8 @@ def test_small_and_ragged(N, M, Nrho, S, P):
     L = 0.5 * N
     f = np.stack([np.stack([W.two_maxwellians(rng, N, L, m) for m in masses]) for _ in range(P)])
     pb = dict(N=N, L=L, M=M, Nrho=Nrho, masses=masses, pairs=pairs)
-    Qo = _oracle(pb, f)
     Qg, _ = _gpu(pb, f, "fp32_tc")
-    for pt in range(P):
-        for p in range(S):
-            for q in range(S):
-                assert _rel(Qg[pt, p, q], Qo[pt, p, q]) < TOL_TC, (pt, p, q, _rel(Qg[pt, p, q], Qo[pt, p, q]))
+    assert _check_pairs(pb, f, Qg, range(P)) < TOL_TC
 
 
 def test_c2_slab_n32_sampled_points():
@@ -68,12 +88,8 @@ def test_c2_slab_n32_sampled_points():
     M = 12, N_rho = 8, VSS); the oracle checks sampled points."""
     pb = W.make_problem("c2_slab_n32")
     Qg, plan = _gpu(pb, pb["f"], "fp32_tc")
-    pts = [0, 13, 23]
-    Qo = _oracle(pb, pb["f"], points=pts)
-    for i, pt in enumerate(pts):
-        for p in range(2):
-            for q in range(2):
-                assert _rel(Qg[pt, p, q], Qo[i, p, q]) < TOL_TC, (pt, p, q, _rel(Qg[pt, p, q], Qo[i, p, q]))
+    batch = _check_pairs(pb, pb["f"], Qg, [0, 13, 23])
+    assert batch < TOL_TC
 
 
 def test_n48_single_pair():
@@ -84,8 +100,8 @@ def test_n48_single_pair():
     pb = dict(N=N, L=L, M=6, Nrho=3, masses=[1.0, 2.0], pairs=pairs)
     Qg, _ = _gpu(pb, f, "fp32_tc")
     prob = O.Problem(N, L, 6, 3, [1.0, 2.0], pairs)
-    Qo, _ = prob.pair(1, 0).collide(f[0, 1], f[0, 0])
-    assert _rel(Qg[0, 1, 0], Qo) < TOL_TC
+    Qo, d = prob.pair(1, 0).collide(f[0, 1], f[0, 0])
+    assert np.abs(Qg[0, 1, 0] - Qo).max() <= TOL_TC * np.abs(Qo).max() + 0.1 * TOL_TC * d["gain_max"]
 
 
 def test_krook_wu_closed_form_on_tensor_cores():
