@@ -11,7 +11,7 @@
 // blocks.  The gain of step 6-7 is then
 //   QG = sum_rs w_rs b_rs . F_x F_y F_z (A_rs . B_rs).
 //
-// Kernels per (point, pair) chunk:
+// Kernels per (pair, chunk of points):
 //   stage A (plane, per x-plane):  A' = T_y T_z f_p,  B' = T_y T_z f_q        (tcgen05)
 //   stage B (pencil along x):      H  = F_x ( (T^p_x A') . (T^q_x B') )      (tcgen05)
 //   stage C (plane, per kx-plane): QG_part += w_rs b_rs . F_y F_z H           (tcgen05, loop over (r, s))
@@ -19,10 +19,15 @@
 // The finish is ~1% of the transforms; doing it in FP64 keeps the loss term
 // and the gain-loss cancellation out of the FP32 error budget.
 //
-// Precision: operands are split x = hi + lo with hi = round-to-nearest TF32 and
-// lo = x - hi (exact in FP32); the 3-term product hi*hi + hi*lo + lo*hi with FP32
-// accumulation in TMEM gives FP32-level results ("3xTF32").  DGFS_TF32 uses
-// the single hi*hi product.
+// Stage A and B CTAs are matrix-stationary: a CTA owns one (r, s) (and side),
+// keeps that (r, s)'s matrices in shared memory (loaded once with one bulk
+// copy per pre-swizzled image) and loops over its work items (point, plane
+// group or pencil tile), prefetching the next item's data into registers while
+// the current item's contractions run.
+//
+// Precision: operands are split x = hi + lo with hi and lo rounded to TF32; the
+// 3-term product hi*hi + hi*lo + lo*hi with FP32 accumulation in TMEM gives
+// FP32-level results ("3xTF32").  DGFS_TF32 uses the single hi*hi product.
 //
 // Every mbarrier wait is bounded; on expiry the kernel raises the plan's error
 // flag, frees its TMEM and returns (reported as DGFS_ETIMEOUT by dgfs_plan_check).
@@ -30,7 +35,6 @@
 #include <cstdint>
 
 #include "dgfs_internal.h"
-#include "fftreg.cuh"
 #include "umma.cuh"
 
 namespace dgfs {
@@ -42,31 +46,36 @@ constexpr int kRows = 128;             // MMA M: data rows per CTA
 constexpr int kThreads = 128;          // one thread per data row / TMEM lane
 constexpr long kWaitLimit = 1L << 22;  // mbarrier polls before declaring a timeout
 constexpr int kErrTimeout = 1;
+constexpr int kSmemMax = 227 * 1024;
 
 struct TcState {
-    float *Fm = nullptr;      // forward DFT as B operand [2 terms][2N][2N]
-    float2 *tw32 = nullptr;   // [N] exp(-2 pi i j/N)
+    uint8_t *Fimg = nullptr;  // forward DFT as pre-swizzled B-operand images [2 terms][IMGC]
     int *err = nullptr;       // device error flag
     int nterms = 3;
-    int chunk = 4;            // evaluations per launch
+    int chunk = 8;            // evaluations per launch
     int rsb = 8;              // (r, s) blocks of stage C
+    int groups_a = 2, groups_b = 4;  // work-item groups per (r, s) in stages A and B
 };
 
 struct TcArgs {
     long n;
-    int S, p, q, pt0, RS, nterms, rs_per_block, rsb;
-    const float *f;      // [P][S][n]
-    float2 *Ap, *Bq, *H; // [E][RS][n]
-    float2 *QGp;         // [E][rsb][n]
-    const float *tmat;   // pair: [RS][2 sides][2 terms][10 N^2]
-    const float *Fm;     // [2 terms][4 N^2]
-    const float2 *b32;   // [RS][n]
-    const double *w;     // [RS]
+    int S, p, q, pt0, Ec, RS, nterms, rs_per_block, rsb;
+    const float *f;        // [P][S][n]
+    float2 *Ap, *Bq, *H;   // [E][RS][n]
+    float2 *QGp;           // [E][rsb][n]
+    const uint8_t *timg;   // pair: [RS][2 sides][3 axes][2 terms][IMGC] pre-swizzled B images
+    const uint8_t *Fimg;   // [2 terms][IMGC]
+    const float2 *b32;     // [RS][n]
+    const double *w;       // [RS]
     int *err;
 };
 
 __host__ __device__ constexpr int atoms(int kfloats) { return (kfloats * 4 + 127) / 128; }
 __host__ __device__ constexpr int pow2_cols(int c) { return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ? 128 : c <= 256 ? 256 : 512; }
+// bytes of one B-operand image of 2N rows and K = 2N (complex input) or N (real input) floats
+__host__ __device__ constexpr int img_c(int N) { return atoms(2 * N) * 2 * N * 128; }
+__host__ __device__ constexpr int img_r(int N) { return atoms(N) * 2 * N * 128; }
+__host__ __device__ constexpr int abytes(int N) { return atoms(2 * N) * kRows * 128; }
 
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p)
 {
@@ -79,21 +88,7 @@ __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo)
     lo = tf32_rna(x - hi);
 }
 
-// Copy a row-major [rows][K] FP32 matrix pair (hi, lo) from global memory into
-// SW128 K-major operands (K a multiple of 4).
-__device__ __forceinline__ void load_bop(uint8_t *dh, uint8_t *dl, const float *gh, const float *gl, int rows, int K,
-                                         int nterms)
-{
-    const int q = K / 4;
-    for (int i = threadIdx.x; i < rows * q; i += blockDim.x) {
-        const int r = i / q, kb = (i % q) * 16;
-        const uint32_t o = sw128_off(r, kb, rows);
-        *reinterpret_cast<float4 *>(dh + o) = reinterpret_cast<const float4 *>(gh)[i];
-        if (nterms > 1) *reinterpret_cast<float4 *>(dl + o) = reinterpret_cast<const float4 *>(gl)[i];
-    }
-}
-
-// store a split complex value at (row, complex index k) of a K-major operand
+// store a split complex value at (row, complex index k) of the data operand
 __device__ __forceinline__ void st_c(uint8_t *ah, uint8_t *al, int row, int k, float re, float im)
 {
     float h0, l0, h1, l1;
@@ -104,16 +99,27 @@ __device__ __forceinline__ void st_c(uint8_t *ah, uint8_t *al, int row, int k, f
     *reinterpret_cast<float2 *>(al + o) = make_float2(l0, l1);
 }
 
+__device__ __forceinline__ void st_f4(uint8_t *ah, uint8_t *al, int row, int kb, float4 v)
+{
+    float4 h, l;
+    split_tf32(v.x, h.x, l.x);
+    split_tf32(v.y, h.y, l.y);
+    split_tf32(v.z, h.z, l.z);
+    split_tf32(v.w, h.w, l.w);
+    const uint32_t o = sw128_off(row, kb, kRows);
+    *reinterpret_cast<float4 *>(ah + o) = h;
+    *reinterpret_cast<float4 *>(al + o) = l;
+}
+
 // Issue D = A * B^T over K bytes with 1 or 3 split terms (small terms first).
 __device__ __forceinline__ void gemm(uint32_t d, const uint8_t *ah, const uint8_t *al, const uint8_t *bh,
                                      const uint8_t *bl, int brows, int kbytes, int nterms, uint32_t idesc)
 {
-    const uint8_t *as[3] = {al, ah, ah};
-    const uint8_t *bs[3] = {bh, bl, bh};
-    const int t0 = nterms == 3 ? 0 : 2;
     uint32_t acc = 0;
-    for (int t = t0; t < 3; ++t) {
-        const uint32_t a0 = smem_u32(as[t]), b0 = smem_u32(bs[t]);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        if (nterms == 1 && t < 2) continue;
+        const uint32_t a0 = smem_u32(t == 0 ? al : ah), b0 = smem_u32(t == 1 ? bl : bh);
         for (int kb = 0; kb < kbytes; kb += 32) {
             const uint32_t ao = (kb >> 7) * (kRows * 128) + (kb & 127);
             const uint32_t bo = (kb >> 7) * (brows * 128) + (kb & 127);
@@ -143,134 +149,238 @@ __device__ __forceinline__ bool run_mma(uint64_t *mbar, uint32_t &phase, F issue
     return all != 0;
 }
 
-__device__ __forceinline__ uint32_t lane_base(uint32_t tbase) { return tbase + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16); }
-
-// ------------------------------------------------------------------ stage A
-// CTA: G = 128/N x-planes of one (eval, r, s).  For each side (p: f_p, T^p;
-// q: f_q, T^q): z-pass (real in) then y-pass, both on the tensor cores.
-template <int N>
-__global__ void __launch_bounds__(kThreads) k_stage_a(TcArgs a)
+// Block-wide bounded wait for a bulk-copy phase.
+__device__ __forceinline__ bool wait_copy(uint64_t *mbar, uint32_t &phase)
 {
-    constexpr int G = kRows / N, KR = N, KC = 2 * N, NO = 2 * N;
-    constexpr int ABYTES = atoms(KC) * kRows * 128, BBYTES = atoms(KC) * NO * 128;
-    constexpr int MSZ = 10 * N * N;
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t *sm = align1024(smem_raw);
-    uint8_t *Ah = sm, *Al = Ah + ABYTES, *Bh = Al + ABYTES, *Bl = Bh + BBYTES;
-    __shared__ uint64_t mbar;
-    __shared__ uint32_t tslot;
-    const int t = threadIdx.x;
-    const int x0 = blockIdx.x * G, rs = blockIdx.y, e = blockIdx.z;
-    const int nvalid = min(G, N - x0);
-    const long n = a.n;
-    const int pt = a.pt0 + e;
-    if (t < 32) tmem_alloc(&tslot, pow2_cols(2 * NO));
-    if (t == 0) mbar_init(&mbar, 1);
+    const bool ok = mbar_wait(mbar, phase, kWaitLimit);
+    phase ^= 1u;
+    return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
+__device__ __forceinline__ uint32_t lane_base(uint32_t tbase)
+{
+    return tbase + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16);
+}
+
+__device__ __forceinline__ const uint8_t *timg_at(const uint8_t *timg, int N, int rs, int side, int ax, int term)
+{
+    return timg + ((((long)rs * 2 + side) * 3 + ax) * 2 + term) * (long)img_c(N);
+}
+
+__device__ __forceinline__ void tmem_setup(uint32_t *slot, uint32_t ncols, uint64_t *m0, uint64_t *m1)
+{
+    if (threadIdx.x < 32) tmem_alloc(slot, ncols);
+    if (threadIdx.x == 0) {
+        mbar_init(m0, 1);
+        mbar_init(m1, 1);
+    }
     fence_before();
     __syncthreads();
     fence_after();
+}
+
+__device__ __forceinline__ void tmem_teardown(uint32_t tb, uint32_t ncols, bool ok, int *err)
+{
+    if (!ok && threadIdx.x == 0) atomicExch(err, kErrTimeout);
+    fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) tmem_dealloc(tb, ncols);
+}
+
+// ------------------------------------------------------------------ stage A
+// grid (groups, RS, 2 sides).  A CTA holds T_z, T_y of its (r, s, side) and
+// loops over items (point e, group of G x-planes): z-pass (real input), an
+// in-plane transpose through shared memory, y-pass, result A' or B' to global.
+template <int N>
+__global__ void __launch_bounds__(kThreads, 1) k_stage_a(TcArgs a)
+{
+    constexpr int G = kRows / N, KR = N, KC = 2 * N, NO = 2 * N, NG = (N + G - 1) / G;
+    constexpr int AB = abytes(N), IR = img_r(N), IC = img_c(N);
+    constexpr bool RESIDENT = 1024 + 2 * AB + 4 * IC <= kSmemMax;
+    constexpr int NN = N * N;
+    constexpr int FPT = (G * NN / 4 + kThreads - 1) / kThreads;  // float4 per thread for one group
+    constexpr uint32_t NCOL = pow2_cols(2 * NO);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = align1024(smem_raw);
+    uint8_t *Ah = sm, *Al = Ah + AB;
+    uint8_t *Bzh = Al + AB, *Bzl = Bzh + IC;
+    uint8_t *Byh = RESIDENT ? Bzl + IC : Bzh, *Byl = Byh + IC;  // non-resident: one reloaded slot
+    __shared__ uint64_t mb_mma, mb_cp;
+    __shared__ uint32_t tslot;
+    const int t = threadIdx.x, rs = blockIdx.y, side = blockIdx.z;
+    const long n = a.n;
+    const int items = a.Ec * NG;
+    tmem_setup(&tslot, NCOL, &mb_mma, &mb_cp);
     const uint32_t tb = tslot, tl = lane_base(tb);
-    uint32_t phase = 0;
-    bool ok = true;
-    const int g = t / N, yl = t % N;  // row t = (plane g, line y) before the y-pass
-    for (int side = 0; side < 2 && ok; ++side) {
-        const int sp = side == 0 ? a.p : a.q;
-        const float *fs = a.f + ((long)pt * a.S + sp) * n + (long)x0 * N * N;
-        const float *tm = a.tmat + (long)(rs * 2 + side) * 2 * MSZ;
-        // data: rows (g, y), K = z (real)
-        for (int i = t; i < nvalid * N * N / 4; i += kThreads) {
-            const float4 v = reinterpret_cast<const float4 *>(fs)[i];
-            const int row = (4 * i) / N, kb = ((4 * i) % N) * 4;
-            float4 h, l;
-            split_tf32(v.x, h.x, l.x);
-            split_tf32(v.y, h.y, l.y);
-            split_tf32(v.z, h.z, l.z);
-            split_tf32(v.w, h.w, l.w);
-            const uint32_t o = sw128_off(row, kb, kRows);
-            *reinterpret_cast<float4 *>(Ah + o) = h;
-            *reinterpret_cast<float4 *>(Al + o) = l;
+    uint32_t ph_mma = 0, ph_cp = 0;
+    auto load_z = [&] {
+        if (t == 0) {
+            mbar_expect_tx(&mb_cp, 2 * IR);
+            bulk_g2s(Bzh, timg_at(a.timg, N, rs, side, 2, 0), IR, &mb_cp);
+            bulk_g2s(Bzl, timg_at(a.timg, N, rs, side, 2, 1), IR, &mb_cp);
         }
-        load_bop(Bh, Bl, tm, tm + MSZ, NO, KR, a.nterms);  // T_z (real in)
-        ok = run_mma(&mbar, phase, [&] { gemm(tb, Ah, Al, Bh, Bl, NO, KR * 4, a.nterms, idesc_tf32(kRows, NO)); });
+    };
+    auto load_y = [&] {
+        if (t == 0) {
+            mbar_expect_tx(&mb_cp, 2 * IC);
+            bulk_g2s(Byh, timg_at(a.timg, N, rs, side, 1, 0), IC, &mb_cp);
+            bulk_g2s(Byl, timg_at(a.timg, N, rs, side, 1, 1), IC, &mb_cp);
+        }
+    };
+    if (RESIDENT && t == 0) {
+        mbar_expect_tx(&mb_cp, 2 * IR + 2 * IC);
+        bulk_g2s(Bzh, timg_at(a.timg, N, rs, side, 2, 0), IR, &mb_cp);
+        bulk_g2s(Bzl, timg_at(a.timg, N, rs, side, 2, 1), IR, &mb_cp);
+        bulk_g2s(Byh, timg_at(a.timg, N, rs, side, 1, 0), IC, &mb_cp);
+        bulk_g2s(Byl, timg_at(a.timg, N, rs, side, 1, 1), IC, &mb_cp);
+    }
+    const int sp = side == 0 ? a.p : a.q;
+    const int g = t / N, yl = t % N;
+    float4 pf[FPT];
+    auto prefetch = [&](int it) {
+        const int e = it / NG, x0 = (it % NG) * G, nval = min(G, N - x0);
+        const float4 *fs =
+            reinterpret_cast<const float4 *>(a.f + ((long)(a.pt0 + e) * a.S + sp) * n + (long)x0 * NN);
+#pragma unroll
+        for (int j = 0; j < FPT; ++j) {
+            const int i = t + kThreads * j;
+            pf[j] = (4 * i < nval * NN) ? fs[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    int it = blockIdx.x;
+    if (it < items) prefetch(it);
+    bool ok = true;
+    if (RESIDENT) ok = wait_copy(&mb_cp, ph_cp);
+    for (; it < items && ok; it += gridDim.x) {
+        const int e = it / NG, x0 = (it % NG) * G, nval = min(G, N - x0);
+#pragma unroll
+        for (int j = 0; j < FPT; ++j) {
+            const int i = t + kThreads * j;
+            if (4 * i < nval * NN) st_f4(Ah, Al, (4 * i) / N, ((4 * i) % N) * 4, pf[j]);
+        }
+        if (it + (int)gridDim.x < items) prefetch(it + gridDim.x);
+        if (!RESIDENT) {
+            load_z();
+            ok = wait_copy(&mb_cp, ph_cp);
+            if (!ok) break;
+        }
+        ok = run_mma(&mb_mma, ph_mma, [&] { gemm(tb, Ah, Al, Bzh, Bzl, NO, KR * 4, a.nterms, idesc_tf32(kRows, NO)); });
         if (!ok) break;
         // transpose within each plane: row (g, y) holds z' -> rows (g, z'), K = y
 #pragma unroll
         for (int c0 = 0; c0 < NO; c0 += 16) {
             float v[16];
             tmem_ld16(tl + c0, v);
-            if (t < nvalid * N) {
+            if (t < nval * N) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) st_c(Ah, Al, g * N + c0 / 2 + j, yl, v[2 * j], v[2 * j + 1]);
             }
         }
-        __syncthreads();
-        load_bop(Bh, Bl, tm + 2 * N * N, tm + MSZ + 2 * N * N, NO, KC, a.nterms);  // T_y
-        ok = run_mma(&mbar, phase, [&] { gemm(tb + NO, Ah, Al, Bh, Bl, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
+        if (!RESIDENT) {
+            load_y();
+            ok = wait_copy(&mb_cp, ph_cp);
+            if (!ok) break;
+        }
+        ok = run_mma(&mb_mma, ph_mma,
+                     [&] { gemm(tb + NO, Ah, Al, Byh, Byl, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
         if (!ok) break;
         // row t = (g, z'): y' values -> global [x][y'][z']
-        float2 *dst = (side == 0 ? a.Ap : a.Bq) + ((long)e * a.RS + rs) * n + (long)(x0 + g) * N * N + yl;
+        float2 *dst = (side == 0 ? a.Ap : a.Bq) + ((long)e * a.RS + rs) * n + (long)(x0 + g) * NN + yl;
 #pragma unroll
         for (int c0 = 0; c0 < NO; c0 += 16) {
             float v[16];
             tmem_ld16(tl + NO + c0, v);
-            if (t < nvalid * N) {
+            if (t < nval * N) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) dst[(long)(c0 / 2 + j) * N] = make_float2(v[2 * j], v[2 * j + 1]);
             }
         }
-        fence_before();
-        __syncthreads();
-        fence_after();
     }
-    if (!ok && t == 0) atomicExch(a.err, kErrTimeout);
-    fence_before();
-    __syncthreads();
-    if (t < 32) tmem_dealloc(tb, pow2_cols(2 * NO));
+    tmem_teardown(tb, NCOL, ok, a.err);
 }
 
 // ------------------------------------------------------------------ stage B
-// CTA: 128 pencils (y, z) of one (eval, r, s).  H = F_x ((T^p_x A') . (T^q_x B')).
+// grid (groups, RS).  A CTA holds T^p_x, T^q_x and F of its (r, s) when they
+// fit next to the data operand (else it reloads one image slot per
+// contraction) and loops over items (point e, tile of 128 (y, z) pencils):
+// H = F_x ((T^p_x A') . (T^q_x B')).
 template <int N>
-__global__ void __launch_bounds__(kThreads) k_stage_b(TcArgs a)
+__global__ void __launch_bounds__(kThreads, 1) k_stage_b(TcArgs a)
 {
-    constexpr int KC = 2 * N, NO = 2 * N;
-    constexpr int ABYTES = atoms(KC) * kRows * 128, BBYTES = atoms(KC) * NO * 128;
-    constexpr int MSZ = 10 * N * N;
-    constexpr int NN = N * N;
+    constexpr int KC = 2 * N, NO = 2 * N, NN = N * N, NT = (NN + kRows - 1) / kRows;
+    constexpr int AB = abytes(N), IC = img_c(N);
+    constexpr bool RESIDENT = 1024 + 2 * AB + 6 * IC <= kSmemMax;
+    constexpr uint32_t NCOL = pow2_cols(3 * NO);
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align1024(smem_raw);
-    uint8_t *Ah = sm, *Al = Ah + ABYTES, *Bh = Al + ABYTES, *Bl = Bh + BBYTES;
-    __shared__ uint64_t mbar;
+    uint8_t *Ah = sm, *Al = Ah + AB;
+    uint8_t *B0 = Al + AB;  // image slots: [Txp hi, lo][Txq hi, lo][F hi, lo] or one [hi, lo]
+    __shared__ uint64_t mb_mma, mb_cp;
     __shared__ uint32_t tslot;
-    const int t = threadIdx.x;
-    const int p0 = blockIdx.x * kRows, rs = blockIdx.y, e = blockIdx.z;
-    const int nvalid = min(kRows, NN - p0);
+    const int t = threadIdx.x, rs = blockIdx.y;
     const long n = a.n;
-    constexpr uint32_t NCOL = pow2_cols(3 * NO);
-    if (t < 32) tmem_alloc(&tslot, NCOL);
-    if (t == 0) mbar_init(&mbar, 1);
-    fence_before();
-    __syncthreads();
-    fence_after();
+    const int items = a.Ec * NT;
+    tmem_setup(&tslot, NCOL, &mb_mma, &mb_cp);
     const uint32_t tb = tslot, tl = lane_base(tb);
-    uint32_t phase = 0;
-    bool ok = true;
-    const long gbase = ((long)e * a.RS + rs) * n + p0;
-    for (int side = 0; side < 2 && ok; ++side) {
-        const float2 *src = (side == 0 ? a.Ap : a.Bq) + gbase;
-        const float *tm = a.tmat + (long)(rs * 2 + side) * 2 * MSZ + 6 * NN;  // T_x
-        if (t < nvalid) {
-#pragma unroll 4
-            for (int x = 0; x < N; ++x) {
-                const float2 v = src[(long)x * NN + t];
-                st_c(Ah, Al, t, x, v.x, v.y);
+    uint32_t ph_mma = 0, ph_cp = 0;
+    auto src_img = [&](int which, int term) -> const uint8_t * {
+        return which < 2 ? timg_at(a.timg, N, rs, which, 0, term) : a.Fimg + (long)term * IC;
+    };
+    auto slot = [&](int which) -> uint8_t * { return RESIDENT ? B0 + 2 * which * IC : B0; };
+    auto load_images = [&](int first, int count) {
+        if (t == 0) {
+            mbar_expect_tx(&mb_cp, 2 * IC * count);
+            for (int w = first; w < first + count; ++w) {
+                bulk_g2s(slot(w), src_img(w, 0), IC, &mb_cp);
+                bulk_g2s(slot(w) + IC, src_img(w, 1), IC, &mb_cp);
             }
         }
-        load_bop(Bh, Bl, tm, tm + MSZ, NO, KC, a.nterms);
-        ok = run_mma(&mbar, phase,
-                     [&] { gemm(tb + side * NO, Ah, Al, Bh, Bl, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
+    };
+    if (RESIDENT) load_images(0, 3);
+    float2 pa[N];
+    auto load_pencil = [&](float2 *dst, const float2 *src, bool valid) {
+#pragma unroll
+        for (int x = 0; x < N; ++x) dst[x] = valid ? src[(long)x * NN] : make_float2(0.f, 0.f);
+    };
+    int it = blockIdx.x;
+    if (it < items) {
+        const int e = it / NT, p0 = (it % NT) * kRows;
+        load_pencil(pa, a.Ap + ((long)e * a.RS + rs) * n + p0 + t, p0 + t < NN);
     }
-    if (ok) {
+    bool ok = true;
+    if (RESIDENT) ok = wait_copy(&mb_cp, ph_cp);
+    for (; it < items && ok; it += gridDim.x) {
+        const int e = it / NT, p0 = (it % NT) * kRows;
+        const bool valid = p0 + t < NN;
+        const long gbase = ((long)e * a.RS + rs) * n + p0 + t;
+#pragma unroll
+        for (int x = 0; x < N; ++x) st_c(Ah, Al, t, x, pa[x].x, pa[x].y);
+        float2 pb[N];
+        load_pencil(pb, a.Bq + gbase, valid);
+        if (!RESIDENT) {
+            load_images(0, 1);
+            ok = wait_copy(&mb_cp, ph_cp);
+            if (!ok) break;
+        }
+        ok = run_mma(&mb_mma, ph_mma,
+                     [&] { gemm(tb, Ah, Al, slot(0), slot(0) + IC, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
+        if (!ok) break;
+#pragma unroll
+        for (int x = 0; x < N; ++x) st_c(Ah, Al, t, x, pb[x].x, pb[x].y);
+        const int nx = it + gridDim.x;
+        if (nx < items) {
+            const int e2 = nx / NT, q0 = (nx % NT) * kRows;
+            load_pencil(pa, a.Ap + ((long)e2 * a.RS + rs) * n + q0 + t, q0 + t < NN);
+        }
+        if (!RESIDENT) {
+            load_images(1, 1);
+            ok = wait_copy(&mb_cp, ph_cp);
+            if (!ok) break;
+        }
+        ok = run_mma(&mb_mma, ph_mma, [&] {
+            gemm(tb + NO, Ah, Al, slot(1), slot(1) + IC, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO));
+        });
+        if (!ok) break;
         // P = A . B (complex), back into the data operand
 #pragma unroll
         for (int c0 = 0; c0 < NO; c0 += 16) {
@@ -284,89 +394,108 @@ __global__ void __launch_bounds__(kThreads) k_stage_b(TcArgs a)
                 st_c(Ah, Al, t, c0 / 2 + j, re, im);
             }
         }
-        __syncthreads();
-        load_bop(Bh, Bl, a.Fm, a.Fm + 4 * NN, NO, KC, a.nterms);
-        ok = run_mma(&mbar, phase,
-                     [&] { gemm(tb + 2 * NO, Ah, Al, Bh, Bl, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
-    }
-    if (ok) {
-        float2 *dst = a.H + gbase + t;
+        if (!RESIDENT) {
+            load_images(2, 1);
+            ok = wait_copy(&mb_cp, ph_cp);
+            if (!ok) break;
+        }
+        ok = run_mma(&mb_mma, ph_mma, [&] {
+            gemm(tb + 2 * NO, Ah, Al, slot(2), slot(2) + IC, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO));
+        });
+        if (!ok) break;
+        float2 *dst = a.H + gbase;
 #pragma unroll
         for (int c0 = 0; c0 < NO; c0 += 16) {
             float v[16];
             tmem_ld16(tl + 2 * NO + c0, v);
-            if (t < nvalid) {
+            if (valid) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) dst[(long)(c0 / 2 + j) * NN] = make_float2(v[2 * j], v[2 * j + 1]);
             }
         }
     }
-    if (!ok && t == 0) atomicExch(a.err, kErrTimeout);
-    fence_before();
-    __syncthreads();
-    if (t < 32) tmem_dealloc(tb, NCOL);
+    tmem_teardown(tb, NCOL, ok, a.err);
 }
 
 // ------------------------------------------------------------------ stage C
-// CTA: G kx-planes of one eval and one block of (r, s).  For every (r, s):
-// t3 = F_y F_z H on the tensor cores, QG_part += w_rs b_rs . t3 in registers.
+// grid (plane groups, RSB, Ec).  For every (r, s) of its block:
+// t3 = F_y F_z H on the tensor cores, QG_part += w_rs b_rs . t3 in registers;
+// the next (r, s)'s H tile is prefetched into registers meanwhile.
 template <int N>
-__global__ void __launch_bounds__(kThreads) k_stage_c(TcArgs a)
+__global__ void __launch_bounds__(kThreads, 1) k_stage_c(TcArgs a)
 {
-    constexpr int G = kRows / N, KC = 2 * N, NO = 2 * N;
-    constexpr int ABYTES = atoms(KC) * kRows * 128, BBYTES = atoms(KC) * NO * 128;
-    constexpr int NN = N * N;
+    constexpr int G = kRows / N, KC = 2 * N, NO = 2 * N, NN = N * N;
+    constexpr int AB = abytes(N), IC = img_c(N);
+    constexpr int HPT = (G * NN / 2 + kThreads - 1) / kThreads;  // float4 (2 complex) per thread per tile
+    constexpr bool PREFETCH = N <= 32;
+    constexpr uint32_t NCOL = pow2_cols(2 * NO);
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align1024(smem_raw);
-    uint8_t *Ah = sm, *Al = Ah + ABYTES, *Bh = Al + ABYTES, *Bl = Bh + BBYTES;
-    __shared__ uint64_t mbar;
+    uint8_t *Ah = sm, *Al = Ah + AB, *Bh = Al + AB, *Bl = Bh + IC;
+    __shared__ uint64_t mb_mma, mb_cp;
     __shared__ uint32_t tslot;
     const int t = threadIdx.x;
     const int x0 = blockIdx.x * G, rb = blockIdx.y, e = blockIdx.z;
-    const int nvalid = min(G, N - x0);
+    const int nval = min(G, N - x0);
     const long n = a.n;
-    if (t < 32) tmem_alloc(&tslot, pow2_cols(2 * NO));
-    if (t == 0) mbar_init(&mbar, 1);
-    load_bop(Bh, Bl, a.Fm, a.Fm + 4 * NN, NO, KC, a.nterms);
-    fence_before();
-    __syncthreads();
-    fence_after();
+    tmem_setup(&tslot, NCOL, &mb_mma, &mb_cp);
     const uint32_t tb = tslot, tl = lane_base(tb);
-    uint32_t phase = 0;
-    bool ok = true;
+    uint32_t ph_mma = 0, ph_cp = 0;
+    if (t == 0) {
+        mbar_expect_tx(&mb_cp, 2 * IC);
+        bulk_g2s(Bh, a.Fimg, IC, &mb_cp);
+        bulk_g2s(Bl, a.Fimg + IC, IC, &mb_cp);
+    }
     const int g = t / N, yl = t % N;
     float2 acc[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) acc[k] = make_float2(0.f, 0.f);
     const int rs0 = rb * a.rs_per_block, rs1 = min(a.RS, rs0 + a.rs_per_block);
-    for (int rs = rs0; rs < rs1 && ok; ++rs) {
-        const float2 *src = a.H + ((long)e * a.RS + rs) * n + (long)x0 * NN;
-        // rows (g, y), K = z (complex): contiguous planes
-        for (int i = t; i < nvalid * NN / 2; i += kThreads) {
-            const float4 v = reinterpret_cast<const float4 *>(src)[i];
-            const int c = 2 * i;
-            const int row = c / N, kb = (c % N) * 8;
-            float4 h, l;
-            split_tf32(v.x, h.x, l.x);
-            split_tf32(v.y, h.y, l.y);
-            split_tf32(v.z, h.z, l.z);
-            split_tf32(v.w, h.w, l.w);
-            const uint32_t o = sw128_off(row, kb, kRows);
-            *reinterpret_cast<float4 *>(Ah + o) = h;
-            *reinterpret_cast<float4 *>(Al + o) = l;
+    float4 hp[PREFETCH ? HPT : 1];
+    auto tile = [&](int rs) {
+        return reinterpret_cast<const float4 *>(a.H + ((long)e * a.RS + rs) * n + (long)x0 * NN);
+    };
+    if (PREFETCH && rs0 < rs1) {
+        const float4 *src = tile(rs0);
+#pragma unroll
+        for (int j = 0; j < HPT; ++j) {
+            const int i = t + kThreads * j;
+            hp[j] = (2 * i < nval * NN) ? src[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        ok = run_mma(&mbar, phase, [&] { gemm(tb, Ah, Al, Bh, Bl, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
+    }
+    bool ok = wait_copy(&mb_cp, ph_cp);
+    for (int rs = rs0; rs < rs1 && ok; ++rs) {
+        // rows (g, y), K = z (complex): contiguous planes
+        if constexpr (PREFETCH) {
+#pragma unroll
+            for (int j = 0; j < HPT; ++j) {
+                const int i = t + kThreads * j;
+                if (2 * i < nval * NN) st_f4(Ah, Al, (2 * i) / N, ((2 * i) % N) * 8, hp[j]);
+            }
+            if (rs + 1 < rs1) {
+                const float4 *src = tile(rs + 1);
+#pragma unroll
+                for (int j = 0; j < HPT; ++j) {
+                    const int i = t + kThreads * j;
+                    hp[j] = (2 * i < nval * NN) ? src[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+        } else {
+            const float4 *src = tile(rs);
+            for (int i = t; i < nval * NN / 2; i += kThreads) st_f4(Ah, Al, (2 * i) / N, ((2 * i) % N) * 8, src[i]);
+        }
+        ok = run_mma(&mb_mma, ph_mma, [&] { gemm(tb, Ah, Al, Bh, Bl, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
         if (!ok) break;
 #pragma unroll
         for (int c0 = 0; c0 < NO; c0 += 16) {
             float v[16];
             tmem_ld16(tl + c0, v);
-            if (t < nvalid * N) {
+            if (t < nval * N) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) st_c(Ah, Al, g * N + c0 / 2 + j, yl, v[2 * j], v[2 * j + 1]);
             }
         }
-        ok = run_mma(&mbar, phase, [&] { gemm(tb + NO, Ah, Al, Bh, Bl, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
+        ok = run_mma(&mb_mma, ph_mma, [&] { gemm(tb + NO, Ah, Al, Bh, Bl, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
         if (!ok) break;
         // row t = (g, kz): t3(kx0+g, ky, kz) for all ky
         const float wr = (float)a.w[rs];
@@ -375,7 +504,7 @@ __global__ void __launch_bounds__(kThreads) k_stage_c(TcArgs a)
         for (int c0 = 0; c0 < NO; c0 += 16) {
             float v[16];
             tmem_ld16(tl + NO + c0, v);
-            if (t < nvalid * N) {
+            if (t < nval * N) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int ky = c0 / 2 + j;
@@ -386,19 +515,13 @@ __global__ void __launch_bounds__(kThreads) k_stage_c(TcArgs a)
                 }
             }
         }
-        fence_before();
-        __syncthreads();
-        fence_after();
     }
-    if (ok && t < nvalid * N) {
+    if (ok && t < nval * N) {
         float2 *dst = a.QGp + ((long)e * a.rsb + rb) * n + (long)(x0 + g) * NN + yl;
 #pragma unroll
         for (int ky = 0; ky < N; ++ky) dst[(long)ky * N] = acc[ky];
     }
-    if (!ok && t == 0) atomicExch(a.err, kErrTimeout);
-    fence_before();
-    __syncthreads();
-    if (t < 32) tmem_dealloc(tb, pow2_cols(2 * NO));
+    tmem_teardown(tb, NCOL, ok, a.err);
 }
 
 // ------------------------------------------------- partial sums of the gain
@@ -418,9 +541,17 @@ __global__ void k_sum_partials(double2 *QG64, const float2 *QGp, int rsb, long n
 }
 
 // ------------------------------------------------------ table preparation
-// T_d[j][j'] = (1/N) sum_l exp(2 pi i l (j - j') / N) phi_d(l), written as split
-// B operands: z (real input) [2N][N]; y, x (complex input) [2N][2N].
-__global__ void k_tmat(float *out, const double2 *phase, int N, int RS)
+__device__ __forceinline__ void put_split(uint8_t *img_hi, uint8_t *img_lo, uint32_t off, double v)
+{
+    const float h = tf32_rna((float)v);
+    *reinterpret_cast<float *>(img_hi + off) = h;
+    *reinterpret_cast<float *>(img_lo + off) = tf32_rna((float)(v - (double)h));
+}
+
+// T_d[j][j'] = (1/N) sum_l exp(2 pi i l (j - j') / N) phi_d(l), written into
+// pre-swizzled B-operand images: z (real input) rows 2j, 2j+1, K = j';
+// y, x (complex input) the real 2x2 block [Re -Im; Im Re] at K = 2j', 2j'+1.
+__global__ void k_timg(uint8_t *out, const double2 *phase, int N, int RS)
 {
     const long total = (long)RS * 2 * 3 * N * N;
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -438,29 +569,23 @@ __global__ void k_tmat(float *out, const double2 *phase, int N, int RS)
     }
     tr /= N;
     ti /= N;
-    const long MSZ = 10L * N * N;
-    float *hi = out + ((long)rs * 2 + side) * 2 * MSZ;
-    float *lo = hi + MSZ;
-    auto put = [&](long idx, double v) {
-        const float h = tf32_rna((float)v);
-        hi[idx] = h;
-        lo[idx] = tf32_rna((float)(v - (double)h));
-    };
-    if (ax == 2) {  // z: real input, [2N][N]
-        put((long)(2 * j) * N + jp, tr);
-        put((long)(2 * j + 1) * N + jp, ti);
+    const int NO = 2 * N;
+    const long IC = img_c(N);
+    uint8_t *hi = out + ((((long)rs * 2 + side) * 3 + ax) * 2 + 0) * IC;
+    uint8_t *lo = hi + IC;
+    if (ax == 2) {
+        put_split(hi, lo, sw128_off(2 * j, 4 * jp, NO), tr);
+        put_split(hi, lo, sw128_off(2 * j + 1, 4 * jp, NO), ti);
     } else {
-        const long off = ax == 1 ? 2L * N * N : 6L * N * N;
-        const int K = 2 * N;
-        put(off + (long)(2 * j) * K + 2 * jp, tr);
-        put(off + (long)(2 * j) * K + 2 * jp + 1, -ti);
-        put(off + (long)(2 * j + 1) * K + 2 * jp, ti);
-        put(off + (long)(2 * j + 1) * K + 2 * jp + 1, tr);
+        put_split(hi, lo, sw128_off(2 * j, 4 * (2 * jp), NO), tr);
+        put_split(hi, lo, sw128_off(2 * j, 4 * (2 * jp + 1), NO), -ti);
+        put_split(hi, lo, sw128_off(2 * j + 1, 4 * (2 * jp), NO), ti);
+        put_split(hi, lo, sw128_off(2 * j + 1, 4 * (2 * jp + 1), NO), tr);
     }
 }
 
-// forward DFT F[k][j] = exp(-2 pi i jk/N) as a split complex-input B operand
-__global__ void k_fmat(float *out, int N)
+// forward DFT F[k][j] = exp(-2 pi i jk/N) as pre-swizzled complex-input images
+__global__ void k_fimg(uint8_t *out, int N)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N * N) return;
@@ -468,17 +593,12 @@ __global__ void k_fmat(float *out, int N)
     double s, c;
     sincospi(2.0 * ((j * k) % N) / N, &s, &c);
     const double fr = c, fi = -s;
-    const int K = 2 * N;
-    float *hi = out, *lo = out + 4 * N * N;
-    auto put = [&](long idx, double v) {
-        const float h = tf32_rna((float)v);
-        hi[idx] = h;
-        lo[idx] = tf32_rna((float)(v - (double)h));
-    };
-    put((long)(2 * k) * K + 2 * j, fr);
-    put((long)(2 * k) * K + 2 * j + 1, -fi);
-    put((long)(2 * k + 1) * K + 2 * j, fi);
-    put((long)(2 * k + 1) * K + 2 * j + 1, fr);
+    const int NO = 2 * N;
+    uint8_t *hi = out, *lo = out + img_c(N);
+    put_split(hi, lo, sw128_off(2 * k, 4 * (2 * j), NO), fr);
+    put_split(hi, lo, sw128_off(2 * k, 4 * (2 * j + 1), NO), -fi);
+    put_split(hi, lo, sw128_off(2 * k + 1, 4 * (2 * j), NO), fi);
+    put_split(hi, lo, sw128_off(2 * k + 1, 4 * (2 * j + 1), NO), fr);
 }
 
 __global__ void k_to_f32(float2 *dst, const double2 *src, long count)
@@ -490,10 +610,21 @@ __global__ void k_to_f32(float2 *dst, const double2 *src, long count)
 unsigned nblk(long total, int t) { return (unsigned)((total + t - 1) / t); }
 
 template <int N>
-size_t stage_smem()
+constexpr size_t smem_a()
 {
-    return 1024 + 2 * (size_t)atoms(2 * N) * kRows * 128 + 2 * (size_t)atoms(2 * N) * (2 * N) * 128;
+    return 1024 + 2 * (size_t)abytes(N) + 4 * (size_t)img_c(N) <= kSmemMax
+               ? 1024 + 2 * (size_t)abytes(N) + 4 * (size_t)img_c(N)
+               : 1024 + 2 * (size_t)abytes(N) + 2 * (size_t)img_c(N);
 }
+template <int N>
+constexpr size_t smem_b()
+{
+    return 1024 + 2 * (size_t)abytes(N) + 6 * (size_t)img_c(N) <= kSmemMax
+               ? 1024 + 2 * (size_t)abytes(N) + 6 * (size_t)img_c(N)
+               : 1024 + 2 * (size_t)abytes(N) + 2 * (size_t)img_c(N);
+}
+template <int N>
+constexpr size_t smem_c() { return 1024 + 2 * (size_t)abytes(N) + 2 * (size_t)img_c(N); }
 
 #define DGFS_TRY(x)                   \
     do {                              \
@@ -529,10 +660,9 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
     a.Bq = Bq;
     a.H = H;
     a.QGp = QGp;
-    a.Fm = ts->Fm;
+    a.Fimg = ts->Fimg;
     a.err = ts->err;
 
-    const size_t smem = stage_smem<N>();
     // FP64 forward transforms of f for the loss term (step 1 of Algorithm 2)
     DGFS_TRY(fp64_forward(plan, P, f, F64, st));
     constexpr int G = kRows / N;
@@ -541,25 +671,26 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
             const PairTables &pt = plan->pairs[p * S + q];
             a.p = p;
             a.q = q;
-            a.tmat = pt.tmat;
+            a.timg = reinterpret_cast<const uint8_t *>(pt.tmat);
             a.b32 = pt.b32;
             a.w = pt.w;
             for (int pt0 = 0; pt0 < P; pt0 += E) {
                 const int Ec = std::min(E, P - pt0);
                 a.pt0 = pt0;
+                a.Ec = Ec;
                 {
                     ProfScope ps(plan, "tc_stage_a", st);
-                    k_stage_a<N><<<dim3((N + G - 1) / G, RS, Ec), kThreads, smem, st>>>(a);
+                    k_stage_a<N><<<dim3(ts->groups_a, RS, 2), kThreads, smem_a<N>(), st>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
                 {
                     ProfScope ps(plan, "tc_stage_b", st);
-                    k_stage_b<N><<<dim3((N * N + kRows - 1) / kRows, RS, Ec), kThreads, smem, st>>>(a);
+                    k_stage_b<N><<<dim3(ts->groups_b, RS), kThreads, smem_b<N>(), st>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
                 {
                     ProfScope ps(plan, "tc_stage_c", st);
-                    k_stage_c<N><<<dim3((N + G - 1) / G, RSB, Ec), kThreads, smem, st>>>(a);
+                    k_stage_c<N><<<dim3((N + G - 1) / G, RSB, Ec), kThreads, smem_c<N>(), st>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
                 {
@@ -577,10 +708,10 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
 template <int N>
 dgfs_status set_smem_attrs()
 {
-    const int smem = (int)stage_smem<N>();
-    DGFS_CUDA(cudaFuncSetAttribute(k_stage_a<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    DGFS_CUDA(cudaFuncSetAttribute(k_stage_b<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    DGFS_CUDA(cudaFuncSetAttribute(k_stage_c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    static_assert(smem_a<N>() <= kSmemMax && smem_b<N>() <= kSmemMax && smem_c<N>() <= kSmemMax, "smem");
+    DGFS_CUDA(cudaFuncSetAttribute(k_stage_a<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a<N>()));
+    DGFS_CUDA(cudaFuncSetAttribute(k_stage_b<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b<N>()));
+    DGFS_CUDA(cudaFuncSetAttribute(k_stage_c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c<N>()));
     return DGFS_OK;
 }
 
@@ -603,22 +734,27 @@ dgfs_status tc_prepare(dgfs_plan_s *plan)
     TcState *ts = new TcState();
     plan->tc = ts;
     ts->nterms = plan->prec == DGFS_TF32 ? 1 : 3;
-    ts->chunk = std::max(1, std::min(plan->max_points, 8));
+    ts->chunk = std::max(1, std::min(plan->max_points, 24));
     ts->rsb = std::min(RS, 8);
-    DGFS_CUDA(cudaMalloc(&ts->Fm, sizeof(float) * 8 * N * N));
-    DGFS_CUDA(cudaMalloc(&ts->tw32, sizeof(float2) * N));
+    // work-item groups: enough CTAs to fill the GPU about twice
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plan->device);
+    ts->groups_a = std::max(1, (2 * sms + 2 * RS - 1) / (2 * RS));
+    ts->groups_b = std::max(1, (2 * sms + RS - 1) / RS);
+    const long IC = img_c(N);
+    DGFS_CUDA(cudaMalloc(&ts->Fimg, 2 * IC));
+    DGFS_CUDA(cudaMemset(ts->Fimg, 0, 2 * IC));
     DGFS_CUDA(cudaMalloc(&ts->err, sizeof(int)));
     DGFS_CUDA(cudaMemset(ts->err, 0, sizeof(int)));
-    k_fmat<<<nblk((long)N * N, 256), 256>>>(ts->Fm, N);
-    DGFS_LAUNCHED(plan);
-    k_to_f32<<<1, 64>>>(ts->tw32, plan->twiddle, N);
+    k_fimg<<<nblk((long)N * N, 256), 256>>>(ts->Fimg, N);
     DGFS_LAUNCHED(plan);
     for (auto &pt : plan->pairs) {
-        DGFS_CUDA(cudaMalloc(&pt.tmat, sizeof(float) * (size_t)RS * 2 * 2 * 10 * N * N));
-        DGFS_CUDA(cudaMemset(pt.tmat, 0, sizeof(float) * (size_t)RS * 2 * 2 * 10 * N * N));
+        const size_t tbytes = (size_t)RS * 2 * 3 * 2 * IC;
+        DGFS_CUDA(cudaMalloc(&pt.tmat, tbytes));
+        DGFS_CUDA(cudaMemset(pt.tmat, 0, tbytes));
         DGFS_CUDA(cudaMalloc(&pt.b32, sizeof(float2) * RS * n));
-        plan->table_bytes += sizeof(float) * (size_t)RS * 40 * N * N + sizeof(float2) * RS * n;
-        k_tmat<<<nblk((long)RS * 6 * N * N, 256), 256>>>(pt.tmat, pt.phase, N, RS);
+        plan->table_bytes += tbytes + sizeof(float2) * RS * n;
+        k_timg<<<nblk((long)RS * 6 * N * N, 256), 256>>>(reinterpret_cast<uint8_t *>(pt.tmat), pt.phase, N, RS);
         DGFS_LAUNCHED(plan);
         k_to_f32<<<nblk(RS * n, 256), 256>>>(pt.b32, pt.b, RS * n);
         DGFS_LAUNCHED(plan);
@@ -638,8 +774,7 @@ void tc_release(dgfs_plan_s *plan)
 {
     TcState *ts = reinterpret_cast<TcState *>(plan->tc);
     if (!ts) return;
-    cudaFree(ts->Fm);
-    cudaFree(ts->tw32);
+    cudaFree(ts->Fimg);
     cudaFree(ts->err);
     delete ts;
     plan->tc = nullptr;
@@ -651,7 +786,8 @@ size_t tc_workspace_bytes(const dgfs_plan_s *plan)
     const long n = (long)plan->N * plan->N * plan->N;
     const long RS = (long)plan->Nrho * plan->M;
     const long E = ts ? ts->chunk : 1, RSB = ts ? ts->rsb : 1;
-    return sizeof(double2) * ((long)plan->max_points * (plan->S + 2) * n) + sizeof(float2) * (3 * E * RS * n + E * RSB * n);
+    return sizeof(double2) * ((long)plan->max_points * (plan->S + 2) * n) +
+           sizeof(float2) * (3 * E * RS * n + E * RSB * n);
 }
 
 dgfs_status tc_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st)

@@ -139,3 +139,27 @@ __device__ __forceinline__ float tf32_rna(float x)
 
 }  // namespace umma
 }  // namespace dgfs
+
+namespace dgfs {
+namespace umma {
+
+// arrive on mbar and add tx_bytes to the transaction count it waits for
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t tx_bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(tx_bytes)
+                 : "memory");
+}
+
+// asynchronous bulk copy global -> shared (16-byte aligned, size a multiple of
+// 16), completion counted on mbar
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+        : "memory");
+}
+
+}  // namespace umma
+}  // namespace dgfs
