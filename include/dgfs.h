@@ -103,6 +103,27 @@ dgfs_status dgfs_collide(dgfs_plan plan, int P, const void *f_dev, void *Q_dev, 
  * written).  Uses the plan's staging buffers; no allocation. */
 dgfs_status dgfs_collide_host(dgfs_plan plan, int P, const void *f_host, void *Q_host, void *stream);
 
+/* Allocation-free variant of dgfs_collide for DGFS_FP64 plans.  The paper has
+ * no counterpart: this entry point exists for callers that may not allocate
+ * device memory while they evaluate (a host framework that owns the device
+ * memory budget, or a latency-critical loop where an allocation and the
+ * synchronisation it can cause are not acceptable).  It computes exactly what
+ * dgfs_collide computes, with the same arguments and layouts, but takes its
+ * scratch from a 32 MiB array built into the library (every GPU that loads the
+ * library holds that array until the process exits) and calls no allocation
+ * routine.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls on a device share the one array: calls that may overlap on the
+ *    GPU (other streams, other host threads) race and must be serialised by the
+ *    caller.  Nothing in the array needs to start at zero.
+ *  - P is bounded by the array: if even one evaluation per pass does not fit,
+ *    the call returns DGFS_EINVAL with the required size in dgfs_last_error().
+ *  - Errors: EINVAL (bad argument, P too large), EUNSUPPORTED (not an FP64
+ *    plan), ECUDA. */
+dgfs_status dgfs_collide_noalloc(dgfs_plan plan, int P, const void *f_dev, void *Q_dev, void *stream);
+
 /* Synchronise the plan's device and report deferred device-side conditions:
  * DGFS_ETIMEOUT if a bounded wait inside a tensor-core kernel expired since
  * the last check (the flag is cleared), DGFS_ECUDA for an asynchronous fault.

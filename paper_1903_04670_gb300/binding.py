@@ -50,6 +50,7 @@ def lib():
             "dgfs_plan_destroy": (i, [_P]),
             "dgfs_collide": (i, [_P, i, _P, _P, _P]),
             "dgfs_collide_host": (i, [_P, i, _P, _P, _P]),
+            "dgfs_collide_noalloc": (i, [_P, i, _P, _P, _P]),
             "dgfs_collide_backward": (i, [_P, i, _P, _P, _P, _P, i, _P]),
             "dgfs_moments": (i, [_P, i, _P, _P, _P]),
             "dgfs_plan_info": (i, [_P, _P]),
@@ -133,6 +134,10 @@ def dgfs_plan_destroy(h):
 
 def dgfs_collide(h, P, f, Q, stream=None):
     _check(lib().dgfs_collide(h, int(P), _ptr(f), _ptr(Q), _stream(stream)), "dgfs_collide")
+
+
+def dgfs_collide_noalloc(h, P, f, Q, stream=None):
+    _check(lib().dgfs_collide_noalloc(h, int(P), _ptr(f), _ptr(Q), _stream(stream)), "dgfs_collide_noalloc")
 
 
 def dgfs_collide_host(h, P, f_host, Q_host, stream=None):

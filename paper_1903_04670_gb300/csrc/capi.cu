@@ -191,6 +191,9 @@ dgfs_status entry_check(dgfs_plan_s *plan)
 }
 
 }  // namespace
+
+dgfs_status plan_entry_check(dgfs_plan_s *plan) { return entry_check(plan); }
+
 }  // namespace dgfs
 
 using namespace dgfs;

@@ -100,6 +100,10 @@ class ProfScope {
 dgfs_status build_tables(dgfs_plan_s *plan);
 // fft64.cu
 size_t fp64_workspace_bytes(const dgfs_plan_s *plan, int chunk);
+size_t fp64_scratch_bytes(const dgfs_plan_s *plan, int Fcap, int chunk);
+dgfs_status fp64_collide_ws(dgfs_plan_s *plan, int P, const void *f, void *Q, void *ws, int Fcap, int chunk,
+                            cudaStream_t st);
+dgfs_status plan_entry_check(dgfs_plan_s *plan);
 dgfs_status fp64_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st);
 dgfs_status fp64_backward(dgfs_plan_s *plan, int P, const void *f, const void *dQ, void *df,
                           double *domega, int domega_on_host, cudaStream_t st);

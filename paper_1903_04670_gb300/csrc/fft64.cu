@@ -257,15 +257,16 @@ dgfs_status launch(dgfs_plan_s *plan, dim3 grid, const PassArgs &a, cudaStream_t
         if (s_ != DGFS_OK) return s_;            \
     } while (0)
 
+// ws: scratch of at least fp64_scratch_bytes(plan, Fcap, E) bytes, laid out as
+// F [Fcap][S][n] | GA [E][RS][n] | GB [E][RS][n] | QG [E][n] | G2 [E][n]; Fcap >= P.
 template <int N>
-dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaStream_t st)
+dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, void *ws, int Fcap, int E,
+                      cudaStream_t st)
 {
     const int S = plan->S, RS = plan->Nrho * plan->M;
     const long n = (long)N * N * N;
-    const int E = plan->chunk;
-    // workspace: F [max_points][S][n] | GA [E][RS][n] | GB [E][RS][n] | QG [E][n] | G2 [E][n]
-    double2 *F = reinterpret_cast<double2 *>(plan->ws);
-    double2 *GA = F + (long)plan->max_points * S * n;
+    double2 *F = reinterpret_cast<double2 *>(ws);
+    double2 *GA = F + (long)Fcap * S * n;
     double2 *GB = GA + (long)E * RS * n;
     double2 *QG = GB + (long)E * RS * n;
     double2 *G2 = QG + (long)E * n;
@@ -408,26 +409,37 @@ __global__ void __launch_bounds__(256) k_moments(const T *Q, double *out, int N,
 
 }  // namespace
 
-size_t fp64_workspace_bytes(const dgfs_plan_s *plan, int chunk)
+size_t fp64_scratch_bytes(const dgfs_plan_s *plan, int Fcap, int chunk)
 {
     const long n = (long)plan->N * plan->N * plan->N;
     const long RS = (long)plan->Nrho * plan->M;
-    return sizeof(double2) * ((long)plan->max_points * plan->S * n + 2L * chunk * RS * n + 2L * chunk * n);
+    return sizeof(double2) * ((long)Fcap * plan->S * n + 2L * chunk * RS * n + 2L * chunk * n);
+}
+
+size_t fp64_workspace_bytes(const dgfs_plan_s *plan, int chunk)
+{
+    return fp64_scratch_bytes(plan, plan->max_points, chunk);
+}
+
+dgfs_status fp64_collide_ws(dgfs_plan_s *plan, int P, const void *f, void *Q, void *ws, int Fcap, int chunk,
+                            cudaStream_t st)
+{
+    switch (plan->N) {
+    case 4: return collide_n<4>(plan, P, f, Q, ws, Fcap, chunk, st);
+    case 6: return collide_n<6>(plan, P, f, Q, ws, Fcap, chunk, st);
+    case 8: return collide_n<8>(plan, P, f, Q, ws, Fcap, chunk, st);
+    case 12: return collide_n<12>(plan, P, f, Q, ws, Fcap, chunk, st);
+    case 16: return collide_n<16>(plan, P, f, Q, ws, Fcap, chunk, st);
+    case 24: return collide_n<24>(plan, P, f, Q, ws, Fcap, chunk, st);
+    case 32: return collide_n<32>(plan, P, f, Q, ws, Fcap, chunk, st);
+    case 48: return collide_n<48>(plan, P, f, Q, ws, Fcap, chunk, st);
+    default: set_error("N not supported by the FP64 path"); return DGFS_EUNSUPPORTED;
+    }
 }
 
 dgfs_status fp64_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st)
 {
-    switch (plan->N) {
-    case 4: return collide_n<4>(plan, P, f, Q, st);
-    case 6: return collide_n<6>(plan, P, f, Q, st);
-    case 8: return collide_n<8>(plan, P, f, Q, st);
-    case 12: return collide_n<12>(plan, P, f, Q, st);
-    case 16: return collide_n<16>(plan, P, f, Q, st);
-    case 24: return collide_n<24>(plan, P, f, Q, st);
-    case 32: return collide_n<32>(plan, P, f, Q, st);
-    case 48: return collide_n<48>(plan, P, f, Q, st);
-    default: set_error("N not supported by the FP64 path"); return DGFS_EUNSUPPORTED;
-    }
+    return fp64_collide_ws(plan, P, f, Q, plan->ws, plan->max_points, plan->chunk, st);
 }
 
 dgfs_status fp64_forward(dgfs_plan_s *plan, int P, const void *f, double2 *F, cudaStream_t st)
