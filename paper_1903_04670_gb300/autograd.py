@@ -1,0 +1,50 @@
+"""torch.autograd wrapper of the collision operator.
+
+Q^(pq)(f_p, f_q) is bilinear in (f_p, f_q) (Eq. 7), so its adjoint is exact:
+the backward pass calls dgfs_collide_backward, which recomputes the per-(rho,
+sigma) translates instead of storing them and also returns dL/d omega_pq
+through beta^(pq)(omega) and the radial weights rho^{gamma+2}, gamma = 2(1 - omega).
+
+The forward may run in any precision form; the backward always runs on an
+FP64 plan built with the same parameters (the tensor-core plans implement the
+forward only), with f promoted to double.  All arithmetic runs in the CUDA
+library; this module only orchestrates calls.
+"""
+import torch
+
+from . import binding as B
+
+
+class CollisionOperator:
+    """Owns a forward plan (any precision) and an FP64 plan for gradients."""
+
+    def __init__(self, N, L, M, N_rho, masses, pairs, precision="fp64", max_points=1, device=0):
+        self.args = (N, L, M, N_rho, list(masses), [dict(p) for p in pairs])
+        self.S = len(masses)
+        self.fwd = B.Plan(N, L, M, N_rho, masses, pairs, precision, max_points, device)
+        self.bwd = self.fwd if precision == "fp64" else B.Plan(N, L, M, N_rho, masses, pairs, "fp64",
+                                                               max_points, device)
+        self.omega = torch.tensor([p["omega"] for p in pairs], dtype=torch.float64,
+                                  device="cuda").view(self.S, self.S)
+
+    def __call__(self, f, omega=None):
+        """Q = collide(f); omega (an [S, S] tensor equal to the plan's values) may be
+        passed with requires_grad to receive dL/d omega."""
+        if omega is None:
+            omega = self.omega
+        return _Collide.apply(f, omega, self)
+
+
+class _Collide(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, f, omega, op):
+        ctx.op = op
+        ctx.save_for_backward(f)
+        return op.fwd.collide(f.contiguous())
+
+    @staticmethod
+    def backward(ctx, dQ):
+        (f,) = ctx.saved_tensors
+        op = ctx.op
+        df, dom = op.bwd.backward(f.contiguous().to(torch.float64), dQ.contiguous().to(torch.float64))
+        return df.to(f.dtype), dom.view(op.S, op.S), None

@@ -445,7 +445,10 @@ dgfs_status fp64_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaS
 dgfs_status fp64_forward(dgfs_plan_s *plan, int P, const void *f, double2 *F, cudaStream_t st)
 {
     switch (plan->N) {
+    case 4: return forward_n<4>(plan, P, f, F, st);
+    case 6: return forward_n<6>(plan, P, f, F, st);
     case 8: return forward_n<8>(plan, P, f, F, st);
+    case 12: return forward_n<12>(plan, P, f, F, st);
     case 16: return forward_n<16>(plan, P, f, F, st);
     case 24: return forward_n<24>(plan, P, f, F, st);
     case 32: return forward_n<32>(plan, P, f, F, st);
@@ -458,7 +461,10 @@ dgfs_status fp64_finish(dgfs_plan_s *plan, int p, int q, int P, double2 *QG, dou
                         const void *f, void *Q, cudaStream_t st)
 {
     switch (plan->N) {
+    case 4: return finish_n<4>(plan, p, q, P, QG, G2, F, f, Q, st);
+    case 6: return finish_n<6>(plan, p, q, P, QG, G2, F, f, Q, st);
     case 8: return finish_n<8>(plan, p, q, P, QG, G2, F, f, Q, st);
+    case 12: return finish_n<12>(plan, p, q, P, QG, G2, F, f, Q, st);
     case 16: return finish_n<16>(plan, p, q, P, QG, G2, F, f, Q, st);
     case 24: return finish_n<24>(plan, p, q, P, QG, G2, F, f, Q, st);
     case 32: return finish_n<32>(plan, p, q, P, QG, G2, F, f, Q, st);
@@ -482,12 +488,4 @@ dgfs_status moments(dgfs_plan_s *plan, int P, const void *Q, double *out, cudaSt
     return DGFS_OK;
 }
 
-}  // namespace dgfs
-
-namespace dgfs {
-dgfs_status fp64_backward(dgfs_plan_s *, int, const void *, const void *, void *, double *, int, cudaStream_t)
-{
-    set_error("adjoint not built");
-    return DGFS_EUNSUPPORTED;
-}
 }  // namespace dgfs

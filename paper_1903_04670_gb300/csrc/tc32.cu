@@ -99,6 +99,19 @@ __device__ __forceinline__ void st_c(uint8_t *ah, uint8_t *al, int row, int k, f
     *reinterpret_cast<float2 *>(al + o) = make_float2(l0, l1);
 }
 
+// store two consecutive split complex values (k even) with one 16-byte access each
+__device__ __forceinline__ void st_c2(uint8_t *ah, uint8_t *al, int row, int k, float2 u, float2 v)
+{
+    float4 h, l;
+    split_tf32(u.x, h.x, l.x);
+    split_tf32(u.y, h.y, l.y);
+    split_tf32(v.x, h.z, l.z);
+    split_tf32(v.y, h.w, l.w);
+    const uint32_t o = sw128_off(row, 8 * k, kRows);
+    *reinterpret_cast<float4 *>(ah + o) = h;
+    *reinterpret_cast<float4 *>(al + o) = l;
+}
+
 __device__ __forceinline__ void st_f4(uint8_t *ah, uint8_t *al, int row, int kb, float4 v)
 {
     float4 h, l;
@@ -354,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_stage_b(TcArgs a)
         const bool valid = p0 + t < NN;
         const long gbase = ((long)e * a.RS + rs) * n + p0 + t;
 #pragma unroll
-        for (int x = 0; x < N; ++x) st_c(Ah, Al, t, x, pa[x].x, pa[x].y);
+        for (int x = 0; x < N; x += 2) st_c2(Ah, Al, t, x, pa[x], pa[x + 1]);
         float2 pb[N];
         load_pencil(pb, a.Bq + gbase, valid);
         if (!RESIDENT) {
@@ -366,7 +379,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_stage_b(TcArgs a)
                      [&] { gemm(tb, Ah, Al, slot(0), slot(0) + IC, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
         if (!ok) break;
 #pragma unroll
-        for (int x = 0; x < N; ++x) st_c(Ah, Al, t, x, pb[x].x, pb[x].y);
+        for (int x = 0; x < N; x += 2) st_c2(Ah, Al, t, x, pb[x], pb[x + 1]);
         const int nx = it + gridDim.x;
         if (nx < items) {
             const int e2 = nx / NT, q0 = (nx % NT) * kRows;
@@ -388,10 +401,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_stage_b(TcArgs a)
             tmem_ld16(tl + c0, va);
             tmem_ld16(tl + NO + c0, vb);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float re = va[2 * j] * vb[2 * j] - va[2 * j + 1] * vb[2 * j + 1];
-                const float im = va[2 * j] * vb[2 * j + 1] + va[2 * j + 1] * vb[2 * j];
-                st_c(Ah, Al, t, c0 / 2 + j, re, im);
+            for (int j = 0; j < 8; j += 2) {
+                const float2 p0 = make_float2(va[2 * j] * vb[2 * j] - va[2 * j + 1] * vb[2 * j + 1],
+                                              va[2 * j] * vb[2 * j + 1] + va[2 * j + 1] * vb[2 * j]);
+                const float2 p1 = make_float2(va[2 * j + 2] * vb[2 * j + 2] - va[2 * j + 3] * vb[2 * j + 3],
+                                              va[2 * j + 2] * vb[2 * j + 3] + va[2 * j + 3] * vb[2 * j + 2]);
+                st_c2(Ah, Al, t, c0 / 2 + j, p0, p1);
             }
         }
         if (!RESIDENT) {
