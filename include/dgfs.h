@@ -36,6 +36,7 @@ extern "C" {
 #endif
 
 typedef struct dgfs_plan_s *dgfs_plan;
+typedef struct dgfs_graph_s *dgfs_graph;
 
 typedef enum {
     DGFS_OK = 0,
@@ -150,7 +151,9 @@ dgfs_status dgfs_moments(dgfs_plan plan, int P, const void *Q_dev, double *out_d
  *  [0] N [1] L [2] M [3] N_rho [4] S [5] precision [6] max_points
  *  [7] workspace bytes [8] table bytes [9] chunk (evaluations per launch)
  *  [10] (r, s) blocks of the accumulation stage (tensor-core plans)
- *  [11] split products per contraction (tensor-core plans) [12..15] reserved. */
+ *  [11] split products per contraction (tensor-core plans)
+ *  [12], [13] CTA groups per (r, s) of the plane and pencil stages (tensor-core plans)
+ *  [14] 1 if dgfs_plan_autotune chose the launch parameters [15] reserved. */
 dgfs_status dgfs_plan_info(dgfs_plan plan, double *info);
 
 /* Copy pair (p, q)'s tables to host FP64 buffers for verification:
@@ -160,6 +163,42 @@ dgfs_status dgfs_plan_info(dgfs_plan plan, double *info);
  * Any output pointer may be NULL.  Synchronous. */
 dgfs_status dgfs_plan_pair_tables(dgfs_plan plan, int p, int q, double *scalars, double *rho,
                                   double *w_rho, double *sigma, double *w_sigma, double *b, double *c);
+
+/* Homogeneous relaxation step f_p += dt sum_q Q^(pq) at every point (the
+ * spatially homogeneous form of Eq. (1) with explicit Euler time stepping, as
+ * in Table 2): f_dev [P][S][n] is updated in place from Q_dev [P][S][S][n].
+ * Element type of the plan.  Errors: EINVAL, ECUDA. */
+dgfs_status dgfs_relax_step(dgfs_plan plan, int P, void *f_dev, const void *Q_dev, double dt, void *stream);
+
+/* Capture a batch of uneven instances into one CUDA graph: `steps` repetitions
+ * of, for each i < count, dgfs_collide(plans[i], P[i], f_dev[i], Q_dev[i]) and,
+ * if dt != 0, dgfs_relax_step(plans[i], P[i], f_dev[i], Q_dev[i], dt).  Plans
+ * may differ in N, S, M, N_rho and precision but must share one device; an
+ * instance's plan must not be used elsewhere while its graph runs (one
+ * workspace per plan).  The buffers are bound at capture time.  Synchronous
+ * capture; *out receives the graph.  Errors: EINVAL, ECUDA and those of the
+ * captured calls. */
+dgfs_status dgfs_graph_capture(int count, const dgfs_plan *plans, const int *P, void *const *f_dev,
+                               void *const *Q_dev, double dt, int steps, dgfs_graph *out);
+
+/* Replay a captured batch on `stream` (asynchronous). */
+dgfs_status dgfs_graph_launch(dgfs_graph graph, void *stream);
+
+/* Number of library kernels one replay of the graph runs. */
+dgfs_status dgfs_graph_kernel_count(dgfs_graph graph, long long *count);
+
+/* Release a graph (synchronises its device).  NULL is accepted. */
+dgfs_status dgfs_graph_destroy(dgfs_graph graph);
+
+/* Autotuner for tensor-core plans: times candidate launch configurations
+ * (points per launch, (r, s) blocks of the accumulation stage, CTA counts of
+ * the plane and pencil stages) with CUDA events on the caller's f_dev / Q_dev
+ * (P points; Q_dev is overwritten) and keeps the fastest; *best_ms (may be
+ * NULL) receives its time per call.  Synchronous.  Errors: EINVAL,
+ * EUNSUPPORTED (FP64 plans have no tunable launch parameters), ECUDA,
+ * ETIMEOUT. */
+dgfs_status dgfs_plan_autotune(dgfs_plan plan, int P, const void *f_dev, void *Q_dev, void *stream,
+                               double *best_ms);
 
 /* Number of the library's kernels launched since the plan was created
  * (host-side counter of launches enqueued by dgfs_* calls on this plan). */

@@ -58,6 +58,12 @@ def lib():
             "dgfs_plan_launch_count": (i, [_P, ctypes.POINTER(ll)]),
             "dgfs_plan_profile": (i, [_P, i]),
             "dgfs_plan_check": (i, [_P]),
+            "dgfs_relax_step": (i, [_P, i, _P, _P, d, _P]),
+            "dgfs_graph_capture": (i, [i, _P, _P, _P, _P, d, i, ctypes.POINTER(_P)]),
+            "dgfs_graph_launch": (i, [_P, _P]),
+            "dgfs_graph_kernel_count": (i, [_P, ctypes.POINTER(ll)]),
+            "dgfs_graph_destroy": (i, [_P]),
+            "dgfs_plan_autotune": (i, [_P, i, _P, _P, _P, ctypes.POINTER(d)]),
             "dgfs_plan_profile_read": (i, [_P, i, _P, _P, _P, ctypes.POINTER(i)]),
             "dgfs_status_string": (ctypes.c_char_p, [i]),
             "dgfs_last_error": (ctypes.c_char_p, []),
@@ -159,7 +165,7 @@ def dgfs_plan_info(h):
     out = (ctypes.c_double * 16)()
     _check(lib().dgfs_plan_info(h, ctypes.cast(out, _P)), "dgfs_plan_info")
     keys = ("N", "L", "M", "N_rho", "S", "precision", "max_points", "workspace_bytes", "table_bytes", "chunk",
-            "rs_blocks", "nterms")
+            "rs_blocks", "nterms", "groups_a", "groups_b", "tuned")
     return {k: out[i] for i, k in enumerate(keys)}
 
 
@@ -182,6 +188,45 @@ def dgfs_plan_launch_count(h):
     v = ctypes.c_longlong(0)
     _check(lib().dgfs_plan_launch_count(h, ctypes.byref(v)), "dgfs_plan_launch_count")
     return int(v.value)
+
+
+def dgfs_relax_step(h, P, f, Q, dt, stream=None):
+    _check(lib().dgfs_relax_step(h, int(P), _ptr(f), _ptr(Q), float(dt), _stream(stream)), "dgfs_relax_step")
+
+
+def dgfs_graph_capture(plans, Ps, fs, Qs, dt=0.0, steps=1):
+    """plans: list of plan handles; fs, Qs: lists of device tensors (bound at capture)."""
+    k = len(plans)
+    ph = (_P * k)(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in plans])
+    pp = (ctypes.c_int * k)(*[int(x) for x in Ps])
+    fp = (_P * k)(*[t.data_ptr() for t in fs])
+    qp = (_P * k)(*[t.data_ptr() for t in Qs])
+    g = _P()
+    _check(lib().dgfs_graph_capture(k, ctypes.cast(ph, _P), ctypes.cast(pp, _P), ctypes.cast(fp, _P),
+                                    ctypes.cast(qp, _P), float(dt), int(steps), ctypes.byref(g)),
+           "dgfs_graph_capture")
+    return g
+
+
+def dgfs_graph_launch(g, stream=None):
+    _check(lib().dgfs_graph_launch(g, _stream(stream)), "dgfs_graph_launch")
+
+
+def dgfs_graph_kernel_count(g):
+    v = ctypes.c_longlong(0)
+    _check(lib().dgfs_graph_kernel_count(g, ctypes.byref(v)), "dgfs_graph_kernel_count")
+    return int(v.value)
+
+
+def dgfs_graph_destroy(g):
+    _check(lib().dgfs_graph_destroy(g), "dgfs_graph_destroy")
+
+
+def dgfs_plan_autotune(h, P, f, Q, stream=None):
+    best = ctypes.c_double(0.0)
+    _check(lib().dgfs_plan_autotune(h, int(P), _ptr(f), _ptr(Q), _stream(stream), ctypes.byref(best)),
+           "dgfs_plan_autotune")
+    return float(best.value)
 
 
 def dgfs_plan_check(h):
@@ -279,6 +324,15 @@ class Plan:
 
     def check(self):
         dgfs_plan_check(self._h)
+
+    def relax_step(self, f, Q, dt, stream=None):
+        dgfs_relax_step(self._h, f.shape[0], f, Q, dt, stream)
+
+    def autotune(self, f, Q=None, stream=None):
+        if Q is None:
+            Q = torch.empty((f.shape[0], self.S, self.S, self.N, self.N, self.N), dtype=self.dtype,
+                            device=f.device)
+        return dgfs_plan_autotune(self._h, f.shape[0], f, Q, stream)
 
     def profile(self, enable=True):
         dgfs_plan_profile(self._h, enable)

@@ -525,6 +525,18 @@ dgfs_status dgfs_plan_profile_read(dgfs_plan plan, int max_classes, char *names,
     return DGFS_OK;
 }
 
+dgfs_status dgfs_plan_autotune(dgfs_plan plan, int P, const void *f_dev, void *Q_dev, void *stream,
+                               double *best_ms)
+{
+    if (!plan || !f_dev || !Q_dev || P < 1 || P > plan->max_points) {
+        set_error("dgfs_plan_autotune: bad plan, pointer or P");
+        return DGFS_EINVAL;
+    }
+    dgfs_status st = entry_check(plan);
+    if (st != DGFS_OK) return st;
+    return tc_autotune(plan, P, f_dev, Q_dev, reinterpret_cast<cudaStream_t>(stream), best_ms);
+}
+
 dgfs_status dgfs_plan_launch_count(dgfs_plan plan, long long *count)
 {
     if (!plan || !count) return DGFS_EINVAL;

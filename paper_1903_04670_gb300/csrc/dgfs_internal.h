@@ -119,5 +119,7 @@ dgfs_status tc_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStr
 size_t tc_workspace_bytes(const dgfs_plan_s *plan);
 dgfs_status tc_check(dgfs_plan_s *plan);
 void tc_info(const dgfs_plan_s *plan, double *info);
+dgfs_status tc_autotune(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st, double *best_ms);
+dgfs_status relax_step(dgfs_plan_s *plan, int P, void *f, const void *Q, double dt, cudaStream_t st);
 
 }  // namespace dgfs

@@ -52,9 +52,11 @@ struct TcState {
     uint8_t *Fimg = nullptr;  // forward DFT as pre-swizzled B-operand images [2 terms][IMGC]
     int *err = nullptr;       // device error flag
     int nterms = 3;
-    int chunk = 8;            // evaluations per launch
-    int rsb = 8;              // (r, s) blocks of stage C
+    int chunk = 8;            // evaluations per launch (<= chunk_max, the workspace's)
+    int rsb = 8;              // (r, s) blocks of stage C (<= rsb_max)
+    int chunk_max = 8, rsb_max = 16;
     int groups_a = 2, groups_b = 4;  // work-item groups per (r, s) in stages A and B
+    int tuned = 0;
 };
 
 struct TcArgs {
@@ -654,14 +656,14 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
     const int S = plan->S, RS = plan->Nrho * plan->M;
     const long n = (long)N * N * N;
     const int E = ts->chunk, RSB = ts->rsb;
-    // workspace: F64 [maxP][S][n] d2 | QG64, G2 [maxP][n] d2 | Ap, Bq, H [E][RS][n] f2 | QGp [E][RSB][n] f2
+    // workspace: F64 [maxP][S][n] d2 | QG64, G2 [maxP][n] d2 | Ap, Bq, H [Emax][RS][n] f2 | QGp [Emax][RSBmax][n] f2
     double2 *F64 = reinterpret_cast<double2 *>(plan->ws);
     double2 *QG64 = F64 + (long)plan->max_points * S * n;
     double2 *G2 = QG64 + (long)plan->max_points * n;
     float2 *Ap = reinterpret_cast<float2 *>(G2 + (long)plan->max_points * n);
-    float2 *Bq = Ap + (long)E * RS * n;
-    float2 *H = Bq + (long)E * RS * n;
-    float2 *QGp = H + (long)E * RS * n;
+    float2 *Bq = Ap + (long)ts->chunk_max * RS * n;
+    float2 *H = Bq + (long)ts->chunk_max * RS * n;
+    float2 *QGp = H + (long)ts->chunk_max * RS * n;
 
     TcArgs a{};
     a.n = n;
@@ -749,7 +751,9 @@ dgfs_status tc_prepare(dgfs_plan_s *plan)
     TcState *ts = new TcState();
     plan->tc = ts;
     ts->nterms = plan->prec == DGFS_TF32 ? 1 : 3;
-    ts->chunk = std::max(1, std::min(plan->max_points, 24));
+    ts->chunk_max = std::max(1, std::min(plan->max_points, 24));
+    ts->chunk = ts->chunk_max;
+    ts->rsb_max = std::min(RS, 16);
     ts->rsb = std::min(RS, 8);
     // work-item groups: enough CTAs to fill the GPU about twice
     int sms = 148;
@@ -800,7 +804,7 @@ size_t tc_workspace_bytes(const dgfs_plan_s *plan)
     const TcState *ts = reinterpret_cast<const TcState *>(plan->tc);
     const long n = (long)plan->N * plan->N * plan->N;
     const long RS = (long)plan->Nrho * plan->M;
-    const long E = ts ? ts->chunk : 1, RSB = ts ? ts->rsb : 1;
+    const long E = ts ? ts->chunk_max : 1, RSB = ts ? ts->rsb_max : 1;
     return sizeof(double2) * ((long)plan->max_points * (plan->S + 2) * n) +
            sizeof(float2) * (3 * E * RS * n + E * RSB * n);
 }
@@ -817,6 +821,74 @@ dgfs_status tc_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStr
     }
 }
 
+// Time candidate launch configurations on the caller's data (each candidate:
+// one untimed call, then the best of two timed calls) and keep the fastest.
+dgfs_status tc_autotune(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st, double *best_ms)
+{
+    TcState *ts = reinterpret_cast<TcState *>(plan->tc);
+    if (!ts) {
+        set_error("dgfs_plan_autotune: only tensor-core plans have launch parameters to tune");
+        return DGFS_EUNSUPPORTED;
+    }
+    const int RS = plan->Nrho * plan->M;
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plan->device);
+    struct Cand { int chunk, rsb, ga, gb; };
+    std::vector<Cand> cands;
+    const int chunks[] = {ts->chunk_max, std::min(ts->chunk_max, 8), std::min(ts->chunk_max, 4)};
+    const int rsbs[] = {std::min(RS, 4), std::min(RS, 8), std::min(RS, 16)};
+    const int waves[] = {1, 2, 4};
+    for (int c : chunks)
+        for (int r : rsbs)
+            for (int w : waves) {
+                const Cand k{c, std::min(r, ts->rsb_max), std::max(1, (w * sms + 2 * RS - 1) / (2 * RS)),
+                             std::max(1, (w * sms + RS - 1) / RS)};
+                bool dup = false;
+                for (auto &o : cands) dup |= o.chunk == k.chunk && o.rsb == k.rsb && o.ga == k.ga && o.gb == k.gb;
+                if (!dup) cands.push_back(k);
+            }
+    cudaEvent_t e0, e1;
+    DGFS_CUDA(cudaEventCreate(&e0));
+    DGFS_CUDA(cudaEventCreate(&e1));
+    const TcState saved = *ts;
+    double best = 1e300;
+    TcState bestcfg = saved;
+    dgfs_status status = DGFS_OK;
+    for (const Cand &k : cands) {
+        ts->chunk = k.chunk;
+        ts->rsb = k.rsb;
+        ts->groups_a = k.ga;
+        ts->groups_b = k.gb;
+        status = tc_collide(plan, P, f, Q, st);
+        if (status != DGFS_OK) break;
+        double t = 1e300;
+        for (int rep = 0; rep < 2 && status == DGFS_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            status = tc_collide(plan, P, f, Q, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) status = cuda_status(cudaGetLastError(), "autotune");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t = std::min(t, (double)ms);
+        }
+        if (status != DGFS_OK) break;
+        if (t < best) {
+            best = t;
+            bestcfg = *ts;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status != DGFS_OK) {
+        *ts = saved;
+        return status;
+    }
+    *ts = bestcfg;
+    ts->tuned = 1;
+    if (best_ms) *best_ms = best;
+    return tc_check(plan);
+}
+
 void tc_info(const dgfs_plan_s *plan, double *info)
 {
     const TcState *ts = reinterpret_cast<const TcState *>(plan->tc);
@@ -824,6 +896,9 @@ void tc_info(const dgfs_plan_s *plan, double *info)
     info[9] = ts->chunk;
     info[10] = ts->rsb;
     info[11] = ts->nterms;
+    info[12] = ts->groups_a;
+    info[13] = ts->groups_b;
+    info[14] = ts->tuned;
 }
 
 dgfs_status tc_check(dgfs_plan_s *plan)
