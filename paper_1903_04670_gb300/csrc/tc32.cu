@@ -43,7 +43,6 @@ namespace {
 using namespace umma;
 
 constexpr int kRows = 128;             // MMA M: data rows per CTA
-constexpr int kThreads = 128;          // one thread per data row / TMEM lane
 constexpr long kWaitLimit = 1L << 22;  // mbarrier polls before declaring a timeout
 constexpr int kErrTimeout = 1;
 constexpr int kSmemMax = 227 * 1024;
@@ -144,32 +143,57 @@ __device__ __forceinline__ void gemm(uint32_t d, const uint8_t *ah, const uint8_
     }
 }
 
-// Block-wide: thread 0 issues `issue()`, commits to mbar; all threads wait.
-// Returns false (for every thread) if the wait expired.
+// Named barrier of one 128-thread pipeline: id 1 + pipeline (id 0 is __syncthreads).
+__device__ __forceinline__ void pbar(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+
+// AND-vote over one pipeline's 128 threads (also a barrier).
+__device__ __forceinline__ bool pbar_and(int id, bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, %2, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)(v ? 1 : 0)), "r"(id)
+        : "memory");
+    return r != 0;
+}
+
+// One pipeline: its thread 0 issues `issue()` and commits to mbar; the
+// pipeline's threads wait.  Returns false (for every thread of the pipeline)
+// if the wait expired.
 template <typename F>
-__device__ __forceinline__ bool run_mma(uint64_t *mbar, uint32_t &phase, F issue)
+__device__ __forceinline__ bool run_mma(uint64_t *mbar, uint32_t &phase, int bar_id, F issue)
 {
     fence_proxy_async();
     fence_before();
-    __syncthreads();
+    pbar(bar_id);
     fence_after();
-    if (threadIdx.x == 0) {
+    if ((threadIdx.x & (kRows - 1)) == 0) {
         issue();
         commit(mbar);
     }
     const bool ok = mbar_wait(mbar, phase, kWaitLimit);
     phase ^= 1u;
-    const int all = __syncthreads_and(ok ? 1 : 0);
+    const bool all = pbar_and(bar_id, ok);
     fence_after();
-    return all != 0;
+    return all;
 }
 
-// Block-wide bounded wait for a bulk-copy phase.
-__device__ __forceinline__ bool wait_copy(uint64_t *mbar, uint32_t &phase)
+// Whole-CTA bounded wait for a bulk-copy phase.
+__device__ __forceinline__ bool wait_copy_cta(uint64_t *mbar, uint32_t &phase)
 {
     const bool ok = mbar_wait(mbar, phase, kWaitLimit);
     phase ^= 1u;
     return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
+// One pipeline's bounded wait for a bulk-copy phase.
+__device__ __forceinline__ bool wait_copy_pipe(uint64_t *mbar, uint32_t &phase, int bar_id)
+{
+    const bool ok = mbar_wait(mbar, phase, kWaitLimit);
+    phase ^= 1u;
+    return pbar_and(bar_id, ok);
 }
 
 __device__ __forceinline__ uint32_t lane_base(uint32_t tbase)
@@ -182,73 +206,78 @@ __device__ __forceinline__ const uint8_t *timg_at(const uint8_t *timg, int N, in
     return timg + ((((long)rs * 2 + side) * 3 + ax) * 2 + term) * (long)img_c(N);
 }
 
-__device__ __forceinline__ void tmem_setup(uint32_t *slot, uint32_t ncols, uint64_t *m0, uint64_t *m1)
+// Allocate ncols TMEM columns for the CTA and initialise `nb` mbarriers.
+__device__ __forceinline__ void cta_setup(uint32_t *slot, uint32_t ncols, uint64_t *mb, int nb)
 {
     if (threadIdx.x < 32) tmem_alloc(slot, ncols);
-    if (threadIdx.x == 0) {
-        mbar_init(m0, 1);
-        mbar_init(m1, 1);
-    }
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nb; ++i) mbar_init(mb + i, 1);
     fence_before();
     __syncthreads();
     fence_after();
 }
 
-__device__ __forceinline__ void tmem_teardown(uint32_t tb, uint32_t ncols, bool ok, int *err)
+__device__ __forceinline__ void cta_teardown(uint32_t tb, uint32_t ncols, bool ok, int *err)
 {
-    if (!ok && threadIdx.x == 0) atomicExch(err, kErrTimeout);
+    if (!ok) atomicExch(err, kErrTimeout);
     fence_before();
     __syncthreads();
     if (threadIdx.x < 32) tmem_dealloc(tb, ncols);
 }
 
+// Pipelines per CTA: each pipeline is 128 threads with its own data operand
+// (hi, lo), TMEM columns, mbarrier and named barrier; the matrix images are
+// shared.  Chosen so that shared memory, TMEM (512 columns) and registers fit.
+template <int N> struct NPipes {
+    static constexpr int A = N <= 16 ? 4 : (N <= 32 ? 2 : 1);
+    static constexpr int B = N <= 16 ? 4 : (N <= 32 ? 2 : 1);
+    static constexpr int C = N <= 8 ? 4 : (N <= 32 ? 2 : 1);
+};
+
 // ------------------------------------------------------------------ stage A
-// grid (groups, RS, 2 sides).  A CTA holds T_z, T_y of its (r, s, side) and
-// loops over items (point e, group of G x-planes): z-pass (real input), an
-// in-plane transpose through shared memory, y-pass, result A' or B' to global.
+// grid (groups, RS, 2 sides).  A CTA holds T_z, T_y of its (r, s, side); each of
+// its NP pipelines loops over items (point e, group of G x-planes): z-pass
+// (real input), an in-plane transpose through shared memory, y-pass, result A'
+// or B' to global.
 template <int N>
-__global__ void __launch_bounds__(kThreads, 1) k_stage_a(TcArgs a)
+__global__ void __launch_bounds__(kRows *NPipes<N>::A, 1) k_stage_a(TcArgs a)
 {
+    constexpr int NP = NPipes<N>::A;
     constexpr int G = kRows / N, KR = N, KC = 2 * N, NO = 2 * N, NG = (N + G - 1) / G;
     constexpr int AB = abytes(N), IR = img_r(N), IC = img_c(N);
-    constexpr bool RESIDENT = 1024 + 2 * AB + 4 * IC <= kSmemMax;
+    constexpr bool RESIDENT = NP > 1 || 1024 + 2 * AB + 2 * IR + 2 * IC <= kSmemMax;
     constexpr int NN = N * N;
-    constexpr int FPT = (G * NN / 4 + kThreads - 1) / kThreads;  // float4 per thread for one group
-    constexpr uint32_t NCOL = pow2_cols(2 * NO);
+    constexpr int FPT = (G * NN / 4 + kRows - 1) / kRows;  // float4 per thread for one group
+    constexpr uint32_t NCOL = pow2_cols(NP * 2 * NO);
+    static_assert(1024 + NP * 2 * AB + (RESIDENT ? 2 * IR + 2 * IC : 2 * IC) <= kSmemMax, "smem");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align1024(smem_raw);
-    uint8_t *Ah = sm, *Al = Ah + AB;
-    uint8_t *Bzh = Al + AB, *Bzl = Bzh + IC;
-    uint8_t *Byh = RESIDENT ? Bzl + IC : Bzh, *Byl = Byh + IC;  // non-resident: one reloaded slot
-    __shared__ uint64_t mb_mma, mb_cp;
+    const int pp = threadIdx.x / kRows, t = threadIdx.x % kRows, bar = 1 + pp;
+    uint8_t *Bzh = sm, *Bzl = Bzh + IR;
+    uint8_t *Byh = RESIDENT ? Bzl + IR : Bzh, *Byl = Byh + IC;
+    uint8_t *Ah = Byl + IC + pp * 2 * AB, *Al = Ah + AB;
+    __shared__ uint64_t mb[NP + 1];  // [0, NP): MMA per pipeline, NP: copies
     __shared__ uint32_t tslot;
-    const int t = threadIdx.x, rs = blockIdx.y, side = blockIdx.z;
+    const int rs = blockIdx.y, side = blockIdx.z;
     const long n = a.n;
     const int items = a.Ec * NG;
-    tmem_setup(&tslot, NCOL, &mb_mma, &mb_cp);
-    const uint32_t tb = tslot, tl = lane_base(tb);
+    cta_setup(&tslot, NCOL, mb, NP + 1);
+    const uint32_t tb = tslot + pp * 2 * NO, tl = lane_base(tb);
     uint32_t ph_mma = 0, ph_cp = 0;
-    auto load_z = [&] {
-        if (t == 0) {
-            mbar_expect_tx(&mb_cp, 2 * IR);
-            bulk_g2s(Bzh, timg_at(a.timg, N, rs, side, 2, 0), IR, &mb_cp);
-            bulk_g2s(Bzl, timg_at(a.timg, N, rs, side, 2, 1), IR, &mb_cp);
+    auto load_imgs = [&](int which) {  // 0: z, 1: y, 2: both
+        if (threadIdx.x == 0) {
+            const uint32_t bytes = which == 0 ? 2 * IR : which == 1 ? 2 * IC : 2 * IR + 2 * IC;
+            mbar_expect_tx(&mb[NP], bytes);
+            if (which != 1) {
+                bulk_g2s(Bzh, timg_at(a.timg, N, rs, side, 2, 0), IR, &mb[NP]);
+                bulk_g2s(Bzl, timg_at(a.timg, N, rs, side, 2, 1), IR, &mb[NP]);
+            }
+            if (which != 0) {
+                bulk_g2s(Byh, timg_at(a.timg, N, rs, side, 1, 0), IC, &mb[NP]);
+                bulk_g2s(Byl, timg_at(a.timg, N, rs, side, 1, 1), IC, &mb[NP]);
+            }
         }
     };
-    auto load_y = [&] {
-        if (t == 0) {
-            mbar_expect_tx(&mb_cp, 2 * IC);
-            bulk_g2s(Byh, timg_at(a.timg, N, rs, side, 1, 0), IC, &mb_cp);
-            bulk_g2s(Byl, timg_at(a.timg, N, rs, side, 1, 1), IC, &mb_cp);
-        }
-    };
-    if (RESIDENT && t == 0) {
-        mbar_expect_tx(&mb_cp, 2 * IR + 2 * IC);
-        bulk_g2s(Bzh, timg_at(a.timg, N, rs, side, 2, 0), IR, &mb_cp);
-        bulk_g2s(Bzl, timg_at(a.timg, N, rs, side, 2, 1), IR, &mb_cp);
-        bulk_g2s(Byh, timg_at(a.timg, N, rs, side, 1, 0), IC, &mb_cp);
-        bulk_g2s(Byl, timg_at(a.timg, N, rs, side, 1, 1), IC, &mb_cp);
-    }
     const int sp = side == 0 ? a.p : a.q;
     const int g = t / N, yl = t % N;
     float4 pf[FPT];
@@ -258,28 +287,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_stage_a(TcArgs a)
             reinterpret_cast<const float4 *>(a.f + ((long)(a.pt0 + e) * a.S + sp) * n + (long)x0 * NN);
 #pragma unroll
         for (int j = 0; j < FPT; ++j) {
-            const int i = t + kThreads * j;
+            const int i = t + kRows * j;
             pf[j] = (4 * i < nval * NN) ? fs[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     };
-    int it = blockIdx.x;
+    const int stride = gridDim.x * NP;
+    int it = blockIdx.x * NP + pp;
     if (it < items) prefetch(it);
     bool ok = true;
-    if (RESIDENT) ok = wait_copy(&mb_cp, ph_cp);
-    for (; it < items && ok; it += gridDim.x) {
+    if (RESIDENT) {
+        load_imgs(2);
+        ok = wait_copy_cta(&mb[NP], ph_cp);
+    }
+    for (; it < items && ok; it += stride) {
         const int e = it / NG, x0 = (it % NG) * G, nval = min(G, N - x0);
 #pragma unroll
         for (int j = 0; j < FPT; ++j) {
-            const int i = t + kThreads * j;
+            const int i = t + kRows * j;
             if (4 * i < nval * NN) st_f4(Ah, Al, (4 * i) / N, ((4 * i) % N) * 4, pf[j]);
         }
-        if (it + (int)gridDim.x < items) prefetch(it + gridDim.x);
+        if (it + stride < items) prefetch(it + stride);
         if (!RESIDENT) {
-            load_z();
-            ok = wait_copy(&mb_cp, ph_cp);
+            load_imgs(0);
+            ok = wait_copy_pipe(&mb[NP], ph_cp, bar);
             if (!ok) break;
         }
-        ok = run_mma(&mb_mma, ph_mma, [&] { gemm(tb, Ah, Al, Bzh, Bzl, NO, KR * 4, a.nterms, idesc_tf32(kRows, NO)); });
+        ok = run_mma(&mb[pp], ph_mma, bar,
+                     [&] { gemm(tb, Ah, Al, Bzh, Bzl, NO, KR * 4, a.nterms, idesc_tf32(kRows, NO)); });
         if (!ok) break;
         // transpose within each plane: row (g, y) holds z' -> rows (g, z'), K = y
 #pragma unroll
@@ -292,11 +326,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_stage_a(TcArgs a)
             }
         }
         if (!RESIDENT) {
-            load_y();
-            ok = wait_copy(&mb_cp, ph_cp);
+            load_imgs(1);
+            ok = wait_copy_pipe(&mb[NP], ph_cp, bar);
             if (!ok) break;
         }
-        ok = run_mma(&mb_mma, ph_mma,
+        ok = run_mma(&mb[pp], ph_mma, bar,
                      [&] { gemm(tb + NO, Ah, Al, Byh, Byl, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
         if (!ok) break;
         // row t = (g, z'): y' values -> global [x][y'][z']
@@ -311,60 +345,66 @@ __global__ void __launch_bounds__(kThreads, 1) k_stage_a(TcArgs a)
             }
         }
     }
-    tmem_teardown(tb, NCOL, ok, a.err);
+    cta_teardown(tslot, NCOL, ok, a.err);
 }
 
 // ------------------------------------------------------------------ stage B
 // grid (groups, RS).  A CTA holds T^p_x, T^q_x and F of its (r, s) when they
-// fit next to the data operand (else it reloads one image slot per
-// contraction) and loops over items (point e, tile of 128 (y, z) pencils):
-// H = F_x ((T^p_x A') . (T^q_x B')).
+// fit next to the data operands (else it reloads one image slot per
+// contraction); each of its NP pipelines loops over items (point e, tile of
+// 128 (y, z) pencils): H = F_x ((T^p_x A') . (T^q_x B')).
 template <int N>
-__global__ void __launch_bounds__(kThreads, 1) k_stage_b(TcArgs a)
+__global__ void __launch_bounds__(kRows *NPipes<N>::B, 1) k_stage_b(TcArgs a)
 {
+    constexpr int NP = NPipes<N>::B;
     constexpr int KC = 2 * N, NO = 2 * N, NN = N * N, NT = (NN + kRows - 1) / kRows;
     constexpr int AB = abytes(N), IC = img_c(N);
-    constexpr bool RESIDENT = 1024 + 2 * AB + 6 * IC <= kSmemMax;
-    constexpr uint32_t NCOL = pow2_cols(3 * NO);
+    constexpr bool RESIDENT = NP > 1 || 1024 + 2 * AB + 6 * IC <= kSmemMax;
+    constexpr uint32_t NCOL = pow2_cols(NP * 3 * NO);
+    static_assert(1024 + NP * 2 * AB + (RESIDENT ? 6 : 2) * IC <= kSmemMax, "smem");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align1024(smem_raw);
-    uint8_t *Ah = sm, *Al = Ah + AB;
-    uint8_t *B0 = Al + AB;  // image slots: [Txp hi, lo][Txq hi, lo][F hi, lo] or one [hi, lo]
-    __shared__ uint64_t mb_mma, mb_cp;
+    const int pp = threadIdx.x / kRows, t = threadIdx.x % kRows, bar = 1 + pp;
+    uint8_t *B0 = sm;  // image slots: [Txp hi, lo][Txq hi, lo][F hi, lo] or one [hi, lo]
+    uint8_t *Ah = B0 + (RESIDENT ? 6 : 2) * IC + pp * 2 * AB, *Al = Ah + AB;
+    __shared__ uint64_t mb[NP + 1];
     __shared__ uint32_t tslot;
-    const int t = threadIdx.x, rs = blockIdx.y;
+    const int rs = blockIdx.y;
     const long n = a.n;
     const int items = a.Ec * NT;
-    tmem_setup(&tslot, NCOL, &mb_mma, &mb_cp);
-    const uint32_t tb = tslot, tl = lane_base(tb);
+    cta_setup(&tslot, NCOL, mb, NP + 1);
+    const uint32_t tb = tslot + pp * 3 * NO, tl = lane_base(tb);
     uint32_t ph_mma = 0, ph_cp = 0;
     auto src_img = [&](int which, int term) -> const uint8_t * {
         return which < 2 ? timg_at(a.timg, N, rs, which, 0, term) : a.Fimg + (long)term * IC;
     };
     auto slot = [&](int which) -> uint8_t * { return RESIDENT ? B0 + 2 * which * IC : B0; };
     auto load_images = [&](int first, int count) {
-        if (t == 0) {
-            mbar_expect_tx(&mb_cp, 2 * IC * count);
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(&mb[NP], 2 * IC * count);
             for (int w = first; w < first + count; ++w) {
-                bulk_g2s(slot(w), src_img(w, 0), IC, &mb_cp);
-                bulk_g2s(slot(w) + IC, src_img(w, 1), IC, &mb_cp);
+                bulk_g2s(slot(w), src_img(w, 0), IC, &mb[NP]);
+                bulk_g2s(slot(w) + IC, src_img(w, 1), IC, &mb[NP]);
             }
         }
     };
-    if (RESIDENT) load_images(0, 3);
     float2 pa[N];
     auto load_pencil = [&](float2 *dst, const float2 *src, bool valid) {
 #pragma unroll
         for (int x = 0; x < N; ++x) dst[x] = valid ? src[(long)x * NN] : make_float2(0.f, 0.f);
     };
-    int it = blockIdx.x;
+    const int stride = gridDim.x * NP;
+    int it = blockIdx.x * NP + pp;
     if (it < items) {
         const int e = it / NT, p0 = (it % NT) * kRows;
         load_pencil(pa, a.Ap + ((long)e * a.RS + rs) * n + p0 + t, p0 + t < NN);
     }
     bool ok = true;
-    if (RESIDENT) ok = wait_copy(&mb_cp, ph_cp);
-    for (; it < items && ok; it += gridDim.x) {
+    if (RESIDENT) {
+        load_images(0, 3);
+        ok = wait_copy_cta(&mb[NP], ph_cp);
+    }
+    for (; it < items && ok; it += stride) {
         const int e = it / NT, p0 = (it % NT) * kRows;
         const bool valid = p0 + t < NN;
         const long gbase = ((long)e * a.RS + rs) * n + p0 + t;
@@ -374,25 +414,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_stage_b(TcArgs a)
         load_pencil(pb, a.Bq + gbase, valid);
         if (!RESIDENT) {
             load_images(0, 1);
-            ok = wait_copy(&mb_cp, ph_cp);
+            ok = wait_copy_pipe(&mb[NP], ph_cp, bar);
             if (!ok) break;
         }
-        ok = run_mma(&mb_mma, ph_mma,
+        ok = run_mma(&mb[pp], ph_mma, bar,
                      [&] { gemm(tb, Ah, Al, slot(0), slot(0) + IC, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
         if (!ok) break;
 #pragma unroll
         for (int x = 0; x < N; x += 2) st_c2(Ah, Al, t, x, pb[x], pb[x + 1]);
-        const int nx = it + gridDim.x;
+        const int nx = it + stride;
         if (nx < items) {
             const int e2 = nx / NT, q0 = (nx % NT) * kRows;
             load_pencil(pa, a.Ap + ((long)e2 * a.RS + rs) * n + q0 + t, q0 + t < NN);
         }
         if (!RESIDENT) {
             load_images(1, 1);
-            ok = wait_copy(&mb_cp, ph_cp);
+            ok = wait_copy_pipe(&mb[NP], ph_cp, bar);
             if (!ok) break;
         }
-        ok = run_mma(&mb_mma, ph_mma, [&] {
+        ok = run_mma(&mb[pp], ph_mma, bar, [&] {
             gemm(tb + NO, Ah, Al, slot(1), slot(1) + IC, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO));
         });
         if (!ok) break;
@@ -404,19 +444,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_stage_b(TcArgs a)
             tmem_ld16(tl + NO + c0, vb);
 #pragma unroll
             for (int j = 0; j < 8; j += 2) {
-                const float2 p0 = make_float2(va[2 * j] * vb[2 * j] - va[2 * j + 1] * vb[2 * j + 1],
-                                              va[2 * j] * vb[2 * j + 1] + va[2 * j + 1] * vb[2 * j]);
-                const float2 p1 = make_float2(va[2 * j + 2] * vb[2 * j + 2] - va[2 * j + 3] * vb[2 * j + 3],
-                                              va[2 * j + 2] * vb[2 * j + 3] + va[2 * j + 3] * vb[2 * j + 2]);
-                st_c2(Ah, Al, t, c0 / 2 + j, p0, p1);
+                const float2 p0v = make_float2(va[2 * j] * vb[2 * j] - va[2 * j + 1] * vb[2 * j + 1],
+                                               va[2 * j] * vb[2 * j + 1] + va[2 * j + 1] * vb[2 * j]);
+                const float2 p1v = make_float2(va[2 * j + 2] * vb[2 * j + 2] - va[2 * j + 3] * vb[2 * j + 3],
+                                               va[2 * j + 2] * vb[2 * j + 3] + va[2 * j + 3] * vb[2 * j + 2]);
+                st_c2(Ah, Al, t, c0 / 2 + j, p0v, p1v);
             }
         }
         if (!RESIDENT) {
             load_images(2, 1);
-            ok = wait_copy(&mb_cp, ph_cp);
+            ok = wait_copy_pipe(&mb[NP], ph_cp, bar);
             if (!ok) break;
         }
-        ok = run_mma(&mb_mma, ph_mma, [&] {
+        ok = run_mma(&mb[pp], ph_mma, bar, [&] {
             gemm(tb + 2 * NO, Ah, Al, slot(2), slot(2) + IC, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO));
         });
         if (!ok) break;
@@ -431,43 +471,47 @@ __global__ void __launch_bounds__(kThreads, 1) k_stage_b(TcArgs a)
             }
         }
     }
-    tmem_teardown(tb, NCOL, ok, a.err);
+    cta_teardown(tslot, NCOL, ok, a.err);
 }
 
 // ------------------------------------------------------------------ stage C
-// grid (plane groups, RSB, Ec).  For every (r, s) of its block:
-// t3 = F_y F_z H on the tensor cores, QG_part += w_rs b_rs . t3 in registers;
-// the next (r, s)'s H tile is prefetched into registers meanwhile.
+// grid (plane groups, ceil(RSB / NP), Ec).  Each pipeline owns one block of
+// (r, s) and, for every (r, s) of it, computes t3 = F_y F_z H on the tensor
+// cores and QG_part += w_rs b_rs . t3 in registers; the next (r, s)'s H tile
+// is prefetched into registers meanwhile.
 template <int N>
-__global__ void __launch_bounds__(kThreads, 1) k_stage_c(TcArgs a)
+__global__ void __launch_bounds__(kRows *NPipes<N>::C, 1) k_stage_c(TcArgs a)
 {
+    constexpr int NP = NPipes<N>::C;
     constexpr int G = kRows / N, KC = 2 * N, NO = 2 * N, NN = N * N;
     constexpr int AB = abytes(N), IC = img_c(N);
-    constexpr int HPT = (G * NN / 2 + kThreads - 1) / kThreads;  // float4 (2 complex) per thread per tile
+    constexpr int HPT = (G * NN / 2 + kRows - 1) / kRows;  // float4 (2 complex) per thread per tile
     constexpr bool PREFETCH = N <= 32;
-    constexpr uint32_t NCOL = pow2_cols(2 * NO);
+    constexpr uint32_t NCOL = pow2_cols(NP * 2 * NO);
+    static_assert(1024 + NP * 2 * AB + 2 * IC <= kSmemMax, "smem");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align1024(smem_raw);
-    uint8_t *Ah = sm, *Al = Ah + AB, *Bh = Al + AB, *Bl = Bh + IC;
-    __shared__ uint64_t mb_mma, mb_cp;
+    const int pp = threadIdx.x / kRows, t = threadIdx.x % kRows, bar = 1 + pp;
+    uint8_t *Bh = sm, *Bl = Bh + IC;
+    uint8_t *Ah = Bl + IC + pp * 2 * AB, *Al = Ah + AB;
+    __shared__ uint64_t mb[NP + 1];
     __shared__ uint32_t tslot;
-    const int t = threadIdx.x;
-    const int x0 = blockIdx.x * G, rb = blockIdx.y, e = blockIdx.z;
+    const int x0 = blockIdx.x * G, rb = blockIdx.y * NP + pp, e = blockIdx.z;
     const int nval = min(G, N - x0);
     const long n = a.n;
-    tmem_setup(&tslot, NCOL, &mb_mma, &mb_cp);
-    const uint32_t tb = tslot, tl = lane_base(tb);
+    cta_setup(&tslot, NCOL, mb, NP + 1);
+    const uint32_t tb = tslot + pp * 2 * NO, tl = lane_base(tb);
     uint32_t ph_mma = 0, ph_cp = 0;
-    if (t == 0) {
-        mbar_expect_tx(&mb_cp, 2 * IC);
-        bulk_g2s(Bh, a.Fimg, IC, &mb_cp);
-        bulk_g2s(Bl, a.Fimg + IC, IC, &mb_cp);
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&mb[NP], 2 * IC);
+        bulk_g2s(Bh, a.Fimg, IC, &mb[NP]);
+        bulk_g2s(Bl, a.Fimg + IC, IC, &mb[NP]);
     }
     const int g = t / N, yl = t % N;
     float2 acc[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) acc[k] = make_float2(0.f, 0.f);
-    const int rs0 = rb * a.rs_per_block, rs1 = min(a.RS, rs0 + a.rs_per_block);
+    const int rs0 = rb * a.rs_per_block, rs1 = rb < a.rsb ? min(a.RS, rs0 + a.rs_per_block) : rs0;
     float4 hp[PREFETCH ? HPT : 1];
     auto tile = [&](int rs) {
         return reinterpret_cast<const float4 *>(a.H + ((long)e * a.RS + rs) * n + (long)x0 * NN);
@@ -476,32 +520,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_stage_c(TcArgs a)
         const float4 *src = tile(rs0);
 #pragma unroll
         for (int j = 0; j < HPT; ++j) {
-            const int i = t + kThreads * j;
+            const int i = t + kRows * j;
             hp[j] = (2 * i < nval * NN) ? src[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
-    bool ok = wait_copy(&mb_cp, ph_cp);
+    bool ok = wait_copy_cta(&mb[NP], ph_cp);
     for (int rs = rs0; rs < rs1 && ok; ++rs) {
         // rows (g, y), K = z (complex): contiguous planes
         if constexpr (PREFETCH) {
 #pragma unroll
             for (int j = 0; j < HPT; ++j) {
-                const int i = t + kThreads * j;
+                const int i = t + kRows * j;
                 if (2 * i < nval * NN) st_f4(Ah, Al, (2 * i) / N, ((2 * i) % N) * 8, hp[j]);
             }
             if (rs + 1 < rs1) {
                 const float4 *src = tile(rs + 1);
 #pragma unroll
                 for (int j = 0; j < HPT; ++j) {
-                    const int i = t + kThreads * j;
+                    const int i = t + kRows * j;
                     hp[j] = (2 * i < nval * NN) ? src[i] : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
         } else {
             const float4 *src = tile(rs);
-            for (int i = t; i < nval * NN / 2; i += kThreads) st_f4(Ah, Al, (2 * i) / N, ((2 * i) % N) * 8, src[i]);
+            for (int i = t; i < nval * NN / 2; i += kRows) st_f4(Ah, Al, (2 * i) / N, ((2 * i) % N) * 8, src[i]);
         }
-        ok = run_mma(&mb_mma, ph_mma, [&] { gemm(tb, Ah, Al, Bh, Bl, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
+        ok = run_mma(&mb[pp], ph_mma, bar,
+                     [&] { gemm(tb, Ah, Al, Bh, Bl, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
         if (!ok) break;
 #pragma unroll
         for (int c0 = 0; c0 < NO; c0 += 16) {
@@ -512,7 +557,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_stage_c(TcArgs a)
                 for (int j = 0; j < 8; ++j) st_c(Ah, Al, g * N + c0 / 2 + j, yl, v[2 * j], v[2 * j + 1]);
             }
         }
-        ok = run_mma(&mb_mma, ph_mma, [&] { gemm(tb + NO, Ah, Al, Bh, Bl, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
+        ok = run_mma(&mb[pp], ph_mma, bar,
+                     [&] { gemm(tb + NO, Ah, Al, Bh, Bl, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
         if (!ok) break;
         // row t = (g, kz): t3(kx0+g, ky, kz) for all ky
         const float wr = (float)a.w[rs];
@@ -533,12 +579,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_stage_c(TcArgs a)
             }
         }
     }
-    if (ok && t < nval * N) {
+    if (ok && rb < a.rsb && t < nval * N) {
         float2 *dst = a.QGp + ((long)e * a.rsb + rb) * n + (long)(x0 + g) * NN + yl;
 #pragma unroll
         for (int ky = 0; ky < N; ++ky) dst[(long)ky * N] = acc[ky];
     }
-    tmem_teardown(tb, NCOL, ok, a.err);
+    cta_teardown(tslot, NCOL, ok, a.err);
 }
 
 // ------------------------------------------------- partial sums of the gain
@@ -629,19 +675,19 @@ unsigned nblk(long total, int t) { return (unsigned)((total + t - 1) / t); }
 template <int N>
 constexpr size_t smem_a()
 {
-    return 1024 + 2 * (size_t)abytes(N) + 4 * (size_t)img_c(N) <= kSmemMax
-               ? 1024 + 2 * (size_t)abytes(N) + 4 * (size_t)img_c(N)
-               : 1024 + 2 * (size_t)abytes(N) + 2 * (size_t)img_c(N);
+    constexpr int NP = NPipes<N>::A;
+    constexpr bool RES = NP > 1 || 1024 + 2 * abytes(N) + 2 * img_r(N) + 2 * img_c(N) <= kSmemMax;
+    return 1024 + (size_t)NP * 2 * abytes(N) + (RES ? 2 * (size_t)img_r(N) + 2 * (size_t)img_c(N) : 2 * (size_t)img_c(N));
 }
 template <int N>
 constexpr size_t smem_b()
 {
-    return 1024 + 2 * (size_t)abytes(N) + 6 * (size_t)img_c(N) <= kSmemMax
-               ? 1024 + 2 * (size_t)abytes(N) + 6 * (size_t)img_c(N)
-               : 1024 + 2 * (size_t)abytes(N) + 2 * (size_t)img_c(N);
+    constexpr int NP = NPipes<N>::B;
+    constexpr bool RES = NP > 1 || 1024 + 2 * abytes(N) + 6 * img_c(N) <= kSmemMax;
+    return 1024 + (size_t)NP * 2 * abytes(N) + (RES ? 6 : 2) * (size_t)img_c(N);
 }
 template <int N>
-constexpr size_t smem_c() { return 1024 + 2 * (size_t)abytes(N) + 2 * (size_t)img_c(N); }
+constexpr size_t smem_c() { return 1024 + (size_t)NPipes<N>::C * 2 * abytes(N) + 2 * (size_t)img_c(N); }
 
 #define DGFS_TRY(x)                   \
     do {                              \
@@ -697,17 +743,18 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
                 a.Ec = Ec;
                 {
                     ProfScope ps(plan, "tc_stage_a", st);
-                    k_stage_a<N><<<dim3(ts->groups_a, RS, 2), kThreads, smem_a<N>(), st>>>(a);
+                    k_stage_a<N><<<dim3(ts->groups_a, RS, 2), kRows * NPipes<N>::A, smem_a<N>(), st>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
                 {
                     ProfScope ps(plan, "tc_stage_b", st);
-                    k_stage_b<N><<<dim3(ts->groups_b, RS), kThreads, smem_b<N>(), st>>>(a);
+                    k_stage_b<N><<<dim3(ts->groups_b, RS), kRows * NPipes<N>::B, smem_b<N>(), st>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
                 {
                     ProfScope ps(plan, "tc_stage_c", st);
-                    k_stage_c<N><<<dim3((N + G - 1) / G, RSB, Ec), kThreads, smem_c<N>(), st>>>(a);
+                    k_stage_c<N><<<dim3((N + G - 1) / G, (RSB + NPipes<N>::C - 1) / NPipes<N>::C, Ec),
+                                   kRows * NPipes<N>::C, smem_c<N>(), st>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
                 {
@@ -758,8 +805,8 @@ dgfs_status tc_prepare(dgfs_plan_s *plan)
     // work-item groups: enough CTAs to fill the GPU about twice
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plan->device);
-    ts->groups_a = std::max(1, (2 * sms + 2 * RS - 1) / (2 * RS));
-    ts->groups_b = std::max(1, (2 * sms + RS - 1) / RS);
+    ts->groups_a = std::max(1, (4 * sms + RS) / (2 * RS));
+    ts->groups_b = std::max(1, (4 * sms + RS / 2) / RS);
     const long IC = img_c(N);
     DGFS_CUDA(cudaMalloc(&ts->Fimg, 2 * IC));
     DGFS_CUDA(cudaMemset(ts->Fimg, 0, 2 * IC));
@@ -837,12 +884,12 @@ dgfs_status tc_autotune(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaSt
     std::vector<Cand> cands;
     const int chunks[] = {ts->chunk_max, std::min(ts->chunk_max, 8), std::min(ts->chunk_max, 4)};
     const int rsbs[] = {std::min(RS, 4), std::min(RS, 8), std::min(RS, 16)};
-    const int waves[] = {1, 2, 4};
+    const int waves[] = {2, 4, 8};
     for (int c : chunks)
         for (int r : rsbs)
             for (int w : waves) {
-                const Cand k{c, std::min(r, ts->rsb_max), std::max(1, (w * sms + 2 * RS - 1) / (2 * RS)),
-                             std::max(1, (w * sms + RS - 1) / RS)};
+                const Cand k{c, std::min(r, ts->rsb_max), std::max(1, (w * sms + RS) / (2 * RS)),
+                             std::max(1, (w * sms + RS / 2) / RS)};
                 bool dup = false;
                 for (auto &o : cands) dup |= o.chunk == k.chunk && o.rsb == k.rsb && o.ga == k.ga && o.gb == k.gb;
                 if (!dup) cands.push_back(k);
