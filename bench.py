@@ -142,7 +142,7 @@ def run_ours(args, rank, world):
     def make(prec):
         return B.Plan(pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"], prec, P, dev)
 
-    precisions = [args.precision] if args.precision != "auto" else ["fp32_tc", "fp64"]
+    precisions = [args.precision] if args.precision != "auto" else ["fp32_tc", "bf16x3", "tf32", "fp64"]
     forms = {}
     main = None
     for prec in precisions:
@@ -344,7 +344,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "fp32_tc", "tf32", "bf16x3"])

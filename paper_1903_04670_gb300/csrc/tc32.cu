@@ -1,4 +1,4 @@
-// Tensor-core (tcgen05) FP32 path of the collision operator (Algorithm 2).
+// Tensor-core (tcgen05) path of the collision operator (Algorithm 2).
 //
 // Reformulation.  With the separable phase of Algorithm 1 (a_rs(l) =
 // pi/L rho_r l.sigma_s), the translate ifft(t1) of Algorithm 2 step 6 is the
@@ -21,40 +21,44 @@
 //
 // Stage A and B CTAs are matrix-stationary: a CTA owns one (r, s) (and side),
 // keeps that (r, s)'s matrices in shared memory (loaded once with one bulk
-// copy per pre-swizzled image) and loops over its work items (point, plane
-// group or pencil tile), prefetching the next item's data into registers while
-// the current item's contractions run.
+// copy per pre-swizzled image) and runs several independent 128-thread
+// pipelines, each looping over work items (point, plane group or pencil tile)
+// and prefetching the next item's data into registers while the current
+// item's contractions run.
 //
-// Precision: operands are split x = hi + lo with hi and lo rounded to TF32; the
-// 3-term product hi*hi + hi*lo + lo*hi with FP32 accumulation in TMEM gives
-// FP32-level results ("3xTF32").  DGFS_TF32 uses the single hi*hi product.
+// Precision: operands are split into TF32 (hi + lo) or BF16 (three terms)
+// parts, see tcfmt.cuh; accumulation is FP32 in TMEM.
 //
 // Every mbarrier wait is bounded; on expiry the kernel raises the plan's error
 // flag, frees its TMEM and returns (reported as DGFS_ETIMEOUT by dgfs_plan_check).
 #include <algorithm>
 #include <cstdint>
+#include <vector>
 
 #include "dgfs_internal.h"
+#include "tcfmt.cuh"
 #include "umma.cuh"
 
 namespace dgfs {
 namespace {
 
 using namespace umma;
+using tcfmt::kRows;
+using tcfmt::Fmt;
 
-constexpr int kRows = 128;             // MMA M: data rows per CTA
 constexpr long kWaitLimit = 1L << 22;  // mbarrier polls before declaring a timeout
 constexpr int kErrTimeout = 1;
 constexpr int kSmemMax = 227 * 1024;
 
 struct TcState {
-    uint8_t *Fimg = nullptr;  // forward DFT as pre-swizzled B-operand images [2 terms][IMGC]
+    int fmt = 0;              // operand format: 0 TF32 split, 1 BF16 three-term split
+    uint8_t *Fimg = nullptr;  // forward DFT as pre-swizzled B-operand images [terms][IMGC]
     int *err = nullptr;       // device error flag
-    int nterms = 3;
+    int nterms = 3;           // products per contraction (TF32: 1 or 3; BF16: 6)
     int chunk = 8;            // evaluations per launch (<= chunk_max, the workspace's)
     int rsb = 8;              // (r, s) blocks of stage C (<= rsb_max)
     int chunk_max = 8, rsb_max = 16;
-    int groups_a = 2, groups_b = 4;  // work-item groups per (r, s) in stages A and B
+    int groups_a = 2, groups_b = 4;  // CTA groups per (r, s) in stages A and B
     int tuned = 0;
 };
 
@@ -64,83 +68,21 @@ struct TcArgs {
     const float *f;        // [P][S][n]
     float2 *Ap, *Bq, *H;   // [E][RS][n]
     float2 *QGp;           // [E][rsb][n]
-    const uint8_t *timg;   // pair: [RS][2 sides][3 axes][2 terms][IMGC] pre-swizzled B images
-    const uint8_t *Fimg;   // [2 terms][IMGC]
+    const uint8_t *timg;   // pair: [RS][2 sides][3 axes][terms][IMGC] pre-swizzled B images
+    const uint8_t *Fimg;   // [terms][IMGC]
     const float2 *b32;     // [RS][n]
     const double *w;       // [RS]
     int *err;
 };
 
-__host__ __device__ constexpr int atoms(int kfloats) { return (kfloats * 4 + 127) / 128; }
-__host__ __device__ constexpr int pow2_cols(int c) { return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ? 128 : c <= 256 ? 256 : 512; }
-// bytes of one B-operand image of 2N rows and K = 2N (complex input) or N (real input) floats
-__host__ __device__ constexpr int img_c(int N) { return atoms(2 * N) * 2 * N * 128; }
-__host__ __device__ constexpr int img_r(int N) { return atoms(N) * 2 * N * 128; }
-__host__ __device__ constexpr int abytes(int N) { return atoms(2 * N) * kRows * 128; }
+__host__ __device__ constexpr int pow2_cols(int c)
+{
+    return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ? 128 : c <= 256 ? 256 : 512;
+}
 
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p)
 {
     return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~(uintptr_t)1023);
-}
-
-__device__ __forceinline__ void split_tf32(float x, float &hi, float &lo)
-{
-    hi = tf32_rna(x);
-    lo = tf32_rna(x - hi);
-}
-
-// store a split complex value at (row, complex index k) of the data operand
-__device__ __forceinline__ void st_c(uint8_t *ah, uint8_t *al, int row, int k, float re, float im)
-{
-    float h0, l0, h1, l1;
-    split_tf32(re, h0, l0);
-    split_tf32(im, h1, l1);
-    const uint32_t o = sw128_off(row, 8 * k, kRows);
-    *reinterpret_cast<float2 *>(ah + o) = make_float2(h0, h1);
-    *reinterpret_cast<float2 *>(al + o) = make_float2(l0, l1);
-}
-
-// store two consecutive split complex values (k even) with one 16-byte access each
-__device__ __forceinline__ void st_c2(uint8_t *ah, uint8_t *al, int row, int k, float2 u, float2 v)
-{
-    float4 h, l;
-    split_tf32(u.x, h.x, l.x);
-    split_tf32(u.y, h.y, l.y);
-    split_tf32(v.x, h.z, l.z);
-    split_tf32(v.y, h.w, l.w);
-    const uint32_t o = sw128_off(row, 8 * k, kRows);
-    *reinterpret_cast<float4 *>(ah + o) = h;
-    *reinterpret_cast<float4 *>(al + o) = l;
-}
-
-__device__ __forceinline__ void st_f4(uint8_t *ah, uint8_t *al, int row, int kb, float4 v)
-{
-    float4 h, l;
-    split_tf32(v.x, h.x, l.x);
-    split_tf32(v.y, h.y, l.y);
-    split_tf32(v.z, h.z, l.z);
-    split_tf32(v.w, h.w, l.w);
-    const uint32_t o = sw128_off(row, kb, kRows);
-    *reinterpret_cast<float4 *>(ah + o) = h;
-    *reinterpret_cast<float4 *>(al + o) = l;
-}
-
-// Issue D = A * B^T over K bytes with 1 or 3 split terms (small terms first).
-__device__ __forceinline__ void gemm(uint32_t d, const uint8_t *ah, const uint8_t *al, const uint8_t *bh,
-                                     const uint8_t *bl, int brows, int kbytes, int nterms, uint32_t idesc)
-{
-    uint32_t acc = 0;
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-        if (nterms == 1 && t < 2) continue;
-        const uint32_t a0 = smem_u32(t == 0 ? al : ah), b0 = smem_u32(t == 1 ? bl : bh);
-        for (int kb = 0; kb < kbytes; kb += 32) {
-            const uint32_t ao = (kb >> 7) * (kRows * 128) + (kb & 127);
-            const uint32_t bo = (kb >> 7) * (brows * 128) + (kb & 127);
-            mma_tf32(d, desc_sw128(a0 + ao), desc_sw128(b0 + bo), idesc, acc);
-            acc = 1;
-        }
-    }
 }
 
 // Named barrier of one 128-thread pipeline: id 1 + pipeline (id 0 is __syncthreads).
@@ -201,9 +143,19 @@ __device__ __forceinline__ uint32_t lane_base(uint32_t tbase)
     return tbase + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16);
 }
 
-__device__ __forceinline__ const uint8_t *timg_at(const uint8_t *timg, int N, int rs, int side, int ax, int term)
+// first term of the image of (r, s, side, axis); terms are IMGC bytes apart
+template <int FMT>
+__device__ __forceinline__ const uint8_t *timg_at(const uint8_t *timg, int N, int rs, int side, int ax)
 {
-    return timg + ((((long)rs * 2 + side) * 3 + ax) * 2 + term) * (long)img_c(N);
+    return timg + (((long)rs * 2 + side) * 3 + ax) * Fmt<FMT>::NT * (long)tcfmt::img_c<FMT>(N);
+}
+
+// Bulk-copy `terms` blocks of `bytes` (source blocks `sstride` apart) to
+// shared memory blocks `dstride` apart, completing on mbar (thread 0 only).
+__device__ __forceinline__ void copy_terms(uint8_t *dst, int dstride, const uint8_t *src, long sstride, int bytes,
+                                           int terms, uint64_t *mbar)
+{
+    for (int t = 0; t < terms; ++t) bulk_g2s(dst + t * dstride, src + t * sstride, bytes, mbar);
 }
 
 // Allocate ncols TMEM columns for the CTA and initialise `nb` mbarriers.
@@ -225,13 +177,25 @@ __device__ __forceinline__ void cta_teardown(uint32_t tb, uint32_t ncols, bool o
     if (threadIdx.x < 32) tmem_dealloc(tb, ncols);
 }
 
-// Pipelines per CTA: each pipeline is 128 threads with its own data operand
-// (hi, lo), TMEM columns, mbarrier and named barrier; the matrix images are
-// shared.  Chosen so that shared memory, TMEM (512 columns) and registers fit.
-template <int N> struct NPipes {
+// Pipelines per CTA: each pipeline is 128 threads with its own data operand,
+// TMEM columns, mbarrier and named barrier; the matrix images are shared.
+// Chosen so that shared memory, TMEM (512 columns) and registers fit.
+template <int N, int FMT> struct NPipes {
     static constexpr int A = N <= 16 ? 4 : (N <= 32 ? 2 : 1);
-    static constexpr int B = N <= 16 ? 4 : (N <= 32 ? 2 : 1);
+    static constexpr int B = N <= 16 ? (FMT == 0 ? 4 : 3) : (N <= 32 ? 2 : 1);
     static constexpr int C = N <= 8 ? 4 : (N <= 32 ? 2 : 1);
+};
+
+// Shared-memory layout sizes of the three stages.
+template <int N, int FMT> struct Smem {
+    static constexpr int NT = Fmt<FMT>::NT;
+    static constexpr int AB = tcfmt::abytes<FMT>(N), IC = tcfmt::img_c<FMT>(N), IR = tcfmt::img_r<FMT>(N);
+    static constexpr bool RES_A = NPipes<N, FMT>::A > 1 || 1024 + NT * (AB + IR + IC) <= kSmemMax;
+    static constexpr bool RES_B = NPipes<N, FMT>::B > 1 || 1024 + NT * (AB + 3 * IC) <= kSmemMax;
+    static constexpr size_t A = 1024 + (size_t)NPipes<N, FMT>::A * NT * AB + (RES_A ? NT * (IR + IC) : NT * IC);
+    static constexpr size_t B = 1024 + (size_t)NPipes<N, FMT>::B * NT * AB + (RES_B ? 3 : 1) * NT * IC;
+    static constexpr size_t C = 1024 + (size_t)NPipes<N, FMT>::C * NT * AB + NT * IC;
+    static_assert(A <= kSmemMax && B <= kSmemMax && C <= kSmemMax, "shared memory");
 };
 
 // ------------------------------------------------------------------ stage A
@@ -239,23 +203,24 @@ template <int N> struct NPipes {
 // its NP pipelines loops over items (point e, group of G x-planes): z-pass
 // (real input), an in-plane transpose through shared memory, y-pass, result A'
 // or B' to global.
-template <int N>
-__global__ void __launch_bounds__(kRows *NPipes<N>::A, 1) k_stage_a(TcArgs a)
+template <int N, int FMT>
+__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs a)
 {
-    constexpr int NP = NPipes<N>::A;
-    constexpr int G = kRows / N, KR = N, KC = 2 * N, NO = 2 * N, NG = (N + G - 1) / G;
-    constexpr int AB = abytes(N), IR = img_r(N), IC = img_c(N);
-    constexpr bool RESIDENT = NP > 1 || 1024 + 2 * AB + 2 * IR + 2 * IC <= kSmemMax;
+    using SM = Smem<N, FMT>;
+    constexpr int NP = NPipes<N, FMT>::A, NT = SM::NT, AB = SM::AB, IR = SM::IR, IC = SM::IC;
+    constexpr bool RESIDENT = SM::RES_A;
+    constexpr int G = kRows / N, KC = 2 * N, NO = 2 * N, NG = (N + G - 1) / G;
+    // real-input K padded to whole 32-byte MMA steps (16 BF16 elements); the pad is zero
+    constexpr int KR = FMT == 1 ? (N + 15) / 16 * 16 : N;
     constexpr int NN = N * N;
     constexpr int FPT = (G * NN / 4 + kRows - 1) / kRows;  // float4 per thread for one group
     constexpr uint32_t NCOL = pow2_cols(NP * 2 * NO);
-    static_assert(1024 + NP * 2 * AB + (RESIDENT ? 2 * IR + 2 * IC : 2 * IC) <= kSmemMax, "smem");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align1024(smem_raw);
     const int pp = threadIdx.x / kRows, t = threadIdx.x % kRows, bar = 1 + pp;
-    uint8_t *Bzh = sm, *Bzl = Bzh + IR;
-    uint8_t *Byh = RESIDENT ? Bzl + IR : Bzh, *Byl = Byh + IC;
-    uint8_t *Ah = Byl + IC + pp * 2 * AB, *Al = Ah + AB;
+    uint8_t *Bz = sm;                            // NT terms, IR apart
+    uint8_t *By = RESIDENT ? Bz + NT * IR : Bz;  // NT terms, IC apart (one reloaded slot if not resident)
+    uint8_t *A0 = sm + (RESIDENT ? NT * (IR + IC) : NT * IC) + pp * NT * AB;
     __shared__ uint64_t mb[NP + 1];  // [0, NP): MMA per pipeline, NP: copies
     __shared__ uint32_t tslot;
     const int rs = blockIdx.y, side = blockIdx.z;
@@ -266,16 +231,10 @@ __global__ void __launch_bounds__(kRows *NPipes<N>::A, 1) k_stage_a(TcArgs a)
     uint32_t ph_mma = 0, ph_cp = 0;
     auto load_imgs = [&](int which) {  // 0: z, 1: y, 2: both
         if (threadIdx.x == 0) {
-            const uint32_t bytes = which == 0 ? 2 * IR : which == 1 ? 2 * IC : 2 * IR + 2 * IC;
+            const uint32_t bytes = which == 0 ? NT * IR : which == 1 ? NT * IC : NT * (IR + IC);
             mbar_expect_tx(&mb[NP], bytes);
-            if (which != 1) {
-                bulk_g2s(Bzh, timg_at(a.timg, N, rs, side, 2, 0), IR, &mb[NP]);
-                bulk_g2s(Bzl, timg_at(a.timg, N, rs, side, 2, 1), IR, &mb[NP]);
-            }
-            if (which != 0) {
-                bulk_g2s(Byh, timg_at(a.timg, N, rs, side, 1, 0), IC, &mb[NP]);
-                bulk_g2s(Byl, timg_at(a.timg, N, rs, side, 1, 1), IC, &mb[NP]);
-            }
+            if (which != 1) copy_terms(Bz, IR, timg_at<FMT>(a.timg, N, rs, side, 2), IC, IR, NT, &mb[NP]);
+            if (which != 0) copy_terms(By, IC, timg_at<FMT>(a.timg, N, rs, side, 1), IC, IC, NT, &mb[NP]);
         }
     };
     const int sp = side == 0 ? a.p : a.q;
@@ -304,7 +263,16 @@ __global__ void __launch_bounds__(kRows *NPipes<N>::A, 1) k_stage_a(TcArgs a)
 #pragma unroll
         for (int j = 0; j < FPT; ++j) {
             const int i = t + kRows * j;
-            if (4 * i < nval * NN) st_f4(Ah, Al, (4 * i) / N, ((4 * i) % N) * 4, pf[j]);
+            if (4 * i < nval * NN) tcfmt::st_f4<FMT>(A0, AB, (4 * i) / N, (4 * i) % N, pf[j]);
+        }
+        if constexpr (KR > N) {  // zero the pad of this thread's row in every term
+            if (t < nval * N)
+#pragma unroll
+                for (int term = 0; term < NT; ++term)
+#pragma unroll
+                    for (int e0 = N; e0 < KR; e0 += 8)
+                        *reinterpret_cast<uint4 *>(A0 + term * AB + sw128_off(t, e0 * Fmt<FMT>::ESZ, kRows)) =
+                            make_uint4(0u, 0u, 0u, 0u);
         }
         if (it + stride < items) prefetch(it + stride);
         if (!RESIDENT) {
@@ -312,8 +280,7 @@ __global__ void __launch_bounds__(kRows *NPipes<N>::A, 1) k_stage_a(TcArgs a)
             ok = wait_copy_pipe(&mb[NP], ph_cp, bar);
             if (!ok) break;
         }
-        ok = run_mma(&mb[pp], ph_mma, bar,
-                     [&] { gemm(tb, Ah, Al, Bzh, Bzl, NO, KR * 4, a.nterms, idesc_tf32(kRows, NO)); });
+        ok = run_mma(&mb[pp], ph_mma, bar, [&] { tcfmt::gemm<FMT>(tb, A0, AB, Bz, IR, NO, KR, a.nterms); });
         if (!ok) break;
         // transpose within each plane: row (g, y) holds z' -> rows (g, z'), K = y
 #pragma unroll
@@ -322,7 +289,8 @@ __global__ void __launch_bounds__(kRows *NPipes<N>::A, 1) k_stage_a(TcArgs a)
             tmem_ld16(tl + c0, v);
             if (t < nval * N) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) st_c(Ah, Al, g * N + c0 / 2 + j, yl, v[2 * j], v[2 * j + 1]);
+                for (int j = 0; j < 8; ++j)
+                    tcfmt::st_c<FMT>(A0, AB, g * N + c0 / 2 + j, yl, v[2 * j], v[2 * j + 1]);
             }
         }
         if (!RESIDENT) {
@@ -330,8 +298,7 @@ __global__ void __launch_bounds__(kRows *NPipes<N>::A, 1) k_stage_a(TcArgs a)
             ok = wait_copy_pipe(&mb[NP], ph_cp, bar);
             if (!ok) break;
         }
-        ok = run_mma(&mb[pp], ph_mma, bar,
-                     [&] { gemm(tb + NO, Ah, Al, Byh, Byl, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
+        ok = run_mma(&mb[pp], ph_mma, bar, [&] { tcfmt::gemm<FMT>(tb + NO, A0, AB, By, IC, NO, KC, a.nterms); });
         if (!ok) break;
         // row t = (g, z'): y' values -> global [x][y'][z']
         float2 *dst = (side == 0 ? a.Ap : a.Bq) + ((long)e * a.RS + rs) * n + (long)(x0 + g) * NN + yl;
@@ -353,39 +320,35 @@ __global__ void __launch_bounds__(kRows *NPipes<N>::A, 1) k_stage_a(TcArgs a)
 // fit next to the data operands (else it reloads one image slot per
 // contraction); each of its NP pipelines loops over items (point e, tile of
 // 128 (y, z) pencils): H = F_x ((T^p_x A') . (T^q_x B')).
-template <int N>
-__global__ void __launch_bounds__(kRows *NPipes<N>::B, 1) k_stage_b(TcArgs a)
+template <int N, int FMT>
+__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b(TcArgs a)
 {
-    constexpr int NP = NPipes<N>::B;
-    constexpr int KC = 2 * N, NO = 2 * N, NN = N * N, NT = (NN + kRows - 1) / kRows;
-    constexpr int AB = abytes(N), IC = img_c(N);
-    constexpr bool RESIDENT = NP > 1 || 1024 + 2 * AB + 6 * IC <= kSmemMax;
+    using SM = Smem<N, FMT>;
+    constexpr int NP = NPipes<N, FMT>::B, NT = SM::NT, AB = SM::AB, IC = SM::IC;
+    constexpr bool RESIDENT = SM::RES_B;
+    constexpr int KC = 2 * N, NO = 2 * N, NN = N * N, NT_TILES = (NN + kRows - 1) / kRows;
     constexpr uint32_t NCOL = pow2_cols(NP * 3 * NO);
-    static_assert(1024 + NP * 2 * AB + (RESIDENT ? 6 : 2) * IC <= kSmemMax, "smem");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align1024(smem_raw);
     const int pp = threadIdx.x / kRows, t = threadIdx.x % kRows, bar = 1 + pp;
-    uint8_t *B0 = sm;  // image slots: [Txp hi, lo][Txq hi, lo][F hi, lo] or one [hi, lo]
-    uint8_t *Ah = B0 + (RESIDENT ? 6 : 2) * IC + pp * 2 * AB, *Al = Ah + AB;
+    uint8_t *B0 = sm;  // image slots [T^p_x][T^q_x][F], NT terms each, or one reloaded slot
+    uint8_t *A0 = B0 + (RESIDENT ? 3 : 1) * NT * IC + pp * NT * AB;
     __shared__ uint64_t mb[NP + 1];
     __shared__ uint32_t tslot;
     const int rs = blockIdx.y;
     const long n = a.n;
-    const int items = a.Ec * NT;
+    const int items = a.Ec * NT_TILES;
     cta_setup(&tslot, NCOL, mb, NP + 1);
     const uint32_t tb = tslot + pp * 3 * NO, tl = lane_base(tb);
     uint32_t ph_mma = 0, ph_cp = 0;
-    auto src_img = [&](int which, int term) -> const uint8_t * {
-        return which < 2 ? timg_at(a.timg, N, rs, which, 0, term) : a.Fimg + (long)term * IC;
+    auto src_img = [&](int which) -> const uint8_t * {
+        return which < 2 ? timg_at<FMT>(a.timg, N, rs, which, 0) : a.Fimg;
     };
-    auto slot = [&](int which) -> uint8_t * { return RESIDENT ? B0 + 2 * which * IC : B0; };
+    auto slot = [&](int which) -> uint8_t * { return RESIDENT ? B0 + which * NT * IC : B0; };
     auto load_images = [&](int first, int count) {
         if (threadIdx.x == 0) {
-            mbar_expect_tx(&mb[NP], 2 * IC * count);
-            for (int w = first; w < first + count; ++w) {
-                bulk_g2s(slot(w), src_img(w, 0), IC, &mb[NP]);
-                bulk_g2s(slot(w) + IC, src_img(w, 1), IC, &mb[NP]);
-            }
+            mbar_expect_tx(&mb[NP], NT * IC * count);
+            for (int w = first; w < first + count; ++w) copy_terms(slot(w), IC, src_img(w), IC, IC, NT, &mb[NP]);
         }
     };
     float2 pa[N];
@@ -396,7 +359,7 @@ __global__ void __launch_bounds__(kRows *NPipes<N>::B, 1) k_stage_b(TcArgs a)
     const int stride = gridDim.x * NP;
     int it = blockIdx.x * NP + pp;
     if (it < items) {
-        const int e = it / NT, p0 = (it % NT) * kRows;
+        const int e = it / NT_TILES, p0 = (it % NT_TILES) * kRows;
         load_pencil(pa, a.Ap + ((long)e * a.RS + rs) * n + p0 + t, p0 + t < NN);
     }
     bool ok = true;
@@ -405,11 +368,11 @@ __global__ void __launch_bounds__(kRows *NPipes<N>::B, 1) k_stage_b(TcArgs a)
         ok = wait_copy_cta(&mb[NP], ph_cp);
     }
     for (; it < items && ok; it += stride) {
-        const int e = it / NT, p0 = (it % NT) * kRows;
+        const int e = it / NT_TILES, p0 = (it % NT_TILES) * kRows;
         const bool valid = p0 + t < NN;
         const long gbase = ((long)e * a.RS + rs) * n + p0 + t;
 #pragma unroll
-        for (int x = 0; x < N; x += 2) st_c2(Ah, Al, t, x, pa[x], pa[x + 1]);
+        for (int x = 0; x < N; x += 2) tcfmt::st_c2<FMT>(A0, AB, t, x, pa[x], pa[x + 1]);
         float2 pb[N];
         load_pencil(pb, a.Bq + gbase, valid);
         if (!RESIDENT) {
@@ -417,14 +380,13 @@ __global__ void __launch_bounds__(kRows *NPipes<N>::B, 1) k_stage_b(TcArgs a)
             ok = wait_copy_pipe(&mb[NP], ph_cp, bar);
             if (!ok) break;
         }
-        ok = run_mma(&mb[pp], ph_mma, bar,
-                     [&] { gemm(tb, Ah, Al, slot(0), slot(0) + IC, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
+        ok = run_mma(&mb[pp], ph_mma, bar, [&] { tcfmt::gemm<FMT>(tb, A0, AB, slot(0), IC, NO, KC, a.nterms); });
         if (!ok) break;
 #pragma unroll
-        for (int x = 0; x < N; x += 2) st_c2(Ah, Al, t, x, pb[x], pb[x + 1]);
+        for (int x = 0; x < N; x += 2) tcfmt::st_c2<FMT>(A0, AB, t, x, pb[x], pb[x + 1]);
         const int nx = it + stride;
         if (nx < items) {
-            const int e2 = nx / NT, q0 = (nx % NT) * kRows;
+            const int e2 = nx / NT_TILES, q0 = (nx % NT_TILES) * kRows;
             load_pencil(pa, a.Ap + ((long)e2 * a.RS + rs) * n + q0 + t, q0 + t < NN);
         }
         if (!RESIDENT) {
@@ -432,9 +394,8 @@ __global__ void __launch_bounds__(kRows *NPipes<N>::B, 1) k_stage_b(TcArgs a)
             ok = wait_copy_pipe(&mb[NP], ph_cp, bar);
             if (!ok) break;
         }
-        ok = run_mma(&mb[pp], ph_mma, bar, [&] {
-            gemm(tb + NO, Ah, Al, slot(1), slot(1) + IC, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO));
-        });
+        ok = run_mma(&mb[pp], ph_mma, bar,
+                     [&] { tcfmt::gemm<FMT>(tb + NO, A0, AB, slot(1), IC, NO, KC, a.nterms); });
         if (!ok) break;
         // P = A . B (complex), back into the data operand
 #pragma unroll
@@ -448,7 +409,7 @@ __global__ void __launch_bounds__(kRows *NPipes<N>::B, 1) k_stage_b(TcArgs a)
                                                va[2 * j] * vb[2 * j + 1] + va[2 * j + 1] * vb[2 * j]);
                 const float2 p1v = make_float2(va[2 * j + 2] * vb[2 * j + 2] - va[2 * j + 3] * vb[2 * j + 3],
                                                va[2 * j + 2] * vb[2 * j + 3] + va[2 * j + 3] * vb[2 * j + 2]);
-                st_c2(Ah, Al, t, c0 / 2 + j, p0v, p1v);
+                tcfmt::st_c2<FMT>(A0, AB, t, c0 / 2 + j, p0v, p1v);
             }
         }
         if (!RESIDENT) {
@@ -456,9 +417,8 @@ __global__ void __launch_bounds__(kRows *NPipes<N>::B, 1) k_stage_b(TcArgs a)
             ok = wait_copy_pipe(&mb[NP], ph_cp, bar);
             if (!ok) break;
         }
-        ok = run_mma(&mb[pp], ph_mma, bar, [&] {
-            gemm(tb + 2 * NO, Ah, Al, slot(2), slot(2) + IC, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO));
-        });
+        ok = run_mma(&mb[pp], ph_mma, bar,
+                     [&] { tcfmt::gemm<FMT>(tb + 2 * NO, A0, AB, slot(2), IC, NO, KC, a.nterms); });
         if (!ok) break;
         float2 *dst = a.H + gbase;
 #pragma unroll
@@ -479,21 +439,20 @@ __global__ void __launch_bounds__(kRows *NPipes<N>::B, 1) k_stage_b(TcArgs a)
 // (r, s) and, for every (r, s) of it, computes t3 = F_y F_z H on the tensor
 // cores and QG_part += w_rs b_rs . t3 in registers; the next (r, s)'s H tile
 // is prefetched into registers meanwhile.
-template <int N>
-__global__ void __launch_bounds__(kRows *NPipes<N>::C, 1) k_stage_c(TcArgs a)
+template <int N, int FMT>
+__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::C, 1) k_stage_c(TcArgs a)
 {
-    constexpr int NP = NPipes<N>::C;
+    using SM = Smem<N, FMT>;
+    constexpr int NP = NPipes<N, FMT>::C, NT = SM::NT, AB = SM::AB, IC = SM::IC;
     constexpr int G = kRows / N, KC = 2 * N, NO = 2 * N, NN = N * N;
-    constexpr int AB = abytes(N), IC = img_c(N);
     constexpr int HPT = (G * NN / 2 + kRows - 1) / kRows;  // float4 (2 complex) per thread per tile
     constexpr bool PREFETCH = N <= 32;
     constexpr uint32_t NCOL = pow2_cols(NP * 2 * NO);
-    static_assert(1024 + NP * 2 * AB + 2 * IC <= kSmemMax, "smem");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align1024(smem_raw);
     const int pp = threadIdx.x / kRows, t = threadIdx.x % kRows, bar = 1 + pp;
-    uint8_t *Bh = sm, *Bl = Bh + IC;
-    uint8_t *Ah = Bl + IC + pp * 2 * AB, *Al = Ah + AB;
+    uint8_t *Bf = sm;  // F, NT terms IC apart
+    uint8_t *A0 = Bf + NT * IC + pp * NT * AB;
     __shared__ uint64_t mb[NP + 1];
     __shared__ uint32_t tslot;
     const int x0 = blockIdx.x * G, rb = blockIdx.y * NP + pp, e = blockIdx.z;
@@ -503,9 +462,8 @@ __global__ void __launch_bounds__(kRows *NPipes<N>::C, 1) k_stage_c(TcArgs a)
     const uint32_t tb = tslot + pp * 2 * NO, tl = lane_base(tb);
     uint32_t ph_mma = 0, ph_cp = 0;
     if (threadIdx.x == 0) {
-        mbar_expect_tx(&mb[NP], 2 * IC);
-        bulk_g2s(Bh, a.Fimg, IC, &mb[NP]);
-        bulk_g2s(Bl, a.Fimg + IC, IC, &mb[NP]);
+        mbar_expect_tx(&mb[NP], NT * IC);
+        copy_terms(Bf, IC, a.Fimg, IC, IC, NT, &mb[NP]);
     }
     const int g = t / N, yl = t % N;
     float2 acc[N];
@@ -526,12 +484,12 @@ __global__ void __launch_bounds__(kRows *NPipes<N>::C, 1) k_stage_c(TcArgs a)
     }
     bool ok = wait_copy_cta(&mb[NP], ph_cp);
     for (int rs = rs0; rs < rs1 && ok; ++rs) {
-        // rows (g, y), K = z (complex): contiguous planes
+        // rows (g, y), K = z (complex): contiguous planes; float4 i holds complex 2i, 2i+1
         if constexpr (PREFETCH) {
 #pragma unroll
             for (int j = 0; j < HPT; ++j) {
                 const int i = t + kRows * j;
-                if (2 * i < nval * NN) st_f4(Ah, Al, (2 * i) / N, ((2 * i) % N) * 8, hp[j]);
+                if (2 * i < nval * NN) tcfmt::st_f4<FMT>(A0, AB, (2 * i) / N, 2 * ((2 * i) % N), hp[j]);
             }
             if (rs + 1 < rs1) {
                 const float4 *src = tile(rs + 1);
@@ -543,10 +501,10 @@ __global__ void __launch_bounds__(kRows *NPipes<N>::C, 1) k_stage_c(TcArgs a)
             }
         } else {
             const float4 *src = tile(rs);
-            for (int i = t; i < nval * NN / 2; i += kRows) st_f4(Ah, Al, (2 * i) / N, ((2 * i) % N) * 8, src[i]);
+            for (int i = t; i < nval * NN / 2; i += kRows)
+                tcfmt::st_f4<FMT>(A0, AB, (2 * i) / N, 2 * ((2 * i) % N), src[i]);
         }
-        ok = run_mma(&mb[pp], ph_mma, bar,
-                     [&] { gemm(tb, Ah, Al, Bh, Bl, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
+        ok = run_mma(&mb[pp], ph_mma, bar, [&] { tcfmt::gemm<FMT>(tb, A0, AB, Bf, IC, NO, KC, a.nterms); });
         if (!ok) break;
 #pragma unroll
         for (int c0 = 0; c0 < NO; c0 += 16) {
@@ -554,11 +512,11 @@ __global__ void __launch_bounds__(kRows *NPipes<N>::C, 1) k_stage_c(TcArgs a)
             tmem_ld16(tl + c0, v);
             if (t < nval * N) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) st_c(Ah, Al, g * N + c0 / 2 + j, yl, v[2 * j], v[2 * j + 1]);
+                for (int j = 0; j < 8; ++j)
+                    tcfmt::st_c<FMT>(A0, AB, g * N + c0 / 2 + j, yl, v[2 * j], v[2 * j + 1]);
             }
         }
-        ok = run_mma(&mb[pp], ph_mma, bar,
-                     [&] { gemm(tb + NO, Ah, Al, Bh, Bl, NO, KC * 4, a.nterms, idesc_tf32(kRows, NO)); });
+        ok = run_mma(&mb[pp], ph_mma, bar, [&] { tcfmt::gemm<FMT>(tb + NO, A0, AB, Bf, IC, NO, KC, a.nterms); });
         if (!ok) break;
         // row t = (g, kz): t3(kx0+g, ky, kz) for all ky
         const float wr = (float)a.w[rs];
@@ -604,16 +562,11 @@ __global__ void k_sum_partials(double2 *QG64, const float2 *QGp, int rsb, long n
 }
 
 // ------------------------------------------------------ table preparation
-__device__ __forceinline__ void put_split(uint8_t *img_hi, uint8_t *img_lo, uint32_t off, double v)
-{
-    const float h = tf32_rna((float)v);
-    *reinterpret_cast<float *>(img_hi + off) = h;
-    *reinterpret_cast<float *>(img_lo + off) = tf32_rna((float)(v - (double)h));
-}
-
 // T_d[j][j'] = (1/N) sum_l exp(2 pi i l (j - j') / N) phi_d(l), written into
-// pre-swizzled B-operand images: z (real input) rows 2j, 2j+1, K = j';
-// y, x (complex input) the real 2x2 block [Re -Im; Im Re] at K = 2j', 2j'+1.
+// pre-swizzled B-operand images (terms IMGC apart): z (real input) rows 2j,
+// 2j+1, K = j'; y, x (complex input) the real 2x2 block [Re -Im; Im Re] at
+// K = 2j', 2j'+1.
+template <int FMT>
 __global__ void k_timg(uint8_t *out, const double2 *phase, int N, int RS)
 {
     const long total = (long)RS * 2 * 3 * N * N;
@@ -633,21 +586,21 @@ __global__ void k_timg(uint8_t *out, const double2 *phase, int N, int RS)
     tr /= N;
     ti /= N;
     const int NO = 2 * N;
-    const long IC = img_c(N);
-    uint8_t *hi = out + ((((long)rs * 2 + side) * 3 + ax) * 2 + 0) * IC;
-    uint8_t *lo = hi + IC;
+    const long IC = tcfmt::img_c<FMT>(N);
+    uint8_t *img = out + (((long)rs * 2 + side) * 3 + ax) * Fmt<FMT>::NT * IC;
     if (ax == 2) {
-        put_split(hi, lo, sw128_off(2 * j, 4 * jp, NO), tr);
-        put_split(hi, lo, sw128_off(2 * j + 1, 4 * jp, NO), ti);
+        tcfmt::put_img<FMT>(img, IC, 2 * j, jp, NO, tr);
+        tcfmt::put_img<FMT>(img, IC, 2 * j + 1, jp, NO, ti);
     } else {
-        put_split(hi, lo, sw128_off(2 * j, 4 * (2 * jp), NO), tr);
-        put_split(hi, lo, sw128_off(2 * j, 4 * (2 * jp + 1), NO), -ti);
-        put_split(hi, lo, sw128_off(2 * j + 1, 4 * (2 * jp), NO), ti);
-        put_split(hi, lo, sw128_off(2 * j + 1, 4 * (2 * jp + 1), NO), tr);
+        tcfmt::put_img<FMT>(img, IC, 2 * j, 2 * jp, NO, tr);
+        tcfmt::put_img<FMT>(img, IC, 2 * j, 2 * jp + 1, NO, -ti);
+        tcfmt::put_img<FMT>(img, IC, 2 * j + 1, 2 * jp, NO, ti);
+        tcfmt::put_img<FMT>(img, IC, 2 * j + 1, 2 * jp + 1, NO, tr);
     }
 }
 
 // forward DFT F[k][j] = exp(-2 pi i jk/N) as pre-swizzled complex-input images
+template <int FMT>
 __global__ void k_fimg(uint8_t *out, int N)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -657,11 +610,11 @@ __global__ void k_fimg(uint8_t *out, int N)
     sincospi(2.0 * ((j * k) % N) / N, &s, &c);
     const double fr = c, fi = -s;
     const int NO = 2 * N;
-    uint8_t *hi = out, *lo = out + img_c(N);
-    put_split(hi, lo, sw128_off(2 * k, 4 * (2 * j), NO), fr);
-    put_split(hi, lo, sw128_off(2 * k, 4 * (2 * j + 1), NO), -fi);
-    put_split(hi, lo, sw128_off(2 * k + 1, 4 * (2 * j), NO), fi);
-    put_split(hi, lo, sw128_off(2 * k + 1, 4 * (2 * j + 1), NO), fr);
+    const long IC = tcfmt::img_c<FMT>(N);
+    tcfmt::put_img<FMT>(out, IC, 2 * k, 2 * j, NO, fr);
+    tcfmt::put_img<FMT>(out, IC, 2 * k, 2 * j + 1, NO, -fi);
+    tcfmt::put_img<FMT>(out, IC, 2 * k + 1, 2 * j, NO, fi);
+    tcfmt::put_img<FMT>(out, IC, 2 * k + 1, 2 * j + 1, NO, fr);
 }
 
 __global__ void k_to_f32(float2 *dst, const double2 *src, long count)
@@ -672,32 +625,16 @@ __global__ void k_to_f32(float2 *dst, const double2 *src, long count)
 
 unsigned nblk(long total, int t) { return (unsigned)((total + t - 1) / t); }
 
-template <int N>
-constexpr size_t smem_a()
-{
-    constexpr int NP = NPipes<N>::A;
-    constexpr bool RES = NP > 1 || 1024 + 2 * abytes(N) + 2 * img_r(N) + 2 * img_c(N) <= kSmemMax;
-    return 1024 + (size_t)NP * 2 * abytes(N) + (RES ? 2 * (size_t)img_r(N) + 2 * (size_t)img_c(N) : 2 * (size_t)img_c(N));
-}
-template <int N>
-constexpr size_t smem_b()
-{
-    constexpr int NP = NPipes<N>::B;
-    constexpr bool RES = NP > 1 || 1024 + 2 * abytes(N) + 6 * img_c(N) <= kSmemMax;
-    return 1024 + (size_t)NP * 2 * abytes(N) + (RES ? 6 : 2) * (size_t)img_c(N);
-}
-template <int N>
-constexpr size_t smem_c() { return 1024 + (size_t)NPipes<N>::C * 2 * abytes(N) + 2 * (size_t)img_c(N); }
-
 #define DGFS_TRY(x)                   \
     do {                              \
         dgfs_status s_ = (x);         \
         if (s_ != DGFS_OK) return s_; \
     } while (0)
 
-template <int N>
+template <int N, int FMT>
 dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaStream_t st)
 {
+    using SM = Smem<N, FMT>;
     TcState *ts = reinterpret_cast<TcState *>(plan->tc);
     const int S = plan->S, RS = plan->Nrho * plan->M;
     const long n = (long)N * N * N;
@@ -743,18 +680,18 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
                 a.Ec = Ec;
                 {
                     ProfScope ps(plan, "tc_stage_a", st);
-                    k_stage_a<N><<<dim3(ts->groups_a, RS, 2), kRows * NPipes<N>::A, smem_a<N>(), st>>>(a);
+                    k_stage_a<N, FMT><<<dim3(ts->groups_a, RS, 2), kRows * NPipes<N, FMT>::A, SM::A, st>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
                 {
                     ProfScope ps(plan, "tc_stage_b", st);
-                    k_stage_b<N><<<dim3(ts->groups_b, RS), kRows * NPipes<N>::B, smem_b<N>(), st>>>(a);
+                    k_stage_b<N, FMT><<<dim3(ts->groups_b, RS), kRows * NPipes<N, FMT>::B, SM::B, st>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
                 {
                     ProfScope ps(plan, "tc_stage_c", st);
-                    k_stage_c<N><<<dim3((N + G - 1) / G, (RSB + NPipes<N>::C - 1) / NPipes<N>::C, Ec),
-                                   kRows * NPipes<N>::C, smem_c<N>(), st>>>(a);
+                    k_stage_c<N, FMT><<<dim3((N + G - 1) / G, (RSB + NPipes<N, FMT>::C - 1) / NPipes<N, FMT>::C, Ec),
+                                        kRows * NPipes<N, FMT>::C, SM::C, st>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
                 {
@@ -769,14 +706,65 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
     return DGFS_OK;
 }
 
-template <int N>
+template <int N, int FMT>
 dgfs_status set_smem_attrs()
 {
-    static_assert(smem_a<N>() <= kSmemMax && smem_b<N>() <= kSmemMax && smem_c<N>() <= kSmemMax, "smem");
-    DGFS_CUDA(cudaFuncSetAttribute(k_stage_a<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a<N>()));
-    DGFS_CUDA(cudaFuncSetAttribute(k_stage_b<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b<N>()));
-    DGFS_CUDA(cudaFuncSetAttribute(k_stage_c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c<N>()));
+    using SM = Smem<N, FMT>;
+    DGFS_CUDA(cudaFuncSetAttribute(k_stage_a<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::A));
+    DGFS_CUDA(cudaFuncSetAttribute(k_stage_b<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B));
+    DGFS_CUDA(cudaFuncSetAttribute(k_stage_c<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::C));
     return DGFS_OK;
+}
+
+template <int FMT>
+dgfs_status dispatch_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st)
+{
+    switch (plan->N) {
+    case 8: return collide_n<8, FMT>(plan, P, f, Q, st);
+    case 16: return collide_n<16, FMT>(plan, P, f, Q, st);
+    case 24: return collide_n<24, FMT>(plan, P, f, Q, st);
+    case 32: return collide_n<32, FMT>(plan, P, f, Q, st);
+    case 48: return collide_n<48, FMT>(plan, P, f, Q, st);
+    default: set_error("N not supported by the tensor-core path"); return DGFS_EUNSUPPORTED;
+    }
+}
+
+template <int FMT>
+dgfs_status dispatch_attrs(int N)
+{
+    switch (N) {
+    case 8: return set_smem_attrs<8, FMT>();
+    case 16: return set_smem_attrs<16, FMT>();
+    case 24: return set_smem_attrs<24, FMT>();
+    case 32: return set_smem_attrs<32, FMT>();
+    case 48: return set_smem_attrs<48, FMT>();
+    default: set_error("N not supported by the tensor-core path"); return DGFS_EUNSUPPORTED;
+    }
+}
+
+template <int FMT>
+dgfs_status build_images(dgfs_plan_s *plan, TcState *ts)
+{
+    const int N = plan->N, RS = plan->Nrho * plan->M;
+    const long n = (long)N * N * N;
+    const long IC = tcfmt::img_c<FMT>(N);
+    constexpr int NT = Fmt<FMT>::NT;
+    DGFS_CUDA(cudaMalloc(&ts->Fimg, NT * IC));
+    DGFS_CUDA(cudaMemset(ts->Fimg, 0, NT * IC));
+    k_fimg<FMT><<<nblk((long)N * N, 256), 256>>>(ts->Fimg, N);
+    DGFS_LAUNCHED(plan);
+    for (auto &pt : plan->pairs) {
+        const size_t tbytes = (size_t)RS * 2 * 3 * NT * IC;
+        DGFS_CUDA(cudaMalloc(&pt.tmat, tbytes));
+        DGFS_CUDA(cudaMemset(pt.tmat, 0, tbytes));
+        DGFS_CUDA(cudaMalloc(&pt.b32, sizeof(float2) * RS * n));
+        plan->table_bytes += tbytes + sizeof(float2) * RS * n;
+        k_timg<FMT><<<nblk((long)RS * 6 * N * N, 256), 256>>>(reinterpret_cast<uint8_t *>(pt.tmat), pt.phase, N, RS);
+        DGFS_LAUNCHED(plan);
+        k_to_f32<<<nblk(RS * n, 256), 256>>>(pt.b32, pt.b, RS * n);
+        DGFS_LAUNCHED(plan);
+    }
+    return dispatch_attrs<FMT>(N);
 }
 
 bool tc_supported_N(int N) { return N == 8 || N == 16 || N == 24 || N == 32 || N == 48; }
@@ -786,52 +774,27 @@ bool tc_supported_N(int N) { return N == 8 || N == 16 || N == 24 || N == 32 || N
 dgfs_status tc_prepare(dgfs_plan_s *plan)
 {
     const int N = plan->N, RS = plan->Nrho * plan->M;
-    const long n = (long)N * N * N;
     if (!tc_supported_N(N)) {
         set_error("tensor-core plans support N in {8, 16, 24, 32, 48}");
         return DGFS_EUNSUPPORTED;
     }
-    if (plan->prec == DGFS_BF16X3) {
-        set_error("the split-BF16 form is not built yet");
-        return DGFS_EUNSUPPORTED;
-    }
     TcState *ts = new TcState();
     plan->tc = ts;
-    ts->nterms = plan->prec == DGFS_TF32 ? 1 : 3;
+    ts->fmt = plan->prec == DGFS_BF16X3 ? 1 : 0;
+    ts->nterms = plan->prec == DGFS_TF32 ? 1 : (plan->prec == DGFS_BF16X3 ? 6 : 3);
     ts->chunk_max = std::max(1, std::min(plan->max_points, 24));
     ts->chunk = ts->chunk_max;
     ts->rsb_max = std::min(RS, 16);
     ts->rsb = std::min(RS, 8);
-    // work-item groups: enough CTAs to fill the GPU about twice
+    // CTA groups: about four waves of CTAs over the GPU
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plan->device);
     ts->groups_a = std::max(1, (4 * sms + RS) / (2 * RS));
     ts->groups_b = std::max(1, (4 * sms + RS / 2) / RS);
-    const long IC = img_c(N);
-    DGFS_CUDA(cudaMalloc(&ts->Fimg, 2 * IC));
-    DGFS_CUDA(cudaMemset(ts->Fimg, 0, 2 * IC));
     DGFS_CUDA(cudaMalloc(&ts->err, sizeof(int)));
     DGFS_CUDA(cudaMemset(ts->err, 0, sizeof(int)));
-    k_fimg<<<nblk((long)N * N, 256), 256>>>(ts->Fimg, N);
-    DGFS_LAUNCHED(plan);
-    for (auto &pt : plan->pairs) {
-        const size_t tbytes = (size_t)RS * 2 * 3 * 2 * IC;
-        DGFS_CUDA(cudaMalloc(&pt.tmat, tbytes));
-        DGFS_CUDA(cudaMemset(pt.tmat, 0, tbytes));
-        DGFS_CUDA(cudaMalloc(&pt.b32, sizeof(float2) * RS * n));
-        plan->table_bytes += tbytes + sizeof(float2) * RS * n;
-        k_timg<<<nblk((long)RS * 6 * N * N, 256), 256>>>(reinterpret_cast<uint8_t *>(pt.tmat), pt.phase, N, RS);
-        DGFS_LAUNCHED(plan);
-        k_to_f32<<<nblk(RS * n, 256), 256>>>(pt.b32, pt.b, RS * n);
-        DGFS_LAUNCHED(plan);
-    }
-    switch (N) {
-    case 8: DGFS_TRY(set_smem_attrs<8>()); break;
-    case 16: DGFS_TRY(set_smem_attrs<16>()); break;
-    case 24: DGFS_TRY(set_smem_attrs<24>()); break;
-    case 32: DGFS_TRY(set_smem_attrs<32>()); break;
-    case 48: DGFS_TRY(set_smem_attrs<48>()); break;
-    }
+    dgfs_status st = ts->fmt == 0 ? build_images<0>(plan, ts) : build_images<1>(plan, ts);
+    if (st != DGFS_OK) return st;
     DGFS_CUDA(cudaDeviceSynchronize());
     return DGFS_OK;
 }
@@ -858,14 +821,8 @@ size_t tc_workspace_bytes(const dgfs_plan_s *plan)
 
 dgfs_status tc_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st)
 {
-    switch (plan->N) {
-    case 8: return collide_n<8>(plan, P, f, Q, st);
-    case 16: return collide_n<16>(plan, P, f, Q, st);
-    case 24: return collide_n<24>(plan, P, f, Q, st);
-    case 32: return collide_n<32>(plan, P, f, Q, st);
-    case 48: return collide_n<48>(plan, P, f, Q, st);
-    default: set_error("N not supported by the tensor-core path"); return DGFS_EUNSUPPORTED;
-    }
+    const TcState *ts = reinterpret_cast<const TcState *>(plan->tc);
+    return ts->fmt == 0 ? dispatch_collide<0>(plan, P, f, Q, st) : dispatch_collide<1>(plan, P, f, Q, st);
 }
 
 // Time candidate launch configurations on the caller's data (each candidate:

@@ -133,3 +133,39 @@ def test_moments_of_fp32_operator():
             ref = O.moments(pb["N"], pb["L"], pb["masses"][p], Q32[0, p, q])
             scale = O.moments(pb["N"], pb["L"], pb["masses"][p], np.abs(Q32[0, p, q]))
             assert np.all(np.abs(mom[0, p, q] - ref) <= 1e-12 * np.abs(scale))
+
+
+TOL_BF16X3 = 1e-3
+
+
+@pytest.mark.parametrize("N,M,Nrho,S,P", [(16, 6, 8, 2, 1), (24, 6, 3, 2, 1), (8, 12, 4, 3, 2)])
+def test_split_bf16_form(N, M, Nrho, S, P):
+    """DGFS_BF16X3: three BF16 terms per operand, six products, FP32
+    accumulation; stated bound 1e-3 relative max-norm (measured near FP32)."""
+    rng = np.random.default_rng(300 + N)
+    masses = [1.0, 2.5, 0.7][:S]
+    pairs = W.pair_params([0.72, 0.8, 0.9][:S], [1.4, 1.0, 1.2][:S], [1.0, 1.1, 0.9][:S])
+    L = 0.5 * N
+    f = np.stack([np.stack([W.two_maxwellians(rng, N, L, m) for m in masses]) for _ in range(P)])
+    pb = dict(N=N, L=L, M=M, Nrho=Nrho, masses=masses, pairs=pairs)
+    Qg, plan = _gpu(pb, f, "bf16x3")
+    Qo = _oracle(pb, f)
+    err = _rel(Qg, Qo)
+    assert err < TOL_BF16X3
+    assert plan.info()["nterms"] == 6
+
+
+def test_split_bf16_c2_and_n48():
+    pb = W.make_problem("c2_slab_n32", points=2)
+    Qg, _ = _gpu(pb, pb["f"], "bf16x3")
+    Qo = _oracle(pb, pb["f"], points=[0, 1])
+    assert _rel(Qg, Qo) < TOL_BF16X3
+    N, L = 48, 12.0
+    rng = np.random.default_rng(481)
+    f = np.stack([W.two_maxwellians(rng, N, L, m) for m in (1.0, 2.0)])[None]
+    pairs = W.pair_params([0.81, 0.81], [1.0, 1.0], [1.0, 1.2])
+    pb = dict(N=N, L=L, M=6, Nrho=3, masses=[1.0, 2.0], pairs=pairs)
+    Qg, _ = _gpu(pb, f, "bf16x3")
+    prob = O.Problem(N, L, 6, 3, [1.0, 2.0], pairs)
+    Qo, _ = prob.pair(0, 1).collide(f[0, 0], f[0, 1])
+    assert _rel(Qg[0, 0, 1], Qo) < TOL_BF16X3
