@@ -128,6 +128,7 @@ def run_ours(args, rank, world):
     import torch
 
     from paper_1903_04670_gb300 import binding as B
+    from paper_1903_04670_gb300 import distributed as D
     from paper_1903_04670_gb300 import workloads as W
 
     torch.cuda.set_device(0 if world == 1 else int(os.environ.get("LOCAL_RANK", rank)))
@@ -181,9 +182,7 @@ def run_ours(args, rank, world):
         launches = plan.launch_count() - n0
         clk = clocks.stop() if clocks else None
         if world > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+            ms = D.max_over_ranks(ms, device="cuda")
         value = world * evals * steps / (ms / 1e3)
         rec = {"value": value, "ms_per_step": ms / steps, "steps": steps, "launches": launches,
                "profile": prof, "plan": plan, "f": f, "Q": Q, "clocks": clk}
