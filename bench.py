@@ -217,7 +217,8 @@ def run_ours(args, rank, world):
         roof = {"bound": "alu", "achieved": work / avg_s / 1e9 if work else None, "peak": peak,
                 "unit": "GFLOP/s", "peak_source": "nominal FP64 of the GB300 (1.25 TFLOP/s)"}
     else:
-        roof = tc_roofline(name, info, P, S, RS, avg_s, peaks, src, cnt / rec["steps"])
+        sigma = plan.pair_tables(0, 0, with_b=False)["sigma"]
+        roof = tc_roofline(name, info, P, S, RS, avg_s, peaks, src, cnt / rec["steps"], sigma)
     roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("achieved") else None
     roof["kernel"] = name
     roof["launches"] = cnt
@@ -274,34 +275,41 @@ def run_ours(args, rank, world):
     return out
 
 
-def tc_executed_flops(name, info, P, S, RS):
+def tc_executed_flops(name, info, P, S, RS, sigma=None):
     """Tensor-core FLOPs a kernel class executes per step (2 M N K per issued
     MMA, padded rows included): M = 128 data rows per CTA, N = 2N outputs,
-    K = N (real input) or 2N (complex input), times the split products."""
+    K = N (real input) or 2N (complex input), times the split products.
+    Translates along an axis where the design direction has no component are
+    the identity and are not issued (sigma: [M][3] design directions)."""
     N = int(info["N"])
     nt = int(info.get("nterms", 3)) or 3
     G = 128 // N
     NO, KR, KC = 2 * N, N, 2 * N
     gem = lambda K: 2.0 * 128 * NO * K * nt
     planes = -(-N // G)
+    if sigma is None:
+        live = [1.0, 1.0, 1.0]
+    else:
+        sg = [list(map(float, v)) for v in sigma]
+        live = [sum(1 for v in sg if v[d] != 0.0) / len(sg) for d in range(3)]
     if name == "tc_stage_a":
-        return S * S * P * planes * RS * 2 * (gem(KR) + gem(KC))
+        return S * S * P * planes * RS * 2 * (live[2] * gem(KR) + live[1] * gem(KC))
     if name == "tc_stage_b":
-        return S * S * P * (-(-N * N // 128)) * RS * 3 * gem(KC)
+        return S * S * P * (-(-N * N // 128)) * RS * (2 * live[0] + 1) * gem(KC)
     if name == "tc_stage_c":
         return S * S * P * planes * RS * 2 * gem(KC)
     return None
 
 
-def tc_roofline(name, info, P, S, RS, avg_s, peaks, src, launches_per_step):
-    flops_step = tc_executed_flops(name, info, P, S, RS)
+def tc_roofline(name, info, P, S, RS, avg_s, peaks, src, launches_per_step, sigma=None):
+    flops_step = tc_executed_flops(name, info, P, S, RS, sigma)
     bf16 = peaks["bf16_tflops"]
     tf32 = bf16 * (1.1 / 2.25)
     ach = flops_step / launches_per_step / avg_s / 1e12 if flops_step else None
     return {"bound": "tensor", "achieved": ach, "peak": tf32, "unit": "TFLOP/s",
             "peak_source": "%s bf16 (%.1f TFLOP/s) x nominal dense tf32/bf16 ratio 1.1/2.25" % (src, bf16),
             "work_per_launch": flops_step / launches_per_step if flops_step else None,
-            "work_unit": "executed tf32 MMA FLOPs (3 split products)"}
+            "work_unit": "executed MMA FLOPs (all split products; identity translates not issued)"}
 
 
 # ------------------------------------------------------------ reference arm

@@ -131,6 +131,15 @@ dgfs_status dgfs_collide_noalloc(dgfs_plan plan, int P, const void *f_dev, void 
  * dgfs_collide_host performs this check itself. */
 dgfs_status dgfs_plan_check(dgfs_plan plan);
 
+/* Self-test of the fault path (instrumentation, no counterpart in the paper):
+ * enqueue a one-block kernel that performs the same bounded mbarrier wait the
+ * tensor-core kernels use, on a barrier that nothing completes (expire != 0)
+ * or that the kernel completes itself (expire == 0).  The expired wait raises
+ * the plan's flag, so the next dgfs_plan_check returns DGFS_ETIMEOUT; the
+ * context stays usable.  Errors: EINVAL, EUNSUPPORTED (FP64 plans have no
+ * device waits), ECUDA. */
+dgfs_status dgfs_plan_selftest_wait(dgfs_plan plan, int expire, void *stream);
+
 /* Adjoint of the bilinear map (f_p, f_q) -> Q^(pq) (bilinearity of Eq. (7)):
  * for an upstream gradient dQ = dL/dQ [P][S][S][n] returns
  *   df[P][S][n]   = sum over pairs of the f_p- and f_q-gradients,

@@ -58,6 +58,7 @@ def lib():
             "dgfs_plan_launch_count": (i, [_P, ctypes.POINTER(ll)]),
             "dgfs_plan_profile": (i, [_P, i]),
             "dgfs_plan_check": (i, [_P]),
+            "dgfs_plan_selftest_wait": (i, [_P, i, _P]),
             "dgfs_relax_step": (i, [_P, i, _P, _P, d, _P]),
             "dgfs_graph_capture": (i, [i, _P, _P, _P, _P, d, i, ctypes.POINTER(_P)]),
             "dgfs_graph_launch": (i, [_P, _P]),
@@ -227,6 +228,10 @@ def dgfs_plan_autotune(h, P, f, Q, stream=None):
     _check(lib().dgfs_plan_autotune(h, int(P), _ptr(f), _ptr(Q), _stream(stream), ctypes.byref(best)),
            "dgfs_plan_autotune")
     return float(best.value)
+
+
+def dgfs_plan_selftest_wait(h, expire, stream=None):
+    _check(lib().dgfs_plan_selftest_wait(h, 1 if expire else 0, _stream(stream)), "dgfs_plan_selftest_wait")
 
 
 def dgfs_plan_check(h):

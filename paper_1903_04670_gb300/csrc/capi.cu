@@ -383,6 +383,14 @@ dgfs_status dgfs_collide_host(dgfs_plan plan, int P, const void *f_host, void *Q
     return tc_check(plan);
 }
 
+dgfs_status dgfs_plan_selftest_wait(dgfs_plan plan, int expire, void *stream)
+{
+    if (!plan) return DGFS_EINVAL;
+    dgfs_status st = entry_check(plan);
+    if (st != DGFS_OK) return st;
+    return tc_selftest_wait(plan, expire, reinterpret_cast<cudaStream_t>(stream));
+}
+
 dgfs_status dgfs_plan_check(dgfs_plan plan)
 {
     if (!plan) return DGFS_EINVAL;

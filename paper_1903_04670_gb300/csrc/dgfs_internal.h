@@ -118,6 +118,7 @@ void tc_release(dgfs_plan_s *plan);
 dgfs_status tc_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st);
 size_t tc_workspace_bytes(const dgfs_plan_s *plan);
 dgfs_status tc_check(dgfs_plan_s *plan);
+dgfs_status tc_selftest_wait(dgfs_plan_s *plan, int expire, cudaStream_t st);
 void tc_info(const dgfs_plan_s *plan, double *info);
 dgfs_status tc_autotune(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st, double *best_ms);
 dgfs_status relax_step(dgfs_plan_s *plan, int P, void *f, const void *Q, double dt, cudaStream_t st);

@@ -60,6 +60,8 @@ struct TcState {
     int chunk_max = 8, rsb_max = 16;
     int groups_a = 2, groups_b = 4;  // CTA groups per (r, s) in stages A and B
     int tuned = 0;
+    uint8_t *idmask = nullptr;  // [RS] bit d set when sigma_{s,d} == 0 (T_d is the identity)
+    int skip_identity = 1;
 };
 
 struct TcArgs {
@@ -72,6 +74,7 @@ struct TcArgs {
     const uint8_t *Fimg;   // [terms][IMGC]
     const float2 *b32;     // [RS][n]
     const double *w;       // [RS]
+    const uint8_t *idmask; // [RS] identity-axis bits (x: 1, y: 2, z: 4), null = none
     int *err;
 };
 
@@ -226,6 +229,7 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs 
     const int rs = blockIdx.y, side = blockIdx.z;
     const long n = a.n;
     const int items = a.Ec * NG;
+    const bool ident_y = a.idmask && (a.idmask[rs] & 2), ident_z = a.idmask && (a.idmask[rs] & 4);
     cta_setup(&tslot, NCOL, mb, NP + 1);
     const uint32_t tb = tslot + pp * 2 * NO, tl = lane_base(tb);
     uint32_t ph_mma = 0, ph_cp = 0;
@@ -260,6 +264,34 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs 
     }
     for (; it < items && ok; it += stride) {
         const int e = it / NG, x0 = (it % NG) * G, nval = min(G, N - x0);
+        if (ident_z) {
+            // sigma_z = 0: T_z = I, the z-pass result is f itself (imaginary part 0)
+            if (ident_y) {  // and T_y = I: A' = f
+                float2 *dst = (side == 0 ? a.Ap : a.Bq) + ((long)e * a.RS + rs) * n + (long)x0 * NN;
+#pragma unroll
+                for (int j = 0; j < FPT; ++j) {
+                    const int i = t + kRows * j;
+                    if (4 * i < nval * NN) {
+                        *reinterpret_cast<float4 *>(dst + 4 * i) = make_float4(pf[j].x, 0.f, pf[j].y, 0.f);
+                        *reinterpret_cast<float4 *>(dst + 4 * i + 2) = make_float4(pf[j].z, 0.f, pf[j].w, 0.f);
+                    }
+                }
+            } else {  // store transposed: row (g, z), complex K = y
+#pragma unroll
+                for (int j = 0; j < FPT; ++j) {
+                    const int i = t + kRows * j;
+                    if (4 * i < nval * NN) {
+                        const int gg = (4 * i) / NN, yy = ((4 * i) / N) % N, zz = (4 * i) % N;
+                        tcfmt::st_c<FMT>(A0, AB, gg * N + zz, yy, pf[j].x, 0.f);
+                        tcfmt::st_c<FMT>(A0, AB, gg * N + zz + 1, yy, pf[j].y, 0.f);
+                        tcfmt::st_c<FMT>(A0, AB, gg * N + zz + 2, yy, pf[j].z, 0.f);
+                        tcfmt::st_c<FMT>(A0, AB, gg * N + zz + 3, yy, pf[j].w, 0.f);
+                    }
+                }
+            }
+            if (it + stride < items) prefetch(it + stride);
+            if (ident_y) continue;
+        } else {
 #pragma unroll
         for (int j = 0; j < FPT; ++j) {
             const int i = t + kRows * j;
@@ -282,6 +314,22 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs 
         }
         ok = run_mma(&mb[pp], ph_mma, bar, [&] { tcfmt::gemm<FMT>(tb, A0, AB, Bz, IR, NO, KR, a.nterms); });
         if (!ok) break;
+        if (ident_y) {
+            // sigma_y = 0: T_y = I, row t = (g, y) already holds A'(x0+g, y, z') for all z'
+            float2 *dst = (side == 0 ? a.Ap : a.Bq) + ((long)e * a.RS + rs) * n + (long)(x0 + g) * NN + yl * N;
+#pragma unroll
+            for (int c0 = 0; c0 < NO; c0 += 16) {
+                float v[16];
+                tmem_ld16(tl + c0, v);
+                if (t < nval * N) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        *reinterpret_cast<float4 *>(dst + c0 / 2 + 2 * j) =
+                            make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                }
+            }
+            continue;
+        }
         // transpose within each plane: row (g, y) holds z' -> rows (g, z'), K = y
 #pragma unroll
         for (int c0 = 0; c0 < NO; c0 += 16) {
@@ -293,6 +341,7 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs 
                     tcfmt::st_c<FMT>(A0, AB, g * N + c0 / 2 + j, yl, v[2 * j], v[2 * j + 1]);
             }
         }
+        }  // z-pass
         if (!RESIDENT) {
             load_imgs(1);
             ok = wait_copy_pipe(&mb[NP], ph_cp, bar);
@@ -338,6 +387,7 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b(TcArgs 
     const int rs = blockIdx.y;
     const long n = a.n;
     const int items = a.Ec * NT_TILES;
+    const bool ident_x = a.idmask && (a.idmask[rs] & 1);
     cta_setup(&tslot, NCOL, mb, NP + 1);
     const uint32_t tb = tslot + pp * 3 * NO, tl = lane_base(tb);
     uint32_t ph_mma = 0, ph_cp = 0;
@@ -371,9 +421,25 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b(TcArgs 
         const int e = it / NT_TILES, p0 = (it % NT_TILES) * kRows;
         const bool valid = p0 + t < NN;
         const long gbase = ((long)e * a.RS + rs) * n + p0 + t;
+        float2 pb[N];
+        if (ident_x) {
+            // sigma_x = 0: T^p_x = T^q_x = I, so P = A' . B' directly
+            load_pencil(pb, a.Bq + gbase, valid);
+#pragma unroll
+            for (int x = 0; x < N; x += 2) {
+                const float2 u = make_float2(pa[x].x * pb[x].x - pa[x].y * pb[x].y, pa[x].x * pb[x].y + pa[x].y * pb[x].x);
+                const float2 v = make_float2(pa[x + 1].x * pb[x + 1].x - pa[x + 1].y * pb[x + 1].y,
+                                             pa[x + 1].x * pb[x + 1].y + pa[x + 1].y * pb[x + 1].x);
+                tcfmt::st_c2<FMT>(A0, AB, t, x, u, v);
+            }
+            const int nx = it + stride;
+            if (nx < items) {
+                const int e2 = nx / NT_TILES, q0 = (nx % NT_TILES) * kRows;
+                load_pencil(pa, a.Ap + ((long)e2 * a.RS + rs) * n + q0 + t, q0 + t < NN);
+            }
+        } else {
 #pragma unroll
         for (int x = 0; x < N; x += 2) tcfmt::st_c2<FMT>(A0, AB, t, x, pa[x], pa[x + 1]);
-        float2 pb[N];
         load_pencil(pb, a.Bq + gbase, valid);
         if (!RESIDENT) {
             load_images(0, 1);
@@ -412,6 +478,7 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b(TcArgs 
                 tcfmt::st_c2<FMT>(A0, AB, t, c0 / 2 + j, p0v, p1v);
             }
         }
+        }  // translates along x
         if (!RESIDENT) {
             load_images(2, 1);
             ok = wait_copy_pipe(&mb[NP], ph_cp, bar);
@@ -674,6 +741,7 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
             a.timg = reinterpret_cast<const uint8_t *>(pt.tmat);
             a.b32 = pt.b32;
             a.w = pt.w;
+            a.idmask = ts->skip_identity ? ts->idmask : nullptr;
             for (int pt0 = 0; pt0 < P; pt0 += E) {
                 const int Ec = std::min(E, P - pt0);
                 a.pt0 = pt0;
@@ -769,6 +837,20 @@ dgfs_status build_images(dgfs_plan_s *plan, TcState *ts)
 
 bool tc_supported_N(int N) { return N == 8 || N == 16 || N == 24 || N == 32 || N == 48; }
 
+// The kernels' bounded-wait path on an mbarrier that nothing completes
+// (expire != 0) or that the kernel completes itself (expire == 0).
+__global__ void k_wait_selftest(int *err, int expire, long polls)
+{
+    __shared__ uint64_t mb;
+    if (threadIdx.x == 0) mbar_init(&mb, 1);
+    __syncthreads();
+    if (!expire && threadIdx.x == 0)
+        asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(smem_u32(&mb))
+                     : "memory");
+    const bool ok = mbar_wait(&mb, 0, polls);
+    if (!__syncthreads_and(ok ? 1 : 0) && threadIdx.x == 0) atomicExch(err, kErrTimeout);
+}
+
 }  // namespace
 
 dgfs_status tc_prepare(dgfs_plan_s *plan)
@@ -793,6 +875,17 @@ dgfs_status tc_prepare(dgfs_plan_s *plan)
     ts->groups_b = std::max(1, (4 * sms + RS / 2) / RS);
     DGFS_CUDA(cudaMalloc(&ts->err, sizeof(int)));
     DGFS_CUDA(cudaMemset(ts->err, 0, sizeof(int)));
+    // axes along which the design direction has no component: the translate
+    // there is exp(i 0) = 1 in k-space, i.e. the identity, and is skipped
+    {
+        std::vector<uint8_t> mask(RS);
+        for (int rs = 0; rs < RS; ++rs) {
+            const double *sg = plan->sigma + 3 * (rs % plan->M);
+            mask[rs] = (uint8_t)((sg[0] == 0.0 ? 1 : 0) | (sg[1] == 0.0 ? 2 : 0) | (sg[2] == 0.0 ? 4 : 0));
+        }
+        DGFS_CUDA(cudaMalloc(&ts->idmask, RS));
+        DGFS_CUDA(cudaMemcpy(ts->idmask, mask.data(), RS, cudaMemcpyHostToDevice));
+    }
     dgfs_status st = ts->fmt == 0 ? build_images<0>(plan, ts) : build_images<1>(plan, ts);
     if (st != DGFS_OK) return st;
     DGFS_CUDA(cudaDeviceSynchronize());
@@ -805,6 +898,7 @@ void tc_release(dgfs_plan_s *plan)
     if (!ts) return;
     cudaFree(ts->Fimg);
     cudaFree(ts->err);
+    cudaFree(ts->idmask);
     delete ts;
     plan->tc = nullptr;
 }
@@ -903,6 +997,18 @@ void tc_info(const dgfs_plan_s *plan, double *info)
     info[12] = ts->groups_a;
     info[13] = ts->groups_b;
     info[14] = ts->tuned;
+}
+
+dgfs_status tc_selftest_wait(dgfs_plan_s *plan, int expire, cudaStream_t st)
+{
+    TcState *ts = reinterpret_cast<TcState *>(plan->tc);
+    if (!ts) {
+        set_error("dgfs_plan_selftest_wait: only tensor-core plans have bounded device waits");
+        return DGFS_EUNSUPPORTED;
+    }
+    k_wait_selftest<<<1, 32, 0, st>>>(ts->err, expire, 4096);
+    DGFS_LAUNCHED(plan);
+    return DGFS_OK;
 }
 
 dgfs_status tc_check(dgfs_plan_s *plan)
