@@ -224,11 +224,33 @@ def run_ours(args, rank, world):
     roof["launches"] = cnt
     roof["avg_launch_ms"] = tot_ms / cnt
     roof["share_of_step"] = tot_ms / sum(v[1] for v in prof.values())
-    roof["traffic"] = None
+    roof["traffic"] = ncu_traffic(name, P)
     out["roofline"] = roof
     out["kernels"] = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in prof.items()}
     out["gpu_launches"] = rec["launches"]
     out["clocks"] = rec["clocks"]
+
+    # the same call replayed from one CUDA graph: the host-side scheduling cost
+    if not args.no_graph:
+        g = B.dgfs_graph_capture([plan._h], [P], [rec["f"]], [rec["Q"]])
+        try:
+            for _ in range(2):
+                B.dgfs_graph_launch(g, stream)
+            torch.cuda.synchronize()
+            gsteps = max(2, min(rec["steps"], 20))
+            gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(gsteps)]
+            for k in range(gsteps):
+                flush.zero_()
+                gev[k][0].record(stream)
+                B.dgfs_graph_launch(g, stream)
+                gev[k][1].record(stream)
+            torch.cuda.synchronize()
+            gms = sum(a.elapsed_time(b) for a, b in gev) / gsteps
+            out["graph"] = {"ms_per_step": gms, "eager_ms_per_step": rec["ms_per_step"], "steps": gsteps,
+                            "kernels_per_replay": B.dgfs_graph_kernel_count(g)}
+        finally:
+            B.dgfs_graph_destroy(g)
 
     # end to end through the host-buffer C-ABI call (pinned host memory)
     if not args.no_e2e:
@@ -301,6 +323,18 @@ def tc_executed_flops(name, info, P, S, RS, sigma=None):
     return None
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the stage kernels of the
+# 3xTF32 form at N = 32, M = 12, N_rho = 8 from one ncu capture on 8 points (one species
+# pair per launch); A', B' and H are per point, so the bytes scale with the points per launch.
+NCU_TRAFFIC_8PT = {"tc_stage_a": 355.3e6, "tc_stage_b": 578.7e6, "tc_stage_c": 264.2e6}
+
+
+def ncu_traffic(name, P):
+    if WORKLOAD != "c2_slab_n32" or name not in NCU_TRAFFIC_8PT:
+        return None
+    return NCU_TRAFFIC_8PT[name] * min(P, 24) / 8.0
+
+
 def tc_roofline(name, info, P, S, RS, avg_s, peaks, src, launches_per_step, sigma=None):
     flops_step = tc_executed_flops(name, info, P, S, RS, sigma)
     bf16 = peaks["bf16_tflops"]
@@ -356,6 +390,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "fp32_tc", "tf32", "bf16x3"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--points", type=int, default=None,

@@ -60,7 +60,7 @@ struct TcState {
     int chunk_max = 8, rsb_max = 16;
     int groups_a = 2, groups_b = 4;  // CTA groups per (r, s) in stages A and B
     int tuned = 0;
-    uint8_t *idmask = nullptr;  // [RS] bit d set when sigma_{s,d} == 0 (T_d is the identity)
+    uint8_t *idmask = nullptr;  // [RS] bit d set when sigma_{s,d} == 0 (T_d is the identity; x and y are skipped)
     int skip_identity = 1;
 };
 
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs 
     const int rs = blockIdx.y, side = blockIdx.z;
     const long n = a.n;
     const int items = a.Ec * NG;
-    const bool ident_y = a.idmask && (a.idmask[rs] & 2), ident_z = a.idmask && (a.idmask[rs] & 4);
+    const bool ident_y = a.idmask && (a.idmask[rs] & 2);
     cta_setup(&tslot, NCOL, mb, NP + 1);
     const uint32_t tb = tslot + pp * 2 * NO, tl = lane_base(tb);
     uint32_t ph_mma = 0, ph_cp = 0;
@@ -264,34 +264,6 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs 
     }
     for (; it < items && ok; it += stride) {
         const int e = it / NG, x0 = (it % NG) * G, nval = min(G, N - x0);
-        if (ident_z) {
-            // sigma_z = 0: T_z = I, the z-pass result is f itself (imaginary part 0)
-            if (ident_y) {  // and T_y = I: A' = f
-                float2 *dst = (side == 0 ? a.Ap : a.Bq) + ((long)e * a.RS + rs) * n + (long)x0 * NN;
-#pragma unroll
-                for (int j = 0; j < FPT; ++j) {
-                    const int i = t + kRows * j;
-                    if (4 * i < nval * NN) {
-                        *reinterpret_cast<float4 *>(dst + 4 * i) = make_float4(pf[j].x, 0.f, pf[j].y, 0.f);
-                        *reinterpret_cast<float4 *>(dst + 4 * i + 2) = make_float4(pf[j].z, 0.f, pf[j].w, 0.f);
-                    }
-                }
-            } else {  // store transposed: row (g, z), complex K = y
-#pragma unroll
-                for (int j = 0; j < FPT; ++j) {
-                    const int i = t + kRows * j;
-                    if (4 * i < nval * NN) {
-                        const int gg = (4 * i) / NN, yy = ((4 * i) / N) % N, zz = (4 * i) % N;
-                        tcfmt::st_c<FMT>(A0, AB, gg * N + zz, yy, pf[j].x, 0.f);
-                        tcfmt::st_c<FMT>(A0, AB, gg * N + zz + 1, yy, pf[j].y, 0.f);
-                        tcfmt::st_c<FMT>(A0, AB, gg * N + zz + 2, yy, pf[j].z, 0.f);
-                        tcfmt::st_c<FMT>(A0, AB, gg * N + zz + 3, yy, pf[j].w, 0.f);
-                    }
-                }
-            }
-            if (it + stride < items) prefetch(it + stride);
-            if (ident_y) continue;
-        } else {
 #pragma unroll
         for (int j = 0; j < FPT; ++j) {
             const int i = t + kRows * j;
@@ -341,7 +313,6 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs 
                     tcfmt::st_c<FMT>(A0, AB, g * N + c0 / 2 + j, yl, v[2 * j], v[2 * j + 1]);
             }
         }
-        }  // z-pass
         if (!RESIDENT) {
             load_imgs(1);
             ok = wait_copy_pipe(&mb[NP], ph_cp, bar);
