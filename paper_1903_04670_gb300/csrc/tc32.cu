@@ -289,30 +289,24 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs 
         if (ident_y) {
             // sigma_y = 0: T_y = I, row t = (g, y) already holds A'(x0+g, y, z') for all z'
             float2 *dst = (side == 0 ? a.Ap : a.Bq) + ((long)e * a.RS + rs) * n + (long)(x0 + g) * NN + yl * N;
-#pragma unroll
-            for (int c0 = 0; c0 < NO; c0 += 16) {
-                float v[16];
-                tmem_ld16(tl + c0, v);
+            tmem_visit<NO>(tl, [&](int c0, const float *v) {
                 if (t < nval * N) {
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
                         *reinterpret_cast<float4 *>(dst + c0 / 2 + 2 * j) =
                             make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                 }
-            }
+            });
             continue;
         }
         // transpose within each plane: row (g, y) holds z' -> rows (g, z'), K = y
-#pragma unroll
-        for (int c0 = 0; c0 < NO; c0 += 16) {
-            float v[16];
-            tmem_ld16(tl + c0, v);
+        tmem_visit<NO>(tl, [&](int c0, const float *v) {
             if (t < nval * N) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
                     tcfmt::st_c<FMT>(A0, AB, g * N + c0 / 2 + j, yl, v[2 * j], v[2 * j + 1]);
             }
-        }
+        });
         if (!RESIDENT) {
             load_imgs(1);
             ok = wait_copy_pipe(&mb[NP], ph_cp, bar);
@@ -322,15 +316,12 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs 
         if (!ok) break;
         // row t = (g, z'): y' values -> global [x][y'][z']
         float2 *dst = (side == 0 ? a.Ap : a.Bq) + ((long)e * a.RS + rs) * n + (long)(x0 + g) * NN + yl;
-#pragma unroll
-        for (int c0 = 0; c0 < NO; c0 += 16) {
-            float v[16];
-            tmem_ld16(tl + NO + c0, v);
+        tmem_visit<NO>(tl + NO, [&](int c0, const float *v) {
             if (t < nval * N) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) dst[(long)(c0 / 2 + j) * N] = make_float2(v[2 * j], v[2 * j + 1]);
             }
-        }
+        });
     }
     cta_teardown(tslot, NCOL, ok, a.err);
 }
@@ -438,8 +429,7 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b(TcArgs 
 #pragma unroll
         for (int c0 = 0; c0 < NO; c0 += 16) {
             float va[16], vb[16];
-            tmem_ld16(tl + c0, va);
-            tmem_ld16(tl + NO + c0, vb);
+            tmem_ld16x2(tl + c0, tl + NO + c0, va, vb);
 #pragma unroll
             for (int j = 0; j < 8; j += 2) {
                 const float2 p0v = make_float2(va[2 * j] * vb[2 * j] - va[2 * j + 1] * vb[2 * j + 1],
@@ -459,15 +449,12 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b(TcArgs 
                      [&] { tcfmt::gemm<FMT>(tb + 2 * NO, A0, AB, slot(2), IC, NO, KC, a.nterms); });
         if (!ok) break;
         float2 *dst = a.H + gbase;
-#pragma unroll
-        for (int c0 = 0; c0 < NO; c0 += 16) {
-            float v[16];
-            tmem_ld16(tl + 2 * NO + c0, v);
+        tmem_visit<NO>(tl + 2 * NO, [&](int c0, const float *v) {
             if (valid) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) dst[(long)(c0 / 2 + j) * NN] = make_float2(v[2 * j], v[2 * j + 1]);
             }
-        }
+        });
     }
     cta_teardown(tslot, NCOL, ok, a.err);
 }
@@ -544,25 +531,19 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::C, 1) k_stage_c(TcArgs 
         }
         ok = run_mma(&mb[pp], ph_mma, bar, [&] { tcfmt::gemm<FMT>(tb, A0, AB, Bf, IC, NO, KC, a.nterms); });
         if (!ok) break;
-#pragma unroll
-        for (int c0 = 0; c0 < NO; c0 += 16) {
-            float v[16];
-            tmem_ld16(tl + c0, v);
+        tmem_visit<NO>(tl, [&](int c0, const float *v) {
             if (t < nval * N) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
                     tcfmt::st_c<FMT>(A0, AB, g * N + c0 / 2 + j, yl, v[2 * j], v[2 * j + 1]);
             }
-        }
+        });
         ok = run_mma(&mb[pp], ph_mma, bar, [&] { tcfmt::gemm<FMT>(tb + NO, A0, AB, Bf, IC, NO, KC, a.nterms); });
         if (!ok) break;
         // row t = (g, kz): t3(kx0+g, ky, kz) for all ky
         const float wr = (float)a.w[rs];
         const float2 *brs = a.b32 + (long)rs * n + (long)(x0 + g) * NN + yl;
-#pragma unroll
-        for (int c0 = 0; c0 < NO; c0 += 16) {
-            float v[16];
-            tmem_ld16(tl + NO + c0, v);
+        tmem_visit<NO>(tl + NO, [&](int c0, const float *v) {
             if (t < nval * N) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
@@ -573,7 +554,7 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::C, 1) k_stage_c(TcArgs 
                     acc[ky].y = fmaf(wr, bb.x * ti + bb.y * tr, acc[ky].y);
                 }
             }
-        }
+        });
     }
     if (ok && rb < a.rsb && t < nval * N) {
         float2 *dst = a.QGp + ((long)e * a.rsb + rb) * n + (long)(x0 + g) * NN + yl;

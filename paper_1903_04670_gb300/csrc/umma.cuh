@@ -129,6 +129,58 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Two 16-column TMEM loads (any two column offsets of this lane) completed by
+// one wait; the wait names the destination registers so that no use of them
+// can be scheduled before it.
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float *va, float *vb)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(ta));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+          "=r"(r[30]), "=r"(r[31])
+        : "r"(tb));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        va[j] = __uint_as_float(r[j]);
+        vb[j] = __uint_as_float(r[16 + j]);
+    }
+}
+
+// Visit NO consecutive FP32 columns of this lane in chunks of 16 columns,
+// f(c0, v) with v[j] = column c0 + j; two chunks share one wait.
+template <int NO, typename F>
+__device__ __forceinline__ void tmem_visit(uint32_t taddr, F &&f)
+{
+#pragma unroll
+    for (int c0 = 0; c0 < NO; c0 += 32) {
+        if (c0 + 32 <= NO) {
+            float a[16], b[16];
+            tmem_ld16x2(taddr + c0, taddr + c0 + 16, a, b);
+            f(c0, a);
+            f(c0 + 16, b);
+        } else {
+            float a[16];
+            tmem_ld16(taddr + c0, a);
+            f(c0, a);
+        }
+    }
+}
+
 // round-to-nearest TF32 value of x (low 13 mantissa bits cleared)
 __device__ __forceinline__ float tf32_rna(float x)
 {
