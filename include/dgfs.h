@@ -37,6 +37,7 @@ extern "C" {
 
 typedef struct dgfs_plan_s *dgfs_plan;
 typedef struct dgfs_graph_s *dgfs_graph;
+typedef struct dgfs_dg_s *dgfs_dg;
 
 typedef enum {
     DGFS_OK = 0,
@@ -227,6 +228,58 @@ dgfs_status dgfs_plan_profile(dgfs_plan plan, int enable);
  * Returns EINVAL if slots ran out (the totals then cover the first 16384). */
 dgfs_status dgfs_plan_profile_read(dgfs_plan plan, int max_classes, char *names, long long *counts,
                                    double *total_ms, int *n_classes);
+
+/* ---- 1-D DG transport around the operator (Eq. (1); Sec. 3) --------------
+ * Eq. (1), df_p/dt + c . grad_x f_p = sum_q Q^(pq)(f_p, f_q), is solved in the
+ * paper by Runge-Kutta discontinuous Galerkin in one space dimension with
+ * purely diffuse walls (Sec. 3, Couette case of Table 2); the paper defers the
+ * formulas to its references, and these entry points implement the textbook
+ * nodal scheme:
+ *  - Ne equal elements on [x0, x1], K Gauss-Legendre nodes per element (DG
+ *    order K); point index e*K + j (element-major), so f[P][S][n] with
+ *    P = Ne*K uses the collision layout;
+ *  - weak form with the nodes as quadrature and the upwind flux c_x f:
+ *      J w_i df_i/dt = c_x sum_j w_j phi_i'(xi_j) f_j - phi_i(+1) F_R + phi_i(-1) F_L,
+ *    J = (x1 - x0) / (2 Ne);
+ *  - diffuse walls: velocities entering the domain see n_w M_w(c), with
+ *    M_w = (m_p/(pi T_w))^{3/2} exp(-m_p |c - u_w|^2 / T_w) and n_w set so
+ *    that the discrete net mass flux sum_c c_x f(c) through the wall is zero;
+ *  - time: three-stage SSP Runge-Kutta (Shu-Osher form).
+ * The DG object keeps a non-owning reference to its plan (which must outlive
+ * it), its stage buffers and its wall tables; calls on one DG object or on
+ * its plan must not overlap. */
+
+/* Create the DG discretisation for a plan.
+ *   walls : host double[8] = {T, ux, uy, uz} of the left wall (x = x0), then
+ *           of the right wall (x = x1); T > 0.
+ *   1 <= K <= 5, Ne >= 1, Ne*K <= the plan's max_points, x1 > x0, S <= 4.
+ * Allocates the stage buffers (two of [P][S][n] and one of [P][S][S][n], in
+ * the plan's element type).  Synchronous.  Errors: EINVAL, ENOMEM, ECUDA. */
+dgfs_status dgfs_dg_create(dgfs_dg *out, dgfs_plan plan, int Ne, int K, double x0, double x1,
+                           const double *walls);
+
+/* Release a DG object (NULL accepted).  Synchronises its device. */
+dgfs_status dgfs_dg_destroy(dgfs_dg dg);
+
+/* Physical positions of the P = Ne*K points: host double[P]. */
+dgfs_status dgfs_dg_nodes(dgfs_dg dg, double *x_host);
+
+/* Right-hand side of Eq. (1) in the DG weak form:
+ *   rhs = -c_x df/dx (upwind DG, diffuse walls) + sum_q Q[pt][p][q]
+ *   f_dev   : device [P][S][n] (P = Ne*K), the plan's element type.
+ *   Q_dev   : device [P][S][S][n] collision results, or NULL for transport only.
+ *   rhs_dev : device [P][S][n] output; must not alias f_dev.
+ * Two kernels (wall-flux reduction, nodal right-hand sides), accumulated in
+ * FP64.  Asynchronous.  Errors: EINVAL, ECUDA. */
+dgfs_status dgfs_dg_rhs(dgfs_dg dg, const void *f_dev, const void *Q_dev, void *rhs_dev, void *stream);
+
+/* One SSP-RK3 step of Eq. (1) in place on f_dev [P][S][n]:
+ *   f1 = f + dt L(f); f2 = 3/4 f + 1/4 (f1 + dt L(f1)); f = 1/3 f + 2/3 (f2 + dt L(f2)),
+ * L(g) = dgfs_dg_rhs(g, with_collisions ? dgfs_collide(g) : NULL).
+ * With collisions, each stage calls the plan's collision operator on all P
+ * points (the step then takes the plan's precision form).  No allocation;
+ * graph-capturable.  Asynchronous.  Errors: EINVAL, ECUDA, ETIMEOUT. */
+dgfs_status dgfs_dg_step(dgfs_dg dg, void *f_dev, double dt, int with_collisions, void *stream);
 
 /* Static strings; never NULL. */
 const char *dgfs_status_string(dgfs_status s);

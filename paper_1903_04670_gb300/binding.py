@@ -66,6 +66,11 @@ def lib():
             "dgfs_graph_destroy": (i, [_P]),
             "dgfs_plan_autotune": (i, [_P, i, _P, _P, _P, ctypes.POINTER(d)]),
             "dgfs_plan_profile_read": (i, [_P, i, _P, _P, _P, ctypes.POINTER(i)]),
+            "dgfs_dg_create": (i, [ctypes.POINTER(_P), _P, i, i, d, d, _P]),
+            "dgfs_dg_destroy": (i, [_P]),
+            "dgfs_dg_nodes": (i, [_P, _P]),
+            "dgfs_dg_rhs": (i, [_P, _P, _P, _P, _P]),
+            "dgfs_dg_step": (i, [_P, _P, d, i, _P]),
             "dgfs_status_string": (ctypes.c_char_p, [i]),
             "dgfs_last_error": (ctypes.c_char_p, []),
             "dgfs_version": (ctypes.c_char_p, []),
@@ -344,3 +349,71 @@ class Plan:
 
     def profile_read(self):
         return dgfs_plan_profile_read(self._h)
+
+
+# ------------------------------------------------------------ 1-D DG transport
+def dgfs_dg_create(plan_h, Ne, K, x0, x1, walls):
+    """walls: ((T_left, (ux, uy, uz)), (T_right, (ux, uy, uz)))."""
+    import numpy as np
+    w = np.array([walls[0][0], *walls[0][1], walls[1][0], *walls[1][1]], dtype=np.float64)
+    h = _P()
+    _check(lib().dgfs_dg_create(ctypes.byref(h), plan_h, int(Ne), int(K), float(x0), float(x1),
+                                w.ctypes.data_as(_P)), "dgfs_dg_create")
+    return h
+
+
+def dgfs_dg_destroy(h):
+    _check(lib().dgfs_dg_destroy(h), "dgfs_dg_destroy")
+
+
+def dgfs_dg_nodes(h, P):
+    import numpy as np
+    x = np.empty(P)
+    _check(lib().dgfs_dg_nodes(h, x.ctypes.data_as(_P)), "dgfs_dg_nodes")
+    return x
+
+
+def dgfs_dg_rhs(h, f, Q, rhs, stream=None):
+    _check(lib().dgfs_dg_rhs(h, _ptr(f), _ptr(Q) if Q is not None else None, _ptr(rhs), _stream(stream)),
+           "dgfs_dg_rhs")
+
+
+def dgfs_dg_step(h, f, dt, with_collisions=True, stream=None):
+    _check(lib().dgfs_dg_step(h, _ptr(f), float(dt), int(bool(with_collisions)), _stream(stream)), "dgfs_dg_step")
+
+
+class Slab:
+    """Owns a DG discretisation of [x0, x1] (Ne elements x K Gauss nodes) built on a Plan."""
+
+    def __init__(self, plan, Ne, K, x0, x1, walls):
+        self.plan, self.Ne, self.K = plan, int(Ne), int(K)
+        self.P = self.Ne * self.K
+        self._h = dgfs_dg_create(plan._h, Ne, K, x0, x1, walls)
+        self.x = dgfs_dg_nodes(self._h, self.P)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            try:
+                dgfs_dg_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def _check_f(self, f):
+        p = self.plan
+        shape = (self.P, p.S, p.N, p.N, p.N)
+        if tuple(f.shape) != shape or f.dtype != p.dtype or not f.is_cuda or not f.is_contiguous():
+            raise ValueError("f must be a contiguous %s CUDA tensor of shape %s" % (p.dtype, shape))
+
+    def rhs(self, f, Q=None, out=None):
+        self._check_f(f)
+        if out is None:
+            out = torch.empty_like(f)
+        dgfs_dg_rhs(self._h, f, Q, out)
+        return out
+
+    def step(self, f, dt, with_collisions=True):
+        self._check_f(f)
+        dgfs_dg_step(self._h, f, dt, with_collisions)
+        return f

@@ -194,6 +194,11 @@ dgfs_status entry_check(dgfs_plan_s *plan)
 
 dgfs_status plan_entry_check(dgfs_plan_s *plan) { return entry_check(plan); }
 
+void host_gauss_legendre(int n, double a, double b, std::vector<double> &x, std::vector<double> &w)
+{
+    gauss_legendre(n, a, b, x, w);
+}
+
 }  // namespace dgfs
 
 using namespace dgfs;

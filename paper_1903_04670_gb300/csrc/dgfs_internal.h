@@ -96,6 +96,8 @@ class ProfScope {
     cudaStream_t st_;
 };
 
+// capi.cu: Gauss-Legendre nodes (increasing) and weights on [a, b]
+void host_gauss_legendre(int n, double a, double b, std::vector<double> &x, std::vector<double> &w);
 // tables.cu
 dgfs_status build_tables(dgfs_plan_s *plan);
 // fft64.cu
