@@ -252,6 +252,42 @@ def run_ours(args, rank, world):
         finally:
             B.dgfs_graph_destroy(g)
 
+    # one SSP-RK3 step of the 1-D DG heat-transfer slab around the operator:
+    # transport kernels plus three collision calls on all 48 points
+    if not args.no_dg:
+        sp = W.make_problem("c5_heat_slab_n32")
+        splan = B.Plan(sp["N"], sp["L"], sp["M"], sp["Nrho"], sp["masses"], sp["pairs"], main,
+                       sp["f"].shape[0], dev)
+        slab = B.Slab(splan, sp["elements"], sp["order"], 0.0, 1.0, sp["walls"])
+        fs = torch.from_numpy(sp["f"]).to("cuda", splan.dtype)
+        dt = 1e-3  # below the SSP-RK3 / DG(K=3) CFL limit h_x / (5 max|c_x|) = 1.6e-3
+        for _ in range(3):
+            slab.step(fs, dt)
+        torch.cuda.synchronize()
+        dsteps = 10
+        splan.profile(True)
+        dev_ = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(dsteps)]
+        for k in range(dsteps):
+            flush.zero_()
+            dev_[k][0].record(stream)
+            slab.step(fs, dt)
+            dev_[k][1].record(stream)
+        torch.cuda.synchronize()
+        dms = sum(a.elapsed_time(b) for a, b in dev_) / dsteps
+        dprof = splan.profile_read()
+        splan.profile(False)
+        tr = sum(v[1] for k, v in dprof.items() if k.startswith("dg_")) / dsteps
+        co = sum(v[1] for k, v in dprof.items() if not k.startswith("dg_")) / dsteps
+        nev = 3 * sp["f"].shape[0] * S * S
+        out["dg_step"] = {"workload": "c5_heat_slab_n32",
+                          "description": "16 elements x 3 Gauss points, 2 species (m = 1, 2), VHS omega = 0.81, "
+                                         "N = 32 on [-8, 8]^3, M = 12, N_rho = 8, diffuse walls at T = 1 and "
+                                         "T = 2; SSP-RK3, dt = 1e-3",
+                          "precision": main, "steps": dsteps, "ms_per_step": dms,
+                          "collision_evals_per_step": nev, "evals_per_s": nev / (dms / 1e3),
+                          "transport_kernel_ms_per_step": tr, "collision_kernel_ms_per_step": co}
+        del slab, splan
+
     # end to end through the host-buffer C-ABI call (pinned host memory)
     if not args.no_e2e:
         es = 8 if main == "fp64" else 4
@@ -391,6 +427,7 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "fp32_tc", "tf32", "bf16x3"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-dg", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--points", type=int, default=None,

@@ -16,7 +16,8 @@
 //  - SSP-RK3 in Shu-Osher form with L(f) = streaming(f) + sum_q Q^(pq)(f).
 //
 // Work per stage: one deterministic reduction of the outgoing wall fluxes
-// (one block per wall and species) and one elementwise kernel over
+// (32 blocks per wall and species, partials added in a fixed order) and one
+// elementwise kernel over
 // (element, species, velocity) that forms the K nodal right-hand sides and
 // the Runge-Kutta combination in registers.  Both are HBM-bound.
 #include <cmath>
@@ -36,7 +37,7 @@ struct dgfs_dg_s {
     double tL[5] = {0}, tR[5] = {0};  // phi_j(-1), phi_j(+1): traces
     std::vector<double> inflow;    // [2][S] sum over entering velocities of c_x M_w
     double *Mw = nullptr;          // device [2][S][n] unit-density wall Maxwellians
-    double *wsum = nullptr;        // device [2][S] outgoing flux sums
+    double *wsum = nullptr;        // device [2][S][chunks] partial outgoing flux sums
     void *f1 = nullptr, *f2 = nullptr, *Q = nullptr;  // SSP-RK3 stage buffers
 };
 
@@ -56,16 +57,22 @@ __device__ __forceinline__ double cx_of(long v, int N, double L)
     return -L + (ix + 0.5) * (2.0 * L / N);
 }
 
-// Outgoing mass-flux sums at the two walls: block (side, p) reduces
-// sum_{c leaving the domain} c_x f_trace(c) over the n velocities in a fixed
-// order.  Left wall: trace of element 0 at xi = -1, leaving = c_x < 0.
+constexpr int kWallChunks = 32;  // blocks per (wall, species) in the flux reduction
+
+// Outgoing mass-flux sums at the two walls: block (side, p, chunk) reduces
+// sum_{c leaving the domain} c_x f_trace(c) over its contiguous share of the
+// n velocities in a fixed order and writes one partial sum; the partials are
+// added in chunk order where they are used.  Left wall: trace of element 0
+// at xi = -1, leaving = c_x < 0.
 template <typename T, int K>
 __global__ void k_wall_out(const T *f, DgCoef cf, int Ne, int S, int N, double L, long n, double *wsum)
 {
     const int side = blockIdx.x, p = blockIdx.y;
     const int e = side == 0 ? 0 : Ne - 1;
+    const long per = (n + kWallChunks - 1) / kWallChunks;
+    const long v0 = blockIdx.z * per, v1 = min(n, v0 + per);
     double acc = 0.0;
-    for (long v = threadIdx.x; v < n; v += blockDim.x) {
+    for (long v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
         const double cx = cx_of(v, N, L);
         if (side == 0 ? cx < 0.0 : cx > 0.0) {
             double u = 0.0;
@@ -82,7 +89,15 @@ __global__ void k_wall_out(const T *f, DgCoef cf, int Ne, int S, int N, double L
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) wsum[side * S + p] = red[0];
+    if (threadIdx.x == 0) wsum[(side * S + p) * kWallChunks + blockIdx.z] = red[0];
+}
+
+__device__ __forceinline__ double wall_sum(const double *wsum, int side, int S, int p)
+{
+    const double *w = wsum + (side * S + p) * kWallChunks;
+    double s = 0.0;
+    for (int i = 0; i < kWallChunks; ++i) s += w[i];
+    return s;
 }
 
 // One thread per (element, species, velocity): the K nodal right-hand sides
@@ -117,7 +132,7 @@ __global__ void k_dg(const T *f, const T *Q, const T *f0, T *out, DgCoef cf, con
 #pragma unroll
             for (int j = 0; j < K; ++j) up += cf.tR[j] * (double)f[at((e - 1) * K + j)];
         } else {
-            up = -wsum[p] * cf.nwL[p] * Mw[(long)p * n + v];
+            up = -wall_sum(wsum, 0, S, p) * cf.nwL[p] * Mw[(long)p * n + v];
         }
         FL = cx * up;
         FR = cx * uR_in;
@@ -128,7 +143,7 @@ __global__ void k_dg(const T *f, const T *Q, const T *f0, T *out, DgCoef cf, con
 #pragma unroll
             for (int j = 0; j < K; ++j) dn += cf.tL[j] * (double)f[at((e + 1) * K + j)];
         } else {
-            dn = -wsum[S + p] * cf.nwR[p] * Mw[((long)S + p) * n + v];
+            dn = -wall_sum(wsum, 1, S, p) * cf.nwR[p] * Mw[((long)S + p) * n + v];
         }
         FL = cx * uL_in;
         FR = cx * dn;
@@ -181,7 +196,7 @@ dgfs_status dg_launch_k(dgfs_dg_s *dg, const void *f, const void *Q, const void 
     const DgCoef cf = coef_of(dg);
     {
         ProfScope ps(plan, "dg_wall_flux", st);
-        k_wall_out<T, K><<<dim3(2, S), 256, 0, st>>>(reinterpret_cast<const T *>(f), cf, dg->Ne, S, N, plan->L, n,
+        k_wall_out<T, K><<<dim3(2, S, kWallChunks), 256, 0, st>>>(reinterpret_cast<const T *>(f), cf, dg->Ne, S, N, plan->L, n,
                                                      dg->wsum);
         DGFS_LAUNCHED(plan);
     }
@@ -298,7 +313,7 @@ dgfs_status dg_build(dgfs_dg_s *dg)
     DGFS_CUDA(cudaSetDevice(plan->device));
     DGFS_CUDA(cudaMalloc(&dg->Mw, sizeof(double) * Mw.size()));
     DGFS_CUDA(cudaMemcpy(dg->Mw, Mw.data(), sizeof(double) * Mw.size(), cudaMemcpyHostToDevice));
-    DGFS_CUDA(cudaMalloc(&dg->wsum, sizeof(double) * 2 * S));
+    DGFS_CUDA(cudaMalloc(&dg->wsum, sizeof(double) * 2 * S * kWallChunks));
     const size_t es = elem_size(plan);
     DGFS_CUDA(cudaMalloc(&dg->f1, es * dg->P * S * n));
     DGFS_CUDA(cudaMalloc(&dg->f2, es * dg->P * S * n));

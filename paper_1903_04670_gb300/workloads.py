@@ -113,6 +113,12 @@ CONFIGS = {
     "c4_adjoint_n32": dict(N=32, L=10.0, M=12, Nrho=8, masses=[1.0, 2.0], omega=[0.81, 0.81],
                            alpha=[1.0, 1.0], d=[1.0, 1.2], points=64, elements=16, order=4,
                            kind="slab", T_left=1.0, T_right=1.5, seed=4),
+    # heat-transfer slab for the DG step: 16 elements x 3 Gauss points, purely
+    # diffuse walls at T = 1 (x = 0) and T = 2 (x = 1), at rest
+    "c5_heat_slab_n32": dict(N=32, L=8.0, M=12, Nrho=8, masses=[1.0, 2.0], omega=[0.81, 0.81],
+                             alpha=[1.0, 1.0], d=[1.0, 1.2], points=48, elements=16, order=3,
+                             kind="slab", T_left=1.0, T_right=2.0, seed=5,
+                             walls=((1.0, (0.0, 0.0, 0.0)), (2.0, (0.0, 0.0, 0.0)))),
 }
 
 
@@ -147,8 +153,12 @@ def make_problem(name, points=None, dtype=np.float64):
     else:
         raise ValueError(cfg["kind"])
     pairs = pair_params(cfg["omega"], cfg["alpha"], cfg["d"])
-    return dict(name=name, N=N, L=L, M=cfg["M"], Nrho=cfg["Nrho"], masses=list(cfg["masses"]),
-                pairs=pairs, f=f.astype(dtype))
+    out = dict(name=name, N=N, L=L, M=cfg["M"], Nrho=cfg["Nrho"], masses=list(cfg["masses"]),
+               pairs=pairs, f=f.astype(dtype))
+    for k in ("elements", "order", "walls"):
+        if k in cfg:
+            out[k] = cfg[k]
+    return out
 
 
 def krook_wu_problem(N, M, Nrho, m1=1.0, m2=1.0, L=12.0):

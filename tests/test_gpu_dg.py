@@ -144,3 +144,20 @@ def test_bad_arguments_are_status_codes():
     with pytest.raises(B.DgfsError) as e:
         B.Slab(plan, 2, 3, 0.0, 1.0, ((0.0, (0, 0, 0)), (1.0, (0, 0, 0))))  # T = 0
     assert e.value.status == 1
+
+
+def test_heat_slab_full_size_transport():
+    """The benchmark's DG workload (16 elements x 3 points, N = 32, M = 12,
+    N_rho = 8, walls at T = 1 and T = 2) in its launch configuration: the
+    transport right-hand side at every point against the DG oracle."""
+    pb = W.make_problem("c5_heat_slab_n32")
+    P = pb["f"].shape[0]
+    plan = B.Plan(pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"], "fp32_tc", P)
+    slab = B.Slab(plan, pb["elements"], pb["order"], 0.0, 1.0, pb["walls"])
+    f = torch.from_numpy(pb["f"]).to("cuda", torch.float32)
+    r = slab.rhs(f).double().cpu().numpy()
+    ref = ODG.Slab(pb["elements"], pb["order"], 0.0, 1.0, pb["N"], pb["L"], pb["masses"], pb["walls"])
+    ro = ref.streaming(_flat(f.double().cpu().numpy()))
+    assert np.abs(_flat(r) - ro).max() <= 1e-6 * np.abs(ro).max()
+    rate, scale = ref.mass_rate(_flat(r)), ref.mass_rate(np.abs(_flat(r)))
+    assert np.all(np.abs(rate) <= 1e-6 * scale)
