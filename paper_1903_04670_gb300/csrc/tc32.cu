@@ -141,6 +141,69 @@ __device__ __forceinline__ bool wait_copy_pipe(uint64_t *mbar, uint32_t &phase, 
     return pbar_and(bar_id, ok);
 }
 
+// Pencils held one per thread, adjacent lanes (2k, 2k+1) holding adjacent
+// pencils whose elements lie `stride` float2 apart in global memory: one
+// 16-byte access covers one element of both pencils of a lane pair (the even
+// lane takes the even elements, the odd lane the odd ones) and a shuffle hands
+// each lane the value of its own pencil.  This halves the global memory
+// instructions of 8-byte per-thread accesses.  base: element 0 of the even
+// lane's pencil (16-byte aligned).  Every lane of the warp must call these.
+template <int CNT>
+__device__ __forceinline__ void load_pair(float2 *dst, const float2 *base, long stride, bool valid)
+{
+    const bool odd = threadIdx.x & 1;
+#pragma unroll
+    for (int x = 0; x < CNT; x += 2) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid) v = *reinterpret_cast<const float4 *>(base + (long)(x + (odd ? 1 : 0)) * stride);
+        // even lane: v = (x of own, x of partner); odd lane: v = (x+1 of partner, x+1 of own)
+        const float gx = odd ? v.x : v.z, gy = odd ? v.y : v.w;
+        const float rx = __shfl_xor_sync(0xffffffffu, gx, 1), ry = __shfl_xor_sync(0xffffffffu, gy, 1);
+        dst[x] = odd ? make_float2(rx, ry) : make_float2(v.x, v.y);
+        dst[x + 1] = odd ? make_float2(v.z, v.w) : make_float2(rx, ry);
+    }
+}
+
+// The same access split in two, so that a prefetch stays asynchronous: the
+// raw 16-byte loads first, the shuffles when the values are needed.
+template <int CNT>
+__device__ __forceinline__ void load_pair_raw(float4 *raw, const float2 *base, long stride, bool valid)
+{
+    const bool odd = threadIdx.x & 1;
+#pragma unroll
+    for (int x = 0; x < CNT; x += 2)
+        raw[x / 2] = valid ? *reinterpret_cast<const float4 *>(base + (long)(x + (odd ? 1 : 0)) * stride)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+template <int CNT>
+__device__ __forceinline__ void unpack_pair(float2 *dst, const float4 *raw)
+{
+    const bool odd = threadIdx.x & 1;
+#pragma unroll
+    for (int x = 0; x < CNT; x += 2) {
+        const float4 v = raw[x / 2];
+        const float gx = odd ? v.x : v.z, gy = odd ? v.y : v.w;
+        const float rx = __shfl_xor_sync(0xffffffffu, gx, 1), ry = __shfl_xor_sync(0xffffffffu, gy, 1);
+        dst[x] = odd ? make_float2(rx, ry) : make_float2(v.x, v.y);
+        dst[x + 1] = odd ? make_float2(v.z, v.w) : make_float2(rx, ry);
+    }
+}
+
+template <int CNT>
+__device__ __forceinline__ void store_pair(float2 *base, const float2 *val, long stride, bool valid)
+{
+    const bool odd = threadIdx.x & 1;
+#pragma unroll
+    for (int x = 0; x < CNT; x += 2) {
+        const float2 give = odd ? val[x] : val[x + 1];
+        const float rx = __shfl_xor_sync(0xffffffffu, give.x, 1), ry = __shfl_xor_sync(0xffffffffu, give.y, 1);
+        const float4 w =
+            odd ? make_float4(rx, ry, val[x + 1].x, val[x + 1].y) : make_float4(val[x].x, val[x].y, rx, ry);
+        if (valid) *reinterpret_cast<float4 *>(base + (long)(x + (odd ? 1 : 0)) * stride) = w;
+    }
+}
+
 __device__ __forceinline__ uint32_t lane_base(uint32_t tbase)
 {
     return tbase + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16);
@@ -315,12 +378,12 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs 
         ok = run_mma(&mb[pp], ph_mma, bar, [&] { tcfmt::gemm<FMT>(tb + NO, A0, AB, By, IC, NO, KC, a.nterms); });
         if (!ok) break;
         // row t = (g, z'): y' values -> global [x][y'][z']
-        float2 *dst = (side == 0 ? a.Ap : a.Bq) + ((long)e * a.RS + rs) * n + (long)(x0 + g) * NN + yl;
+        float2 *dstp = (side == 0 ? a.Ap : a.Bq) + ((long)e * a.RS + rs) * n + (long)(x0 + g) * NN + (yl & ~1);
         tmem_visit<NO>(tl + NO, [&](int c0, const float *v) {
-            if (t < nval * N) {
+            float2 h[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) dst[(long)(c0 / 2 + j) * N] = make_float2(v[2 * j], v[2 * j + 1]);
-            }
+            for (int j = 0; j < 8; ++j) h[j] = make_float2(v[2 * j], v[2 * j + 1]);
+            store_pair<8>(dstp + (long)(c0 / 2) * N, h, N, t < nval * N);
         });
     }
     cta_teardown(tslot, NCOL, ok, a.err);
@@ -363,16 +426,17 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b(TcArgs 
             for (int w = first; w < first + count; ++w) copy_terms(slot(w), IC, src_img(w), IC, IC, NT, &mb[NP]);
         }
     };
-    float2 pa[N];
-    auto load_pencil = [&](float2 *dst, const float2 *src, bool valid) {
-#pragma unroll
-        for (int x = 0; x < N; ++x) dst[x] = valid ? src[(long)x * NN] : make_float2(0.f, 0.f);
+    // this thread's pencil p0 + t, loaded with 16-byte accesses shared with the
+    // neighbouring lane (raw; unpack_pair when used)
+    float4 pa_raw[N / 2];
+    auto load_pencil = [&](float4 *raw, const float2 *src, bool valid) {
+        load_pair_raw<N>(raw, src - (t & 1), NN, valid);
     };
     const int stride = gridDim.x * NP;
     int it = blockIdx.x * NP + pp;
     if (it < items) {
         const int e = it / NT_TILES, p0 = (it % NT_TILES) * kRows;
-        load_pencil(pa, a.Ap + ((long)e * a.RS + rs) * n + p0 + t, p0 + t < NN);
+        load_pencil(pa_raw, a.Ap + ((long)e * a.RS + rs) * n + p0 + t, p0 + t < NN);
     }
     bool ok = true;
     if (RESIDENT) {
@@ -383,10 +447,13 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b(TcArgs 
         const int e = it / NT_TILES, p0 = (it % NT_TILES) * kRows;
         const bool valid = p0 + t < NN;
         const long gbase = ((long)e * a.RS + rs) * n + p0 + t;
-        float2 pb[N];
+        float4 pb_raw[N / 2];
         if (ident_x) {
             // sigma_x = 0: T^p_x = T^q_x = I, so P = A' . B' directly
-            load_pencil(pb, a.Bq + gbase, valid);
+            load_pencil(pb_raw, a.Bq + gbase, valid);
+            float2 pa[N], pb[N];
+            unpack_pair<N>(pa, pa_raw);
+            unpack_pair<N>(pb, pb_raw);
 #pragma unroll
             for (int x = 0; x < N; x += 2) {
                 const float2 u = make_float2(pa[x].x * pb[x].x - pa[x].y * pb[x].y, pa[x].x * pb[x].y + pa[x].y * pb[x].x);
@@ -397,12 +464,16 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b(TcArgs 
             const int nx = it + stride;
             if (nx < items) {
                 const int e2 = nx / NT_TILES, q0 = (nx % NT_TILES) * kRows;
-                load_pencil(pa, a.Ap + ((long)e2 * a.RS + rs) * n + q0 + t, q0 + t < NN);
+                load_pencil(pa_raw, a.Ap + ((long)e2 * a.RS + rs) * n + q0 + t, q0 + t < NN);
             }
         } else {
+        {
+            float2 pa[N];
+            unpack_pair<N>(pa, pa_raw);
 #pragma unroll
-        for (int x = 0; x < N; x += 2) tcfmt::st_c2<FMT>(A0, AB, t, x, pa[x], pa[x + 1]);
-        load_pencil(pb, a.Bq + gbase, valid);
+            for (int x = 0; x < N; x += 2) tcfmt::st_c2<FMT>(A0, AB, t, x, pa[x], pa[x + 1]);
+        }
+        load_pencil(pb_raw, a.Bq + gbase, valid);
         if (!RESIDENT) {
             load_images(0, 1);
             ok = wait_copy_pipe(&mb[NP], ph_cp, bar);
@@ -410,12 +481,16 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b(TcArgs 
         }
         ok = run_mma(&mb[pp], ph_mma, bar, [&] { tcfmt::gemm<FMT>(tb, A0, AB, slot(0), IC, NO, KC, a.nterms); });
         if (!ok) break;
+        {
+            float2 pb[N];
+            unpack_pair<N>(pb, pb_raw);
 #pragma unroll
-        for (int x = 0; x < N; x += 2) tcfmt::st_c2<FMT>(A0, AB, t, x, pb[x], pb[x + 1]);
+            for (int x = 0; x < N; x += 2) tcfmt::st_c2<FMT>(A0, AB, t, x, pb[x], pb[x + 1]);
+        }
         const int nx = it + stride;
         if (nx < items) {
             const int e2 = nx / NT_TILES, q0 = (nx % NT_TILES) * kRows;
-            load_pencil(pa, a.Ap + ((long)e2 * a.RS + rs) * n + q0 + t, q0 + t < NN);
+            load_pencil(pa_raw, a.Ap + ((long)e2 * a.RS + rs) * n + q0 + t, q0 + t < NN);
         }
         if (!RESIDENT) {
             load_images(1, 1);
@@ -448,12 +523,12 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b(TcArgs 
         ok = run_mma(&mb[pp], ph_mma, bar,
                      [&] { tcfmt::gemm<FMT>(tb + 2 * NO, A0, AB, slot(2), IC, NO, KC, a.nterms); });
         if (!ok) break;
-        float2 *dst = a.H + gbase;
+        float2 *dstp = a.H + gbase - (t & 1);
         tmem_visit<NO>(tl + 2 * NO, [&](int c0, const float *v) {
-            if (valid) {
+            float2 h[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) dst[(long)(c0 / 2 + j) * NN] = make_float2(v[2 * j], v[2 * j + 1]);
-            }
+            for (int j = 0; j < 8; ++j) h[j] = make_float2(v[2 * j], v[2 * j + 1]);
+            store_pair<8>(dstp + (long)(c0 / 2) * NN, h, NN, valid);
         });
     }
     cta_teardown(tslot, NCOL, ok, a.err);
@@ -542,24 +617,24 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::C, 1) k_stage_c(TcArgs 
         if (!ok) break;
         // row t = (g, kz): t3(kx0+g, ky, kz) for all ky
         const float wr = (float)a.w[rs];
-        const float2 *brs = a.b32 + (long)rs * n + (long)(x0 + g) * NN + yl;
+        const float2 *brsp = a.b32 + (long)rs * n + (long)(x0 + g) * NN + (yl & ~1);
         tmem_visit<NO>(tl + NO, [&](int c0, const float *v) {
+            float2 bb[8];
+            load_pair<8>(bb, brsp + (long)(c0 / 2) * N, N, t < nval * N);
             if (t < nval * N) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int ky = c0 / 2 + j;
-                    const float2 bb = brs[(long)ky * N];
                     const float tr = v[2 * j], ti = v[2 * j + 1];
-                    acc[ky].x = fmaf(wr, bb.x * tr - bb.y * ti, acc[ky].x);
-                    acc[ky].y = fmaf(wr, bb.x * ti + bb.y * tr, acc[ky].y);
+                    acc[ky].x = fmaf(wr, bb[j].x * tr - bb[j].y * ti, acc[ky].x);
+                    acc[ky].y = fmaf(wr, bb[j].x * ti + bb[j].y * tr, acc[ky].y);
                 }
             }
         });
     }
-    if (ok && rb < a.rsb && t < nval * N) {
-        float2 *dst = a.QGp + ((long)e * a.rsb + rb) * n + (long)(x0 + g) * NN + yl;
-#pragma unroll
-        for (int ky = 0; ky < N; ++ky) dst[(long)ky * N] = acc[ky];
+    if (ok && rb < a.rsb) {  // uniform over the pipeline
+        float2 *dstp = a.QGp + ((long)e * a.rsb + rb) * n + (long)(x0 + g) * NN + (yl & ~1);
+        store_pair<N>(dstp, acc, N, t < nval * N);
     }
     cta_teardown(tslot, NCOL, ok, a.err);
 }
