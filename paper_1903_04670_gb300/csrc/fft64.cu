@@ -17,7 +17,8 @@
 //   P4 y: H = fft_y(H)
 //   P5 x: QG += w_rs / n^2 * b_rs * fft_x(H)   (loop over all (r, s) in-thread)
 // Finish: Q = beta/n Re( ifft3_u(QG) - f_p * ifft3_u(c * F_q) ) with unnormalised
-// inverse transforms ifft3_u.  Memory layout is natural (x slowest) everywhere;
+// inverse transforms ifft3_u; both real parts come from one complex transform
+// of Z = Herm(QG) + i Herm(c F_q) (k_herm).  Memory layout is natural (x slowest) everywhere;
 // pencils along x and y are read with threads consecutive in z (coalesced).
 #include <algorithm>
 
@@ -40,9 +41,9 @@ enum Mode {
     INV_AB,         // GA/GB = ifft(phi * GA/GB) in place
     PROD,           // GA = fft(ifft(phi+ GA) * ifft(phi- GB))
     MAC,            // QG = sum_rs w b fft(GA)     grid.z = eval
-    FIN1,           // QG = ifft(QG), G2 = ifft(c F_q)
-    FIN2,           // in place inverse on QG, G2
-    FIN3            // Q = beta/n Re(ifft(QG) - f_p ifft(G2))
+    FIN1,           // G2 = ifft(G2), G2 = Z = Herm(QG) + i Herm(c F_q) from k_herm
+    FIN2,           // in place inverse on G2
+    FIN3            // Q = beta/n (Re ifft(G2) - f_p Im ifft(G2))
 };
 
 struct PassArgs {
@@ -171,40 +172,21 @@ __global__ void __launch_bounds__(128) k_pass(PassArgs a)
 #pragma unroll
         for (int k = 0; k < N; ++k) qg[pencil_off<N, AXIS>(pi, k)] = acc_s[k * T + t];
     } else if constexpr (MODE == FIN1 || MODE == FIN2) {
-        const int e = blockIdx.z;
-        double2 *qg = a.QG + (long)e * n;
-        double2 *g2 = a.G2 + (long)e * n;
+        // in-place inverse pass on Z = Herm(QG) + i Herm(c F_q) (see k_herm)
+        double2 *g2 = a.G2 + (long)blockIdx.z * n;
 #pragma unroll
-        for (int j = 0; j < N; ++j) v[j] = qg[pencil_off<N, AXIS>(pi, j)];
-        fft<N, +1>(v, tw);
-#pragma unroll
-        for (int k = 0; k < N; ++k) qg[pencil_off<N, AXIS>(pi, k)] = v[k];
-        if constexpr (MODE == FIN1) {
-            const double2 *Fq = a.F + ((long)(a.pt0 + e) * a.S + a.q) * n;
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-                const long o = pencil_off<N, AXIS>(pi, j);
-                v[j] = cmul(a.c[o], Fq[o]);
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < N; ++j) v[j] = g2[pencil_off<N, AXIS>(pi, j)];
-        }
+        for (int j = 0; j < N; ++j) v[j] = g2[pencil_off<N, AXIS>(pi, j)];
         fft<N, +1>(v, tw);
 #pragma unroll
         for (int k = 0; k < N; ++k) g2[pencil_off<N, AXIS>(pi, k)] = v[k];
     } else if constexpr (MODE == FIN3) {
+        // last inverse pass: ifft3_u(Z) = Re ifft3_u(QG) + i Re ifft3_u(c F_q)
         const int e = blockIdx.z;
         const int pt = a.pt0 + e;
-        const double2 *qg = a.QG + (long)e * n;
         const double2 *g2 = a.G2 + (long)e * n;
-        double2 u[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) v[j] = qg[pencil_off<N, AXIS>(pi, j)];
+        for (int j = 0; j < N; ++j) v[j] = g2[pencil_off<N, AXIS>(pi, j)];
         fft<N, +1>(v, tw);
-#pragma unroll
-        for (int j = 0; j < N; ++j) u[j] = g2[pencil_off<N, AXIS>(pi, j)];
-        fft<N, +1>(u, tw);
         const long fbase = ((long)pt * a.S + a.p) * n;
         const long qbase = (((long)pt * a.S + a.p) * a.S + a.q) * n;
         const double sc = a.beta * a.inv_n;
@@ -214,7 +196,7 @@ __global__ void __launch_bounds__(128) k_pass(PassArgs a)
 #pragma unroll
             for (int k = 0; k < N; ++k) {
                 const long o = pencil_off<N, AXIS>(pi, k);
-                Q[o] = (float)(sc * (v[k].x - (double)fr[o] * u[k].x));
+                Q[o] = (float)(sc * (v[k].x - (double)fr[o] * v[k].y));
             }
         } else {
             const double *fr = a.f + fbase;
@@ -222,10 +204,32 @@ __global__ void __launch_bounds__(128) k_pass(PassArgs a)
 #pragma unroll
             for (int k = 0; k < N; ++k) {
                 const long o = pencil_off<N, AXIS>(pi, k);
-                Q[o] = sc * (v[k].x - fr[o] * u[k].x);
+                Q[o] = sc * (v[k].x - fr[o] * v[k].y);
             }
         }
     }
+}
+
+// Step 10 needs only real parts: Re ifft3(X) = ifft3(Herm X) with
+// Herm X(k) = (X(k) + conj X(-k)) / 2 (indices mod N), whose transform is
+// real.  The gain and loss transforms therefore share one complex inverse
+// transform: Z = Herm(QG) + i Herm(c F_q), ifft3(Z) = Re ifft3(QG) + i Re ifft3(c F_q).
+// One thread per (point e, index k); Z goes to G2.
+__global__ void k_herm(double2 *G2, const double2 *QG, const double2 *F, const double2 *c, int N, long n, int S,
+                       int q, int pt0, int E)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long)E * n) return;
+    const long e = i / n, k = i % n;
+    const int kx = (int)(k / ((long)N * N)), ky = (int)((k / N) % N), kz = (int)(k % N);
+    const long mk = ((long)((N - kx) % N) * N + (N - ky) % N) * N + (N - kz) % N;
+    const double2 *qg = QG + e * n;
+    const double2 *Fq = F + ((long)(pt0 + e) * S + q) * n;
+    const double2 a0 = qg[k], a1 = qg[mk];
+    const double2 l0 = cmul(c[k], Fq[k]), l1 = cmul(c[mk], Fq[mk]);
+    const double h1x = 0.5 * (a0.x + a1.x), h1y = 0.5 * (a0.y - a1.y);
+    const double h2x = 0.5 * (l0.x + l1.x), h2y = 0.5 * (l0.y - l1.y);
+    G2[e * n + k] = make_double2(h1x - h2y, h1y + h2x);
 }
 
 constexpr int kThreads = 128;
@@ -246,6 +250,17 @@ dgfs_status launch(dgfs_plan_s *plan, dim3 grid, const PassArgs &a, cudaStream_t
     {
         ProfScope ps(plan, names[MODE], st);
         k_pass<N, AXIS, MODE><<<grid, T, smem, st>>>(a);
+    }
+    DGFS_LAUNCHED(plan);
+    return DGFS_OK;
+}
+
+dgfs_status launch_herm(dgfs_plan_s *plan, const PassArgs &a, int N, int E, cudaStream_t st)
+{
+    const long total = (long)E * a.n;
+    {
+        ProfScope ps(plan, "fp64_herm", st);
+        k_herm<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a.G2, a.QG, a.F, a.c, N, a.n, a.S, a.q, a.pt0, E);
     }
     DGFS_LAUNCHED(plan);
     return DGFS_OK;
@@ -312,6 +327,7 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, void 
                 a.buf = GA;
                 DGFS_TRY((launch<N, 1, FWD_INPLACE>(plan, dim3(1, RS, Ec), a, st)));
                 DGFS_TRY((launch<N, 0, MAC>(plan, dim3(1, 1, Ec), a, st)));
+                DGFS_TRY(launch_herm(plan, a, N, Ec, st));
                 DGFS_TRY((launch<N, 0, FIN1>(plan, dim3(1, 1, Ec), a, st)));
                 DGFS_TRY((launch<N, 1, FIN2>(plan, dim3(1, 1, Ec), a, st)));
                 DGFS_TRY((launch<N, 2, FIN3>(plan, dim3(1, 1, Ec), a, st)));
@@ -363,6 +379,7 @@ dgfs_status finish_n(dgfs_plan_s *plan, int p, int q, int P, double2 *QG, double
     a.inv_n = 1.0 / (double)a.n;
     a.Q = Q;
     a.tw = plan->twiddle;
+    DGFS_TRY(launch_herm(plan, a, N, P, st));
     DGFS_TRY((launch<N, 0, FIN1>(plan, dim3(1, 1, P), a, st)));
     DGFS_TRY((launch<N, 1, FIN2>(plan, dim3(1, 1, P), a, st)));
     DGFS_TRY((launch<N, 2, FIN3>(plan, dim3(1, 1, P), a, st)));
