@@ -96,7 +96,8 @@ dgfs_status dgfs_plan_destroy(dgfs_plan plan);
  *   Q^(pq) = beta^(pq) Re( ifft( sum_{r,s} w_r w_s b_rs . fft( ifft(t1) ifft(t2) ) )
  *                          - f_p . ifft( c . fft(f_q) ) )
  *   t1 = exp(+i m_q/(m_p+m_q) a_rs) fft(f_p), t2 = exp(-i m_p/(m_p+m_q) a_rs) fft(f_q).
- *   f_dev : device [P][S][n] input.   Q_dev : device [P][S][S][n] output.
+ *   f_dev : device [P][S][n] input (16-byte aligned for tensor-core plans).
+ *   Q_dev : device [P][S][S][n] output.
  *   1 <= P <= max_points.  No allocation.  Errors: EINVAL, ECUDA. */
 dgfs_status dgfs_collide(dgfs_plan plan, int P, const void *f_dev, void *Q_dev, void *stream);
 

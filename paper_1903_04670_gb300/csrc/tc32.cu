@@ -943,6 +943,10 @@ size_t tc_workspace_bytes(const dgfs_plan_s *plan)
 dgfs_status tc_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st)
 {
     const TcState *ts = reinterpret_cast<const TcState *>(plan->tc);
+    if (reinterpret_cast<uintptr_t>(f) & 15) {  // f tiles are read with 16-byte loads
+        set_error("dgfs_collide: f must be 16-byte aligned for tensor-core plans");
+        return DGFS_EINVAL;
+    }
     return ts->fmt == 0 ? dispatch_collide<0>(plan, P, f, Q, st) : dispatch_collide<1>(plan, P, f, Q, st);
 }
 

@@ -54,3 +54,13 @@ def test_bad_arguments_are_status_codes(tc_plan):
     assert e.value.status == 1
     with pytest.raises(ValueError):
         plan.collide(f[:1].double().contiguous())  # wrong dtype is rejected by the binding
+
+
+def test_misaligned_f_is_rejected_by_tensor_core_plans(tc_plan):
+    pb, plan = tc_plan
+    buf = torch.zeros(16 ** 3 * 2 + 1, dtype=torch.float32, device="cuda")
+    f = buf[1:].view(1, 2, 16, 16, 16)  # 4-byte offset from an aligned allocation
+    Q = torch.empty((1, 2, 2, 16, 16, 16), dtype=torch.float32, device="cuda")
+    with pytest.raises(B.DgfsError) as e:
+        B.dgfs_collide(plan._h, 1, f, Q)
+    assert e.value.status == 1
