@@ -230,10 +230,10 @@ dgfs_status dgfs_plan_profile(dgfs_plan plan, int enable);
 dgfs_status dgfs_plan_profile_read(dgfs_plan plan, int max_classes, char *names, long long *counts,
                                    double *total_ms, int *n_classes);
 
-/* ---- 1-D DG transport around the operator (Eq. (1); Sec. 3) --------------
+/* ---- 1-D DG transport around the operator (Eq. (1); Sec. 3.3) ------------
  * Eq. (1), df_p/dt + c . grad_x f_p = sum_q Q^(pq)(f_p, f_q), is solved in the
  * paper by Runge-Kutta discontinuous Galerkin in one space dimension with
- * purely diffuse walls (Sec. 3, Couette case of Table 2); the paper defers the
+ * purely diffuse walls (Sec. 3.3, Couette case of Table 2); the paper defers the
  * formulas to its references, and these entry points implement the textbook
  * nodal scheme:
  *  - Ne equal elements on [x0, x1], K Gauss-Legendre nodes per element (DG

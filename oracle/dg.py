@@ -4,7 +4,7 @@ Test infrastructure only: ``tests/``, ``__graft_entry__.smoke()`` and
 ``bench.py``'s CPU legs may import it; the CUDA library never does.
 
 The paper solves Eq. (1), df_p/dt + c . grad_x f_p = sum_q Q^(pq), by
-Runge-Kutta discontinuous Galerkin in one space dimension (Sec. 3 and the
+Runge-Kutta discontinuous Galerkin in one space dimension (Sec. 3.3 and the
 Couette case of Table 2: DG order 3, purely diffuse walls) and defers the
 formulas to its references.  This module writes out the textbook scheme it
 names, in plain numpy with loops over elements:

@@ -1,7 +1,7 @@
 // 1-D nodal DG streaming term, purely diffuse walls and the SSP-RK3 step
 // around the collision operator: Eq. (1), df_p/dt + c . grad_x f_p =
 // sum_q Q^(pq), solved by Runge-Kutta discontinuous Galerkin in one space
-// dimension (Sec. 3; diffuse walls as in the Couette case of Table 2).  The
+// dimension (Sec. 3.3; diffuse walls as in the Couette case of Table 2).  The
 // paper names the scheme and defers its formulas to its references; this is
 // the textbook nodal form:
 //
