@@ -88,6 +88,18 @@ dgfs_status dgfs_plan_create(dgfs_plan *out, int N, double L, int M, int N_rho, 
                              const double *masses, const dgfs_pair *pairs,
                              dgfs_precision prec, int max_points, int device);
 
+/* Declared fast variant (no counterpart in the paper's algorithm): when every
+ * pair has alpha = 1 (VHS, so the angular integral is 4 pi sinc(theta |k|)
+ * and b_rs does not depend on the design direction s) and the design weights
+ * are equal, sum_{r,s} w_r w_s b_rs fft(A_rs B_rs) = sum_r w_r w_s b_r
+ * fft(sum_s A_rs B_rs): the forward transforms and the accumulation run once
+ * per radial node instead of once per (r, s).  Exact in exact arithmetic;
+ * results differ from Algorithm 2's order only by rounding.  It is on by
+ * default for plans that qualify (FP64 plans); enable = 0 restores the
+ * literal Algorithm 2 order.  Errors: EINVAL, EUNSUPPORTED (enable != 0 on a
+ * plan that does not qualify). */
+dgfs_status dgfs_plan_set_collapse(dgfs_plan plan, int enable);
+
 /* Release a plan and everything it owns.  NULL is accepted.  Synchronous. */
 dgfs_status dgfs_plan_destroy(dgfs_plan plan);
 
@@ -164,7 +176,8 @@ dgfs_status dgfs_moments(dgfs_plan plan, int P, const void *Q_dev, double *out_d
  *  [10] (r, s) blocks of the accumulation stage (tensor-core plans)
  *  [11] split products per contraction (tensor-core plans)
  *  [12], [13] CTA groups per (r, s) of the plane and pencil stages (tensor-core plans)
- *  [14] 1 if dgfs_plan_autotune chose the launch parameters [15] reserved. */
+ *  [14] 1 if dgfs_plan_autotune chose the launch parameters
+ *  [15] 1 if the sigma collapse is on (dgfs_plan_set_collapse). */
 dgfs_status dgfs_plan_info(dgfs_plan plan, double *info);
 
 /* Copy pair (p, q)'s tables to host FP64 buffers for verification:

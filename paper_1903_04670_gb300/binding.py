@@ -66,6 +66,7 @@ def lib():
             "dgfs_graph_destroy": (i, [_P]),
             "dgfs_plan_autotune": (i, [_P, i, _P, _P, _P, ctypes.POINTER(d)]),
             "dgfs_plan_profile_read": (i, [_P, i, _P, _P, _P, ctypes.POINTER(i)]),
+            "dgfs_plan_set_collapse": (i, [_P, i]),
             "dgfs_dg_create": (i, [ctypes.POINTER(_P), _P, i, i, d, d, _P]),
             "dgfs_dg_destroy": (i, [_P]),
             "dgfs_dg_nodes": (i, [_P, _P]),
@@ -171,7 +172,7 @@ def dgfs_plan_info(h):
     out = (ctypes.c_double * 16)()
     _check(lib().dgfs_plan_info(h, ctypes.cast(out, _P)), "dgfs_plan_info")
     keys = ("N", "L", "M", "N_rho", "S", "precision", "max_points", "workspace_bytes", "table_bytes", "chunk",
-            "rs_blocks", "nterms", "groups_a", "groups_b", "tuned")
+            "rs_blocks", "nterms", "groups_a", "groups_b", "tuned", "collapse")
     return {k: out[i] for i, k in enumerate(keys)}
 
 
@@ -188,6 +189,10 @@ def dgfs_plan_pair_tables(h, p, q, N, M, N_rho, with_b=True):
                                        cp(c)), "dgfs_plan_pair_tables")
     keys = ("R", "beta", "gamma", "eta", "dlogbeta", "cq", "cp", "overridden")
     return dict(scalars=dict(zip(keys, sc.tolist())), rho=rho, w_rho=wr, sigma=sig, w_sigma=ws, b=b, c=c)
+
+
+def dgfs_plan_set_collapse(h, enable):
+    _check(lib().dgfs_plan_set_collapse(h, int(bool(enable))), "dgfs_plan_set_collapse")
 
 
 def dgfs_plan_launch_count(h):
@@ -331,6 +336,9 @@ class Plan:
 
     def launch_count(self):
         return dgfs_plan_launch_count(self._h)
+
+    def set_collapse(self, enable):
+        dgfs_plan_set_collapse(self._h, enable)
 
     def check(self):
         dgfs_plan_check(self._h)

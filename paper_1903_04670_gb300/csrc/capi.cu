@@ -194,6 +194,18 @@ dgfs_status entry_check(dgfs_plan_s *plan)
 
 dgfs_status plan_entry_check(dgfs_plan_s *plan) { return entry_check(plan); }
 
+// The sum over design directions may move before the forward transforms when
+// b_rs does not depend on s: eta = alpha - 1 = 0 for every pair (the angular
+// integral is then 4 pi sinc(theta abs(k)), Sec. 2.2) and equal design weights.
+bool collapse_eligible(const dgfs_plan_s *plan)
+{
+    for (const dgfs_pair &pp : plan->pair_params)
+        if (pp.alpha != 1.0) return false;
+    for (int s = 1; s < plan->M; ++s)
+        if (plan->wsig[s] != plan->wsig[0]) return false;
+    return plan->prec == DGFS_FP64 || tc_supports_collapse(plan);
+}
+
 void host_gauss_legendre(int n, double a, double b, std::vector<double> &x, std::vector<double> &w)
 {
     gauss_legendre(n, a, b, x, w);
@@ -305,6 +317,7 @@ dgfs_status dgfs_plan_create(dgfs_plan *out, int N, double L, int M, int N_rho, 
             }
             gauss_legendre(N_rho, 0.0, pt.R, pt.rho, pt.wrho);
         }
+    plan->collapse = collapse_eligible(plan) ? 1 : 0;
 
     dgfs_status st = build_tables(plan);
     if (st == DGFS_OK) {
@@ -366,6 +379,18 @@ dgfs_status dgfs_collide(dgfs_plan plan, int P, const void *f_dev, void *Q_dev, 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (plan->prec == DGFS_FP64) return fp64_collide(plan, P, f_dev, Q_dev, s);
     return tc_collide(plan, P, f_dev, Q_dev, s);
+}
+
+dgfs_status dgfs_plan_set_collapse(dgfs_plan plan, int enable)
+{
+    if (!plan) return DGFS_EINVAL;
+    if (enable && !collapse_eligible(plan)) {
+        set_error("dgfs_plan_set_collapse: needs alpha = 1 for every pair (b independent of the design "
+                  "direction) and a path that implements it");
+        return DGFS_EUNSUPPORTED;
+    }
+    plan->collapse = enable ? 1 : 0;
+    return DGFS_OK;
 }
 
 dgfs_status dgfs_collide_host(dgfs_plan plan, int P, const void *f_host, void *Q_host, void *stream)
@@ -448,6 +473,7 @@ dgfs_status dgfs_plan_info(dgfs_plan plan, double *info)
     info[8] = (double)plan->table_bytes;
     info[9] = plan->chunk;
     tc_info(plan, info);
+    info[15] = plan->collapse;
     return DGFS_OK;
 }
 

@@ -59,6 +59,8 @@ struct dgfs_plan_s {
     long long launches = 0;
     // tensor-core form state (tc32.cu)
     void *tc = nullptr;
+    // 1: sum over design directions before the forward transforms (VHS only)
+    int collapse = 0;
     // per-kernel CUDA-event profiler (capi.cu), null unless enabled
     void *prof = nullptr;
 };
@@ -96,6 +98,8 @@ class ProfScope {
     cudaStream_t st_;
 };
 
+// capi.cu: whether the sigma collapse is exact and implemented for the plan
+bool collapse_eligible(const dgfs_plan_s *plan);
 // capi.cu: Gauss-Legendre nodes (increasing) and weights on [a, b]
 void host_gauss_legendre(int n, double a, double b, std::vector<double> &x, std::vector<double> &w);
 // tables.cu
@@ -120,6 +124,7 @@ void tc_release(dgfs_plan_s *plan);
 dgfs_status tc_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st);
 size_t tc_workspace_bytes(const dgfs_plan_s *plan);
 dgfs_status tc_check(dgfs_plan_s *plan);
+bool tc_supports_collapse(const dgfs_plan_s *plan);
 dgfs_status tc_selftest_wait(dgfs_plan_s *plan, int expire, cudaStream_t st);
 void tc_info(const dgfs_plan_s *plan, double *info);
 dgfs_status tc_autotune(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st, double *best_ms);

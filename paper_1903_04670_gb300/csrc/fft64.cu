@@ -40,6 +40,7 @@ enum Mode {
     INV_AB_FIRST,   // GA/GB = ifft(phi * F_p/q)   grid.y = rs, grid.z = eval
     INV_AB,         // GA/GB = ifft(phi * GA/GB) in place
     PROD,           // GA = fft(ifft(phi+ GA) * ifft(phi- GB))
+    PROD_SUM,       // GA[r M] = fft(sum_s ifft(phi+ GA_rs) * ifft(phi- GB_rs))   grid.y = r
     MAC,            // QG = sum_rs w b fft(GA)     grid.z = eval
     FIN1,           // G2 = ifft(G2), G2 = Z = Herm(QG) + i Herm(c F_q) from k_herm
     FIN2,           // in place inverse on G2
@@ -49,6 +50,8 @@ enum Mode {
 struct PassArgs {
     long n;
     int S, p, q, pt0, RS;
+    int M = 1;            // design size (PROD_SUM) and the stride of (r, s) grids in MAC / FWD_INPLACE
+    int grid_step = 1;    // FWD_INPLACE on GA: grid index = z * RS + y * grid_step
     const double *f;      // real f [P][S][n] (double)  or float when f32 != 0
     int f32;              // element type of f and Q: 0 double, 1 float
     double2 *F;           // [P][S][n]
@@ -100,7 +103,8 @@ __global__ void __launch_bounds__(128) k_pass(PassArgs a)
 #pragma unroll
         for (int k = 0; k < N; ++k) F[pencil_off<N, AXIS>(pi, k)] = v[k];
     } else if constexpr (MODE == FWD_INPLACE) {
-        double2 *g = a.buf + ((long)blockIdx.z * gridDim.y + blockIdx.y) * n;
+        double2 *g = a.buf + (a.grid_step == 1 ? ((long)blockIdx.z * gridDim.y + blockIdx.y)
+                                               : ((long)blockIdx.z * a.RS + (long)blockIdx.y * a.grid_step)) * n;
 #pragma unroll
         for (int j = 0; j < N; ++j) v[j] = g[pencil_off<N, AXIS>(pi, j)];
         fft<N, -1>(v, tw);
@@ -146,12 +150,38 @@ __global__ void __launch_bounds__(128) k_pass(PassArgs a)
         fft<N, -1>(v, tw);
 #pragma unroll
         for (int k = 0; k < N; ++k) ga[pencil_off<N, AXIS>(pi, k)] = v[k];
+    } else if constexpr (MODE == PROD_SUM) {
+        // sigma collapse: b_rs does not depend on s (eta = 0) and every w_s is
+        // 4 pi / M, so sum_s w_s b_rs fft(A_rs B_rs) = w_s b_r fft(sum_s A_rs B_rs)
+        const int r = blockIdx.y, e = blockIdx.z;
+        double2 u[N], acc[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[j] = make_double2(0.0, 0.0);
+        for (int s = 0; s < a.M; ++s) {
+            const int rs = r * a.M + s;
+            const double2 *php = a.phase + ((long)rs * 6 + 0 * 3 + AXIS) * N;
+            const double2 *phq = a.phase + ((long)rs * 6 + 1 * 3 + AXIS) * N;
+            const double2 *ga = a.GA + ((long)e * a.RS + rs) * n;
+            const double2 *gb = a.GB + ((long)e * a.RS + rs) * n;
+#pragma unroll
+            for (int j = 0; j < N; ++j) v[j] = cmul(ga[pencil_off<N, AXIS>(pi, j)], php[j]);
+            fft<N, +1>(v, tw);
+#pragma unroll
+            for (int j = 0; j < N; ++j) u[j] = cmul(gb[pencil_off<N, AXIS>(pi, j)], phq[j]);
+            fft<N, +1>(u, tw);
+#pragma unroll
+            for (int j = 0; j < N; ++j) acc[j] = cadd(acc[j], cmul(v[j], u[j]));
+        }
+        fft<N, -1>(acc, tw);
+        double2 *go = a.GA + ((long)e * a.RS + (long)r * a.M) * n;
+#pragma unroll
+        for (int k = 0; k < N; ++k) go[pencil_off<N, AXIS>(pi, k)] = acc[k];
     } else if constexpr (MODE == MAC) {
         const int e = blockIdx.z;
         const int T = blockDim.x, t = threadIdx.x;
 #pragma unroll
         for (int k = 0; k < N; ++k) acc_s[k * T + t] = make_double2(0.0, 0.0);
-        for (int rs = 0; rs < a.RS; ++rs) {
+        for (int rs = 0; rs < a.RS; rs += a.grid_step) {
             const double2 *ga = a.GA + ((long)e * a.RS + rs) * n;
             const double2 *brs = a.b + (long)rs * n;
             const double wr = a.w[rs] * a.inv_n2;
@@ -246,7 +276,7 @@ dgfs_status launch(dgfs_plan_s *plan, dim3 grid, const PassArgs &a, cudaStream_t
                                        (int)smem));
     }
     static const char *names[] = {"fp64_fwd_real", "fp64_fwd", "fp64_inv_first", "fp64_inv", "fp64_prod",
-                                  "fp64_mac", "fp64_fin1", "fp64_fin2", "fp64_fin3"};
+                                  "fp64_prod_sum", "fp64_mac", "fp64_fin1", "fp64_fin2", "fp64_fin3"};
     {
         ProfScope ps(plan, names[MODE], st);
         k_pass<N, AXIS, MODE><<<grid, T, smem, st>>>(a);
@@ -323,10 +353,21 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, void 
                 a.pt0 = pt0;
                 DGFS_TRY((launch<N, 0, INV_AB_FIRST>(plan, dim3(1, RS, Ec), a, st)));
                 DGFS_TRY((launch<N, 1, INV_AB>(plan, dim3(1, RS, Ec), a, st)));
-                DGFS_TRY((launch<N, 2, PROD>(plan, dim3(1, RS, Ec), a, st)));
                 a.buf = GA;
-                DGFS_TRY((launch<N, 1, FWD_INPLACE>(plan, dim3(1, RS, Ec), a, st)));
+                if (plan->collapse) {
+                    // sum over the design directions before the forward transforms
+                    a.M = plan->M;
+                    a.grid_step = plan->M;
+                    DGFS_TRY((launch<N, 2, PROD_SUM>(plan, dim3(1, plan->Nrho, Ec), a, st)));
+                    DGFS_TRY((launch<N, 1, FWD_INPLACE>(plan, dim3(1, plan->Nrho, Ec), a, st)));
+                } else {
+                    a.M = 1;
+                    a.grid_step = 1;
+                    DGFS_TRY((launch<N, 2, PROD>(plan, dim3(1, RS, Ec), a, st)));
+                    DGFS_TRY((launch<N, 1, FWD_INPLACE>(plan, dim3(1, RS, Ec), a, st)));
+                }
                 DGFS_TRY((launch<N, 0, MAC>(plan, dim3(1, 1, Ec), a, st)));
+                a.grid_step = 1;
                 DGFS_TRY(launch_herm(plan, a, N, Ec, st));
                 DGFS_TRY((launch<N, 0, FIN1>(plan, dim3(1, 1, Ec), a, st)));
                 DGFS_TRY((launch<N, 1, FIN2>(plan, dim3(1, 1, Ec), a, st)));

@@ -1042,6 +1042,8 @@ dgfs_status tc_selftest_wait(dgfs_plan_s *plan, int expire, cudaStream_t st)
     return DGFS_OK;
 }
 
+bool tc_supports_collapse(const dgfs_plan_s *) { return false; }
+
 dgfs_status tc_check(dgfs_plan_s *plan)
 {
     TcState *ts = reinterpret_cast<TcState *>(plan->tc);
