@@ -67,6 +67,7 @@ struct TcState {
 struct TcArgs {
     long n;
     int S, p, q, pt0, Ec, RS, nterms, rs_per_block, rsb;
+    int collapse_M;        // > 1: stage C sums the M directions of each radial node first (sigma collapse)
     const float *f;        // [P][S][n]
     float2 *Ap, *Bq, *H;   // [E][RS][n]
     float2 *QGp;           // [E][rsb][n]
@@ -574,7 +575,7 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::C, 1) k_stage_c(TcArgs 
     auto tile = [&](int rs) {
         return reinterpret_cast<const float4 *>(a.H + ((long)e * a.RS + rs) * n + (long)x0 * NN);
     };
-    if (PREFETCH && rs0 < rs1) {
+    if (PREFETCH && a.collapse_M == 1 && rs0 < rs1) {
         const float4 *src = tile(rs0);
 #pragma unroll
         for (int j = 0; j < HPT; ++j) {
@@ -583,7 +584,60 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::C, 1) k_stage_c(TcArgs 
         }
     }
     bool ok = wait_copy_cta(&mb[NP], ph_cp);
-    for (int rs = rs0; rs < rs1 && ok; ++rs) {
+    // sigma collapse: b_rs and w_rs do not depend on s, so the M tiles of one
+    // radial node are summed (FP32, in registers) and transformed once
+    constexpr int HS = (G * NN / 2 + kRows - 1) / kRows;  // float4 per thread per tile
+    for (int r0 = rs0; a.collapse_M > 1 && r0 < rs1 && ok; r0 += a.collapse_M) {
+        float4 hs[HS];
+#pragma unroll
+        for (int j = 0; j < HS; ++j) hs[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int sd = 0; sd < a.collapse_M; ++sd) {
+            const float4 *src = tile(r0 + sd);
+#pragma unroll
+            for (int j = 0; j < HS; ++j) {
+                const int i = t + kRows * j;
+                if (2 * i < nval * NN) {
+                    const float4 v = src[i];
+                    hs[j].x += v.x;
+                    hs[j].y += v.y;
+                    hs[j].z += v.z;
+                    hs[j].w += v.w;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < HS; ++j) {
+            const int i = t + kRows * j;
+            if (2 * i < nval * NN) tcfmt::st_f4<FMT>(A0, AB, (2 * i) / N, 2 * ((2 * i) % N), hs[j]);
+        }
+        ok = run_mma(&mb[pp], ph_mma, bar, [&] { tcfmt::gemm<FMT>(tb, A0, AB, Bf, IC, NO, KC, a.nterms); });
+        if (!ok) break;
+        tmem_visit<NO>(tl, [&](int c0, const float *v) {
+            if (t < nval * N) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    tcfmt::st_c<FMT>(A0, AB, g * N + c0 / 2 + j, yl, v[2 * j], v[2 * j + 1]);
+            }
+        });
+        ok = run_mma(&mb[pp], ph_mma, bar, [&] { tcfmt::gemm<FMT>(tb + NO, A0, AB, Bf, IC, NO, KC, a.nterms); });
+        if (!ok) break;
+        const float wr = (float)a.w[r0];
+        const float2 *brsp = a.b32 + (long)r0 * n + (long)(x0 + g) * NN + (yl & ~1);
+        tmem_visit<NO>(tl + NO, [&](int c0, const float *v) {
+            float2 bb[8];
+            load_pair<8>(bb, brsp + (long)(c0 / 2) * N, N, t < nval * N);
+            if (t < nval * N) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int ky = c0 / 2 + j;
+                    const float tr = v[2 * j], ti = v[2 * j + 1];
+                    acc[ky].x = fmaf(wr, bb[j].x * tr - bb[j].y * ti, acc[ky].x);
+                    acc[ky].y = fmaf(wr, bb[j].x * ti + bb[j].y * tr, acc[ky].y);
+                }
+            }
+        });
+    }
+    for (int rs = rs0; a.collapse_M == 1 && rs < rs1 && ok; ++rs) {
         // rows (g, y), K = z (complex): contiguous planes; float4 i holds complex 2i, 2i+1
         if constexpr (PREFETCH) {
 #pragma unroll
@@ -732,7 +786,11 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
     TcState *ts = reinterpret_cast<TcState *>(plan->tc);
     const int S = plan->S, RS = plan->Nrho * plan->M;
     const long n = (long)N * N * N;
-    const int E = ts->chunk, RSB = ts->rsb;
+    const int E = ts->chunk;
+    // accumulation blocks of (r, s); with the sigma collapse every block holds whole radial nodes
+    const int RSB = plan->collapse ? (plan->Nrho + (plan->Nrho + ts->rsb - 1) / ts->rsb - 1) /
+                                         ((plan->Nrho + ts->rsb - 1) / ts->rsb)
+                                   : ts->rsb;
     // workspace: F64 [maxP][S][n] d2 | QG64, G2 [maxP][n] d2 | Ap, Bq, H [Emax][RS][n] f2 | QGp [Emax][RSBmax][n] f2
     double2 *F64 = reinterpret_cast<double2 *>(plan->ws);
     double2 *QG64 = F64 + (long)plan->max_points * S * n;
@@ -748,7 +806,8 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
     a.RS = RS;
     a.nterms = ts->nterms;
     a.rsb = RSB;
-    a.rs_per_block = (RS + RSB - 1) / RSB;
+    a.rs_per_block = plan->collapse ? plan->M * ((plan->Nrho + ts->rsb - 1) / ts->rsb) : (RS + RSB - 1) / RSB;
+    a.collapse_M = plan->collapse ? plan->M : 1;
     a.f = reinterpret_cast<const float *>(f);
     a.Ap = Ap;
     a.Bq = Bq;
@@ -1042,7 +1101,8 @@ dgfs_status tc_selftest_wait(dgfs_plan_s *plan, int expire, cudaStream_t st)
     return DGFS_OK;
 }
 
-bool tc_supports_collapse(const dgfs_plan_s *) { return false; }
+// the plane stage sums the tiles of a radial node's directions (stage C)
+bool tc_supports_collapse(const dgfs_plan_s *) { return true; }
 
 dgfs_status tc_check(dgfs_plan_s *plan)
 {

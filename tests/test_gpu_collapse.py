@@ -46,3 +46,21 @@ def test_collapse_refused_for_vss_plans():
     with pytest.raises(B.DgfsError) as e:
         plan.set_collapse(True)
     assert e.value.status == 5
+
+
+@pytest.mark.parametrize("prec", ["fp32_tc", "bf16x3"])
+@pytest.mark.parametrize("N,M,Nrho,S,P", [(8, 6, 5, 2, 3), (16, 12, 4, 2, 2), (24, 6, 3, 3, 1), (32, 12, 8, 2, 2)])
+def test_tensor_core_collapse_matches_oracle(prec, N, M, Nrho, S, P):
+    pb, f = _vhs(N, M, Nrho, S, P, seed=3 * N + M)
+    plan = B.Plan(pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"], prec, P)
+    assert plan.info()["collapse"] == 1
+    fd = torch.from_numpy(f).to("cuda", torch.float32)
+    Qc = plan.collide(fd).double().cpu().numpy()
+    plan.check()
+    plan.set_collapse(False)
+    Ql = plan.collide(fd).double().cpu().numpy()
+    Qo = O.Problem(pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"]).collide_all(f)
+    scale = np.abs(Qo).max()
+    tol = 1e-5 if prec == "fp32_tc" else 1e-3
+    assert np.abs(Qc - Qo).max() <= tol * scale
+    assert np.abs(Ql - Qo).max() <= tol * scale
