@@ -295,6 +295,37 @@ dgfs_status dgfs_dg_rhs(dgfs_dg dg, const void *f_dev, const void *Q_dev, void *
  * graph-capturable.  Asynchronous.  Errors: EINVAL, ECUDA, ETIMEOUT. */
 dgfs_status dgfs_dg_step(dgfs_dg dg, void *f_dev, double dt, int with_collisions, void *stream);
 
+/* ---- Several slabs side by side (the paper's linear domain decomposition,
+ * Sec. 3.3: elements split into contiguous blocks, one per process, sharing
+ * O(S N^3) values per interface).  A DG object then covers one block of
+ * elements, [x0, x1] being the block's own interval; at an internal
+ * interface its neighbour's boundary trace replaces the wall.  Traces are
+ * FP64 device arrays [S][n] (n = N^3). */
+
+/* Boundary traces of f_dev [P][S][n]: left_dev = element 0 at xi = -1, the
+ * value the left neighbour needs; right_dev = element Ne-1 at xi = +1, the
+ * value the right neighbour needs.  Either may be NULL.  Asynchronous.
+ * Errors: EINVAL, ECUDA. */
+dgfs_status dgfs_dg_traces(dgfs_dg dg, const void *f_dev, double *left_dev, double *right_dev, void *stream);
+
+/* dgfs_dg_rhs with neighbour traces: halo_left_dev is the left neighbour's
+ * right trace (used for velocities entering from the left, c_x > 0),
+ * halo_right_dev the right neighbour's left trace (c_x < 0); NULL = the wall
+ * of dgfs_dg_create at that side.  Asynchronous.  Errors: EINVAL, ECUDA. */
+dgfs_status dgfs_dg_rhs_halo(dgfs_dg dg, const void *f_dev, const void *Q_dev, void *rhs_dev,
+                             const double *halo_left_dev, const double *halo_right_dev, void *stream);
+
+/* One Runge-Kutta stage, the building block of dgfs_dg_step for
+ * decomposed slabs (traces are exchanged between stages):
+ *   out = a0 f0 + a1 (f_in + dt L(f_in)),  L as in dgfs_dg_step, halos as in
+ *   dgfs_dg_rhs_halo.
+ * out may alias f0 but not f_in; f0 may be NULL when a0 = 0.  With
+ * collisions, the plan's operator is evaluated on f_in into the DG object's
+ * buffer.  Asynchronous.  Errors: EINVAL, ECUDA, ETIMEOUT. */
+dgfs_status dgfs_dg_stage(dgfs_dg dg, const void *f_in_dev, const void *f0_dev, void *out_dev, double a0, double a1,
+                          double dt, int with_collisions, const double *halo_left_dev,
+                          const double *halo_right_dev, void *stream);
+
 /* Static strings; never NULL. */
 const char *dgfs_status_string(dgfs_status s);
 const char *dgfs_last_error(void);

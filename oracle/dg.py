@@ -121,8 +121,18 @@ class Slab:
             inn = np.sum(cx[cx < 0] * M[cx < 0])
         return (-out / inn) * M
 
-    def streaming(self, f):
-        """-c_x df/dx in the DG weak form: f[P][S][N^3] -> [P][S][N^3]."""
+    def traces(self, f):
+        """(left, right): element 0 at xi = -1 and element Ne-1 at xi = +1, [S][N^3]."""
+        f = np.asarray(f, dtype=np.float64)
+        K = self.K
+        left = np.stack([self.phiL @ f[0:K, p, :] for p in range(self.S)])
+        right = np.stack([self.phiR @ f[(self.Ne - 1) * K:self.Ne * K, p, :] for p in range(self.S)])
+        return left, right
+
+    def streaming(self, f, halo_left=None, halo_right=None):
+        """-c_x df/dx in the DG weak form: f[P][S][N^3] -> [P][S][N^3].  A halo
+        (the neighbouring slab's trace at the shared face, [S][N^3]) replaces
+        the wall at that side."""
         Ne, K = self.Ne, self.K
         f = np.asarray(f, dtype=np.float64)
         out = np.zeros_like(f)
@@ -135,10 +145,14 @@ class Slab:
                 uR_in = self.phiR @ u
                 if e > 0:
                     uL_out = self.phiR @ f[(e - 1) * K:e * K, p, :]
+                elif halo_left is not None:
+                    uL_out = halo_left[p]
                 else:
                     uL_out = self.wall_state(0, p, uL_in)
                 if e < Ne - 1:
                     uR_out = self.phiL @ f[(e + 1) * K:(e + 2) * K, p, :]
+                elif halo_right is not None:
+                    uR_out = halo_right[p]
                 else:
                     uR_out = self.wall_state(1, p, uR_in)
                 FL = cx * np.where(pos, uL_out, uL_in)  # left face: upwind is the left side when c_x > 0

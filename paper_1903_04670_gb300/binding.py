@@ -72,6 +72,9 @@ def lib():
             "dgfs_dg_nodes": (i, [_P, _P]),
             "dgfs_dg_rhs": (i, [_P, _P, _P, _P, _P]),
             "dgfs_dg_step": (i, [_P, _P, d, i, _P]),
+            "dgfs_dg_traces": (i, [_P, _P, _P, _P, _P]),
+            "dgfs_dg_rhs_halo": (i, [_P, _P, _P, _P, _P, _P, _P]),
+            "dgfs_dg_stage": (i, [_P, _P, _P, _P, d, d, d, i, _P, _P, _P]),
             "dgfs_status_string": (ctypes.c_char_p, [i]),
             "dgfs_last_error": (ctypes.c_char_p, []),
             "dgfs_version": (ctypes.c_char_p, []),
@@ -390,6 +393,25 @@ def dgfs_dg_step(h, f, dt, with_collisions=True, stream=None):
     _check(lib().dgfs_dg_step(h, _ptr(f), float(dt), int(bool(with_collisions)), _stream(stream)), "dgfs_dg_step")
 
 
+def _opt(t):
+    return _ptr(t) if t is not None else None
+
+
+def dgfs_dg_traces(h, f, left, right, stream=None):
+    _check(lib().dgfs_dg_traces(h, _ptr(f), _opt(left), _opt(right), _stream(stream)), "dgfs_dg_traces")
+
+
+def dgfs_dg_rhs_halo(h, f, Q, rhs, halo_left, halo_right, stream=None):
+    _check(lib().dgfs_dg_rhs_halo(h, _ptr(f), _opt(Q), _ptr(rhs), _opt(halo_left), _opt(halo_right),
+                                  _stream(stream)), "dgfs_dg_rhs_halo")
+
+
+def dgfs_dg_stage(h, f_in, f0, out, a0, a1, dt, with_collisions, halo_left, halo_right, stream=None):
+    _check(lib().dgfs_dg_stage(h, _ptr(f_in), _opt(f0), _ptr(out), float(a0), float(a1), float(dt),
+                               int(bool(with_collisions)), _opt(halo_left), _opt(halo_right), _stream(stream)),
+           "dgfs_dg_stage")
+
+
 class Slab:
     """Owns a DG discretisation of [x0, x1] (Ne elements x K Gauss nodes) built on a Plan."""
 
@@ -425,3 +447,25 @@ class Slab:
         self._check_f(f)
         dgfs_dg_step(self._h, f, dt, with_collisions)
         return f
+
+    def traces(self, f):
+        """(left, right) boundary traces, FP64 [S][N^3] device tensors."""
+        self._check_f(f)
+        p = self.plan
+        left = torch.empty((p.S, p.N ** 3), dtype=torch.float64, device=f.device)
+        right = torch.empty_like(left)
+        dgfs_dg_traces(self._h, f, left, right)
+        return left, right
+
+    def rhs_halo(self, f, Q=None, halo_left=None, halo_right=None, out=None):
+        self._check_f(f)
+        if out is None:
+            out = torch.empty_like(f)
+        dgfs_dg_rhs_halo(self._h, f, Q, out, halo_left, halo_right)
+        return out
+
+    def stage(self, f_in, f0, out, a0, a1, dt, with_collisions=True, halo_left=None, halo_right=None):
+        self._check_f(f_in)
+        self._check_f(out)
+        dgfs_dg_stage(self._h, f_in, f0, out, a0, a1, dt, with_collisions, halo_left, halo_right)
+        return out

@@ -107,7 +107,8 @@ __device__ __forceinline__ double wall_sum(const double *wsum, int side, int S, 
 // never f.
 template <typename T, int K, bool STAGE>
 __global__ void k_dg(const T *f, const T *Q, const T *f0, T *out, DgCoef cf, const double *Mw, const double *wsum,
-                     int Ne, int S, int N, double L, long n, double a0, double a1, double dt)
+                     const double *halo_l, const double *halo_r, int Ne, int S, int N, double L, long n, double a0,
+                     double a1, double dt)
 {
     const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long)Ne * S * n) return;
@@ -132,7 +133,7 @@ __global__ void k_dg(const T *f, const T *Q, const T *f0, T *out, DgCoef cf, con
 #pragma unroll
             for (int j = 0; j < K; ++j) up += cf.tR[j] * (double)f[at((e - 1) * K + j)];
         } else {
-            up = -wall_sum(wsum, 0, S, p) * cf.nwL[p] * Mw[(long)p * n + v];
+            up = halo_l ? halo_l[(long)p * n + v] : -wall_sum(wsum, 0, S, p) * cf.nwL[p] * Mw[(long)p * n + v];
         }
         FL = cx * up;
         FR = cx * uR_in;
@@ -143,7 +144,8 @@ __global__ void k_dg(const T *f, const T *Q, const T *f0, T *out, DgCoef cf, con
 #pragma unroll
             for (int j = 0; j < K; ++j) dn += cf.tL[j] * (double)f[at((e + 1) * K + j)];
         } else {
-            dn = -wall_sum(wsum, 1, S, p) * cf.nwR[p] * Mw[((long)S + p) * n + v];
+            dn = halo_r ? halo_r[(long)p * n + v]
+                        : -wall_sum(wsum, 1, S, p) * cf.nwR[p] * Mw[((long)S + p) * n + v];
         }
         FL = cx * uL_in;
         FR = cx * dn;
@@ -168,6 +170,25 @@ __global__ void k_dg(const T *f, const T *Q, const T *f0, T *out, DgCoef cf, con
     }
 }
 
+// Boundary traces of this slab, FP64 [S][n]: element 0 at xi = -1 (left) and
+// element Ne - 1 at xi = +1 (right), the values a neighbouring slab needs.
+template <typename T, int K>
+__global__ void k_traces(const T *f, DgCoef cf, int Ne, int S, long n, double *left, double *right)
+{
+    const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (long)S * n) return;
+    const long v = gid % n;
+    const int p = (int)(gid / n);
+    double l = 0.0, r = 0.0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        l += cf.tL[j] * (double)f[((long)j * S + p) * n + v];
+        r += cf.tR[j] * (double)f[((long)((Ne - 1) * K + j) * S + p) * n + v];
+    }
+    if (left) left[gid] = l;
+    if (right) right[gid] = r;
+}
+
 DgCoef coef_of(const dgfs_dg_s *dg)
 {
     DgCoef c{};
@@ -186,10 +207,21 @@ DgCoef coef_of(const dgfs_dg_s *dg)
     return c;
 }
 
+struct DgCall {
+    const void *f, *Q, *f0;
+    void *out;
+    bool stage;
+    double a0, a1, dt;
+    const double *halo_l, *halo_r;  // null: wall at that side
+};
+
 template <typename T, int K>
-dgfs_status dg_launch_k(dgfs_dg_s *dg, const void *f, const void *Q, const void *f0, void *out, bool stage, double a0,
-                        double a1, double dt, cudaStream_t st)
+dgfs_status dg_launch_k(dgfs_dg_s *dg, const DgCall &c, cudaStream_t st)
 {
+    const void *f = c.f, *Q = c.Q, *f0 = c.f0;
+    void *out = c.out;
+    const bool stage = c.stage;
+    const double a0 = c.a0, a1 = c.a1, dt = c.dt;
     dgfs_plan_s *plan = dg->plan;
     const int N = plan->N, S = plan->S;
     const long n = (long)N * N * N;
@@ -206,35 +238,73 @@ dgfs_status dg_launch_k(dgfs_dg_s *dg, const void *f, const void *Q, const void 
     if (stage)
         k_dg<T, K, true><<<blocks, 256, 0, st>>>(reinterpret_cast<const T *>(f), reinterpret_cast<const T *>(Q),
                                                  reinterpret_cast<const T *>(f0), reinterpret_cast<T *>(out), cf,
-                                                 dg->Mw, dg->wsum, dg->Ne, S, N, plan->L, n, a0, a1, dt);
+                                                 dg->Mw, dg->wsum, c.halo_l, c.halo_r, dg->Ne, S, N, plan->L, n, a0,
+                                                 a1, dt);
     else
         k_dg<T, K, false><<<blocks, 256, 0, st>>>(reinterpret_cast<const T *>(f), reinterpret_cast<const T *>(Q),
-                                                  nullptr, reinterpret_cast<T *>(out), cf, dg->Mw, dg->wsum, dg->Ne,
-                                                  S, N, plan->L, n, 0.0, 0.0, 0.0);
+                                                  nullptr, reinterpret_cast<T *>(out), cf, dg->Mw, dg->wsum, c.halo_l,
+                                                  c.halo_r, dg->Ne, S, N, plan->L, n, 0.0, 0.0, 0.0);
+    DGFS_LAUNCHED(plan);
+    return DGFS_OK;
+}
+
+template <typename T, int K>
+dgfs_status traces_k(dgfs_dg_s *dg, const void *f, double *left, double *right, cudaStream_t st)
+{
+    dgfs_plan_s *plan = dg->plan;
+    const long n = (long)plan->N * plan->N * plan->N, total = (long)plan->S * n;
+    ProfScope ps(plan, "dg_traces", st);
+    k_traces<T, K><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(reinterpret_cast<const T *>(f), coef_of(dg),
+                                                                     dg->Ne, plan->S, n, left, right);
     DGFS_LAUNCHED(plan);
     return DGFS_OK;
 }
 
 template <typename T>
-dgfs_status dg_launch_t(dgfs_dg_s *dg, const void *f, const void *Q, const void *f0, void *out, bool stage,
-                        double a0, double a1, double dt, cudaStream_t st)
+dgfs_status dg_launch_t(dgfs_dg_s *dg, const DgCall &c, cudaStream_t st)
 {
     switch (dg->K) {
-    case 1: return dg_launch_k<T, 1>(dg, f, Q, f0, out, stage, a0, a1, dt, st);
-    case 2: return dg_launch_k<T, 2>(dg, f, Q, f0, out, stage, a0, a1, dt, st);
-    case 3: return dg_launch_k<T, 3>(dg, f, Q, f0, out, stage, a0, a1, dt, st);
-    case 4: return dg_launch_k<T, 4>(dg, f, Q, f0, out, stage, a0, a1, dt, st);
-    case 5: return dg_launch_k<T, 5>(dg, f, Q, f0, out, stage, a0, a1, dt, st);
+    case 1: return dg_launch_k<T, 1>(dg, c, st);
+    case 2: return dg_launch_k<T, 2>(dg, c, st);
+    case 3: return dg_launch_k<T, 3>(dg, c, st);
+    case 4: return dg_launch_k<T, 4>(dg, c, st);
+    case 5: return dg_launch_k<T, 5>(dg, c, st);
     }
     set_error("dg: K out of range");
     return DGFS_EINVAL;
 }
 
-dgfs_status dg_launch(dgfs_dg_s *dg, const void *f, const void *Q, const void *f0, void *out, bool stage, double a0,
-                      double a1, double dt, cudaStream_t st)
+dgfs_status dg_launch(dgfs_dg_s *dg, const DgCall &c, cudaStream_t st)
 {
-    if (dg->plan->prec == DGFS_FP64) return dg_launch_t<double>(dg, f, Q, f0, out, stage, a0, a1, dt, st);
-    return dg_launch_t<float>(dg, f, Q, f0, out, stage, a0, a1, dt, st);
+    if (dg->plan->prec == DGFS_FP64) return dg_launch_t<double>(dg, c, st);
+    return dg_launch_t<float>(dg, c, st);
+}
+
+template <typename T>
+dgfs_status traces_t(dgfs_dg_s *dg, const void *f, double *left, double *right, cudaStream_t st)
+{
+    switch (dg->K) {
+    case 1: return traces_k<T, 1>(dg, f, left, right, st);
+    case 2: return traces_k<T, 2>(dg, f, left, right, st);
+    case 3: return traces_k<T, 3>(dg, f, left, right, st);
+    case 4: return traces_k<T, 4>(dg, f, left, right, st);
+    case 5: return traces_k<T, 5>(dg, f, left, right, st);
+    }
+    set_error("dg: K out of range");
+    return DGFS_EINVAL;
+}
+
+// One Runge-Kutta stage: out = a0 f0 + a1 (f_in + dt L(f_in)), with the
+// collision operator of the plan evaluated on f_in when requested.
+dgfs_status dg_stage(dgfs_dg_s *dg, const void *f_in, const void *f0, void *out, double a0, double a1, double dt,
+                     int with_collisions, const double *halo_l, const double *halo_r, cudaStream_t st)
+{
+    if (with_collisions) {
+        const dgfs_status s = dgfs_collide(dg->plan, dg->P, f_in, dg->Q, st);
+        if (s != DGFS_OK) return s;
+    }
+    const DgCall c{f_in, with_collisions ? dg->Q : nullptr, f0, out, true, a0, a1, dt, halo_l, halo_r};
+    return dg_launch(dg, c, st);
 }
 
 void dg_free(dgfs_dg_s *dg)
@@ -388,7 +458,48 @@ dgfs_status dgfs_dg_rhs(dgfs_dg dg, const void *f_dev, const void *Q_dev, void *
     }
     dgfs_status st = plan_entry_check(dg->plan);
     if (st != DGFS_OK) return st;
-    return dg_launch(dg, f_dev, Q_dev, nullptr, rhs_dev, false, 0.0, 0.0, 0.0, reinterpret_cast<cudaStream_t>(stream));
+    const DgCall c{f_dev, Q_dev, nullptr, rhs_dev, false, 0.0, 0.0, 0.0, nullptr, nullptr};
+    return dg_launch(dg, c, reinterpret_cast<cudaStream_t>(stream));
+}
+
+dgfs_status dgfs_dg_rhs_halo(dgfs_dg dg, const void *f_dev, const void *Q_dev, void *rhs_dev,
+                             const double *halo_left_dev, const double *halo_right_dev, void *stream)
+{
+    if (!dg || !f_dev || !rhs_dev || f_dev == rhs_dev) {
+        set_error("dgfs_dg_rhs_halo: bad handle or pointer (rhs must not alias f)");
+        return DGFS_EINVAL;
+    }
+    dgfs_status st = plan_entry_check(dg->plan);
+    if (st != DGFS_OK) return st;
+    const DgCall c{f_dev, Q_dev, nullptr, rhs_dev, false, 0.0, 0.0, 0.0, halo_left_dev, halo_right_dev};
+    return dg_launch(dg, c, reinterpret_cast<cudaStream_t>(stream));
+}
+
+dgfs_status dgfs_dg_traces(dgfs_dg dg, const void *f_dev, double *left_dev, double *right_dev, void *stream)
+{
+    if (!dg || !f_dev || (!left_dev && !right_dev)) {
+        set_error("dgfs_dg_traces: bad handle or pointer");
+        return DGFS_EINVAL;
+    }
+    dgfs_status st = plan_entry_check(dg->plan);
+    if (st != DGFS_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (dg->plan->prec == DGFS_FP64) return traces_t<double>(dg, f_dev, left_dev, right_dev, s);
+    return traces_t<float>(dg, f_dev, left_dev, right_dev, s);
+}
+
+dgfs_status dgfs_dg_stage(dgfs_dg dg, const void *f_in_dev, const void *f0_dev, void *out_dev, double a0, double a1,
+                          double dt, int with_collisions, const double *halo_left_dev,
+                          const double *halo_right_dev, void *stream)
+{
+    if (!dg || !f_in_dev || !out_dev || f_in_dev == out_dev || (a0 != 0.0 && !f0_dev) || !std::isfinite(dt)) {
+        set_error("dgfs_dg_stage: bad handle, pointer (out must not alias f_in) or coefficient");
+        return DGFS_EINVAL;
+    }
+    dgfs_status st = plan_entry_check(dg->plan);
+    if (st != DGFS_OK) return st;
+    return dg_stage(dg, f_in_dev, f0_dev, out_dev, a0, a1, dt, with_collisions, halo_left_dev, halo_right_dev,
+                    reinterpret_cast<cudaStream_t>(stream));
 }
 
 dgfs_status dgfs_dg_step(dgfs_dg dg, void *f_dev, double dt, int with_collisions, void *stream)
@@ -400,15 +511,10 @@ dgfs_status dgfs_dg_step(dgfs_dg dg, void *f_dev, double dt, int with_collisions
     dgfs_status st = plan_entry_check(dg->plan);
     if (st != DGFS_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const void *Q = with_collisions ? dg->Q : nullptr;
     struct Stage { const void *in; void *out; double a0, a1; };
     const Stage stages[3] = {{f_dev, dg->f1, 0.0, 1.0}, {dg->f1, dg->f2, 0.75, 0.25}, {dg->f2, f_dev, 1.0 / 3.0, 2.0 / 3.0}};
     for (const Stage &sg : stages) {
-        if (with_collisions) {
-            st = dgfs_collide(dg->plan, dg->P, sg.in, dg->Q, stream);
-            if (st != DGFS_OK) return st;
-        }
-        st = dg_launch(dg, sg.in, Q, f_dev, sg.out, true, sg.a0, sg.a1, dt, s);
+        st = dg_stage(dg, sg.in, f_dev, sg.out, sg.a0, sg.a1, dt, with_collisions, nullptr, nullptr, s);
         if (st != DGFS_OK) return st;
     }
     return DGFS_OK;

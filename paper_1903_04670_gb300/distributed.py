@@ -47,3 +47,57 @@ def gather_shards(local, P, rank, world):
         a, b = shard_range(P, r, world)
         out.append(parts[r][: b - a])
     return torch.cat(out, dim=0)
+
+
+# ------------------------------------------------- DG slab split over ranks
+def element_range(Ne, rank, world):
+    """Contiguous block [e0, e1) of the Ne DG elements owned by `rank` (DG
+    elements stay whole, so the split is over elements, not points)."""
+    return shard_range(Ne, rank, world)
+
+
+def exchange_traces(left, right, rank, world):
+    """Trace halo exchange at the interfaces between neighbouring ranks.
+
+    left / right: this rank's boundary traces (its first element at its left
+    face, its last element at its right face), tensors of equal shape.  The
+    left trace goes to rank - 1, the right trace to rank + 1.  Returns
+    (halo_left, halo_right): the left neighbour's right trace and the right
+    neighbour's left trace, None at the ends of the domain (the walls).  This
+    is the only exchange of the decomposed DG step: O(S N^3) values per
+    interface (the paper's linear domain decomposition, Sec. 3.3)."""
+    if world == 1:
+        return None, None
+    halo_left = torch.empty_like(right) if rank > 0 else None
+    halo_right = torch.empty_like(left) if rank < world - 1 else None
+    ops = []
+    if rank > 0:
+        ops.append(dist.P2POp(dist.isend, left.contiguous(), rank - 1))
+        ops.append(dist.P2POp(dist.irecv, halo_left, rank - 1))
+    if rank < world - 1:
+        ops.append(dist.P2POp(dist.isend, right.contiguous(), rank + 1))
+        ops.append(dist.P2POp(dist.irecv, halo_right, rank + 1))
+    for req in dist.batch_isend_irecv(ops):
+        req.wait()
+    return halo_left, halo_right
+
+
+# SSP-RK3 in Shu-Osher form: (input, f0 weight a0, weight a1), stage 0 reads f
+SSP_RK3 = ((0, 0.0, 1.0), (1, 0.75, 0.25), (2, 1.0 / 3.0, 2.0 / 3.0))
+
+
+def dg_step_decomposed(slab, f, dt, with_collisions=True, rank=0, world=1, work=None):
+    """One SSP-RK3 step of this rank's block of elements, exchanging boundary
+    traces before every stage.  slab: binding.Slab over the rank's own
+    elements (walls of the global domain at the global ends); f: its
+    [P_local][S][N][N][N] tensor, updated in place.  work: optional pair of
+    stage buffers shaped like f."""
+    f1, f2 = work if work is not None else (torch.empty_like(f), torch.empty_like(f))
+    bufs = (f, f1, f2)
+    outs = (f1, f2, f)
+    for k, (src, a0, a1) in enumerate(SSP_RK3):
+        fin = bufs[src]
+        left, right = slab.traces(fin)
+        hl, hr = exchange_traces(left, right, rank, world)
+        slab.stage(fin, f if a0 != 0.0 else None, outs[k], a0, a1, dt, with_collisions, hl, hr)
+    return f

@@ -161,3 +161,42 @@ def test_heat_slab_full_size_transport():
     assert np.abs(_flat(r) - ro).max() <= 1e-6 * np.abs(ro).max()
     rate, scale = ref.mass_rate(_flat(r)), ref.mass_rate(np.abs(_flat(r)))
     assert np.all(np.abs(rate) <= 1e-6 * scale)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32_tc", 1e-6)])
+def test_split_slab_with_trace_halos_equals_whole_slab(prec, tol):
+    """Two halves of the slab on one GPU, run one after the other (no kernel
+    waits on another), with the boundary traces handed across before every
+    stage: the right-hand side and one collisional SSP-RK3 step equal those
+    of the whole slab."""
+    from paper_1903_04670_gb300 import distributed as D
+
+    plan, slab, f, ref, prob = _setup(prec, Ne=4, K=3)
+    K = 3
+    halves = [B.Slab(plan, 2, K, 0.0, 0.5, WALLS), B.Slab(plan, 2, K, 0.5, 1.0, WALLS)]
+    fd = torch.from_numpy(f).to("cuda", plan.dtype)
+    parts = [fd[: 2 * K].clone(), fd[2 * K:].clone()]
+
+    def exchange(fs):
+        tr = [h.traces(x) for h, x in zip(halves, fs)]
+        return [(None, tr[1][0]), (tr[0][1], None)]  # (halo_left, halo_right) per half
+
+    full = slab.rhs(fd).double()
+    hal = exchange(parts)
+    got = torch.cat([h.rhs_halo(x, None, *hl) for h, x, hl in zip(halves, parts, hal)]).double()
+    assert (got - full).abs().max() <= tol * full.abs().max()
+
+    dt = 0.01
+    whole = fd.clone()
+    slab.step(whole, dt)
+    work = [(torch.empty_like(x), torch.empty_like(x)) for x in parts]
+    for k, (src, a0, a1) in enumerate(D.SSP_RK3):
+        bufs = [(x, w[0], w[1]) for x, w in zip(parts, work)]
+        fins = [b[src] for b in bufs]
+        hal = exchange(fins)
+        for i, h in enumerate(halves):
+            out = (bufs[i][1], bufs[i][2], bufs[i][0])[k]
+            h.stage(fins[i], parts[i] if a0 != 0.0 else None, out, a0, a1, dt, True, *hal[i])
+    got = torch.cat(parts).double()
+    d_ref = (whole.double() - fd.double())
+    assert (got - whole.double()).abs().max() <= max(tol, 1e-12) * d_ref.abs().max() * 10

@@ -1,7 +1,8 @@
-"""The multi-rank path on CPU: two gloo ranks each evaluate their contiguous
+"""The multi-rank paths on CPU: gloo ranks each evaluate their contiguous
 block of points (with the oracle as the per-rank compute, since the CPU has no
 GPU) and the gathered result equals the single-process result bit for bit;
-the timing reduction takes the MAX over ranks."""
+the timing reduction takes the MAX over ranks; a DG slab split over ranks with
+the trace halo exchange steps exactly like the undivided slab."""
 import os
 import socket
 
@@ -67,3 +68,80 @@ def test_two_gloo_ranks_equal_single_process(tmp_path):
     ref = prob.collide_all(pb["f"])
     assert res["tmax"] == 2.0
     assert np.array_equal(res["Q"].numpy(), ref)
+
+
+class _OracleBlock:
+    """The operations dg_step_decomposed needs from a slab, done by the DG
+    oracle on this rank's block of elements (CPU stand-in for binding.Slab)."""
+
+    def __init__(self, ref):
+        self.ref = ref
+
+    def traces(self, f):
+        l, r = self.ref.traces(f.reshape(f.shape[0], f.shape[1], -1).numpy())
+        return torch.from_numpy(l), torch.from_numpy(r)
+
+    def stage(self, fin, f0, out, a0, a1, dt, with_collisions, hl, hr):
+        g = fin.reshape(fin.shape[0], fin.shape[1], -1).numpy()
+        r = self.ref.streaming(g, None if hl is None else hl.numpy(), None if hr is None else hr.numpy())
+        new = g + dt * r
+        if a0 != 0.0:
+            new = a0 * f0.reshape(new.shape).numpy() + a1 * new
+        else:
+            new = a1 * new
+        out.copy_(torch.from_numpy(new).reshape(out.shape))
+        return out
+
+
+WALLS = ((1.0, (0.0, -0.2, 0.0)), (2.0, (0.0, 0.2, 0.0)))
+SLAB = dict(Ne=5, K=3, N=6, L=4.0, masses=(1.0, 2.0))
+
+
+def _slab_f():
+    rng = np.random.default_rng(11)
+    P = SLAB["Ne"] * SLAB["K"]
+    return rng.uniform(0.1, 1.0, size=(P, len(SLAB["masses"]), SLAB["N"], SLAB["N"], SLAB["N"]))
+
+
+def _dg_worker(rank, world, port, out_path):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from oracle import dg as ODG
+
+    Ne, K = SLAB["Ne"], SLAB["K"]
+    e0, e1 = D.element_range(Ne, rank, world)
+    he = 1.0 / Ne
+    ref = ODG.Slab(e1 - e0, K, e0 * he, e1 * he, SLAB["N"], SLAB["L"], SLAB["masses"], WALLS)
+    f = torch.from_numpy(_slab_f()[e0 * K:e1 * K].copy())
+    D.dg_step_decomposed(_OracleBlock(ref), f, 0.004, with_collisions=False, rank=rank, world=world)
+    parts = [None] * world
+    dist.all_gather_object(parts, (e0, f.numpy()))
+    if rank == 0:
+        torch.save(parts, out_path)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_decomposed_dg_step_equals_single_slab(tmp_path, world):
+    """Elements split over gloo ranks, boundary traces exchanged before every
+    SSP-RK3 stage: the same result as the undivided slab."""
+    from oracle import dg as ODG
+
+    out = str(tmp_path / "dg.pt")
+    mp.start_processes(_dg_worker, args=(world, _free_port(), out), nprocs=world, join=True, start_method="spawn")
+    parts = sorted(torch.load(out, weights_only=False), key=lambda t: t[0])
+    got = np.concatenate([p[1] for p in parts])
+    ref = ODG.Slab(SLAB["Ne"], SLAB["K"], 0.0, 1.0, SLAB["N"], SLAB["L"], SLAB["masses"], WALLS)
+    f = _slab_f()
+    want = ref.ssp_rk3(f.reshape(f.shape[0], f.shape[1], -1), 0.004).reshape(f.shape)
+    assert np.abs(got - want).max() <= 1e-14 * np.abs(want).max()
+
+
+def test_element_range_keeps_elements_whole():
+    for Ne in (1, 4, 5, 16):
+        for world in (1, 2, 3):
+            spans = [D.element_range(Ne, r, world) for r in range(world)]
+            assert spans[0][0] == 0 and spans[-1][1] == Ne
+            assert all(b == c for (_, b), (c, _) in zip(spans, spans[1:]))
