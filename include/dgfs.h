@@ -100,6 +100,24 @@ dgfs_status dgfs_plan_create(dgfs_plan *out, int N, double L, int M, int N_rho, 
  * plan that does not qualify). */
 dgfs_status dgfs_plan_set_collapse(dgfs_plan plan, int enable);
 
+/* ---- Dealiased operator (declared variant) ------------------------------
+ * Algorithm 2 forms the translate product on the N-point grid, so its Fourier
+ * coefficients are the cyclic sum over l + m = k (mod N); the Galerkin form of
+ * Eq. (7) sums over l + m = k without wrap-around.  These entry points give
+ * the latter by the 3/2 rule, on a plan created at N' = 3N/2 (same L):
+ *   1. f' = spectral interpolant of f on the N' grid: the coefficients of f
+ *      at its N wavenumbers with the planes carrying -N/2 zeroed (their +N/2
+ *      partner is not on the N grid, so only then is the interpolant real);
+ *   2. Q' = dgfs_collide on the N' plan (its precision form);
+ *   3. Q = the N original wavenumbers of Q', -N/2 planes zeroed, on the N grid.
+ * The resampling is FP64.  f_dev [P][S][N^3] and Q_dev [P][S][S][N^3] in the
+ * plan's element type; work_dev: caller-owned device scratch, 256-byte
+ * aligned, at least dgfs_dealias_work_bytes bytes.  No allocation.
+ * Asynchronous.  Errors: EINVAL (also when the plan's N is not 3N/2), ECUDA. */
+dgfs_status dgfs_dealias_work_bytes(dgfs_plan plan, int P, int N, size_t *bytes);
+dgfs_status dgfs_collide_dealiased(dgfs_plan plan, int P, int N, const void *f_dev, void *Q_dev, void *work_dev,
+                                   size_t work_bytes, void *stream);
+
 /* Release a plan and everything it owns.  NULL is accepted.  Synchronous. */
 dgfs_status dgfs_plan_destroy(dgfs_plan plan);
 

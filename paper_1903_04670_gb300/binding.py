@@ -67,6 +67,8 @@ def lib():
             "dgfs_plan_autotune": (i, [_P, i, _P, _P, _P, ctypes.POINTER(d)]),
             "dgfs_plan_profile_read": (i, [_P, i, _P, _P, _P, ctypes.POINTER(i)]),
             "dgfs_plan_set_collapse": (i, [_P, i]),
+            "dgfs_dealias_work_bytes": (i, [_P, i, i, ctypes.POINTER(ctypes.c_size_t)]),
+            "dgfs_collide_dealiased": (i, [_P, i, i, _P, _P, _P, ctypes.c_size_t, _P]),
             "dgfs_dg_create": (i, [ctypes.POINTER(_P), _P, i, i, d, d, _P]),
             "dgfs_dg_destroy": (i, [_P]),
             "dgfs_dg_nodes": (i, [_P, _P]),
@@ -196,6 +198,18 @@ def dgfs_plan_pair_tables(h, p, q, N, M, N_rho, with_b=True):
 
 def dgfs_plan_set_collapse(h, enable):
     _check(lib().dgfs_plan_set_collapse(h, int(bool(enable))), "dgfs_plan_set_collapse")
+
+
+def dgfs_dealias_work_bytes(h, P, N):
+    v = ctypes.c_size_t(0)
+    _check(lib().dgfs_dealias_work_bytes(h, int(P), int(N), ctypes.byref(v)), "dgfs_dealias_work_bytes")
+    return int(v.value)
+
+
+def dgfs_collide_dealiased(h, P, N, f, Q, work, stream=None):
+    _check(lib().dgfs_collide_dealiased(h, int(P), int(N), _ptr(f), _ptr(Q), _ptr(work),
+                                        ctypes.c_size_t(work.numel() * work.element_size()), _stream(stream)),
+           "dgfs_collide_dealiased")
 
 
 def dgfs_plan_launch_count(h):
@@ -342,6 +356,18 @@ class Plan:
 
     def set_collapse(self, enable):
         dgfs_plan_set_collapse(self._h, enable)
+
+    def collide_dealiased(self, f, N, Q=None, work=None):
+        """Linear-convolution operator on the N grid (this plan is built at 3N/2)."""
+        if not (f.is_cuda and f.dtype == self.dtype and f.is_contiguous() and f.shape[2:] == (N, N, N)):
+            raise ValueError("f must be a contiguous %s CUDA tensor [P][S][N][N][N]" % self.dtype)
+        P = f.shape[0]
+        if Q is None:
+            Q = torch.empty((P, self.S, self.S, N, N, N), dtype=self.dtype, device=f.device)
+        if work is None:
+            work = torch.empty(dgfs_dealias_work_bytes(self._h, P, N), dtype=torch.uint8, device=f.device)
+        dgfs_collide_dealiased(self._h, P, N, f, Q, work)
+        return Q
 
     def check(self):
         dgfs_plan_check(self._h)
