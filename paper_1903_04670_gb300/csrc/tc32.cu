@@ -953,12 +953,13 @@ dgfs_status tc_prepare(dgfs_plan_s *plan)
     ts->chunk_max = std::max(1, std::min(plan->max_points, 24));
     ts->chunk = ts->chunk_max;
     ts->rsb_max = std::min(RS, 16);
-    ts->rsb = std::min(RS, 8);
+    ts->rsb = std::min(RS, 4);
     // CTA groups: about four waves of CTAs over the GPU
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plan->device);
-    ts->groups_a = std::max(1, (4 * sms + RS) / (2 * RS));
-    ts->groups_b = std::max(1, (4 * sms + RS / 2) / RS);
+    // about 8 waves of CTAs per stage (the autotuner's usual choice at N = 32)
+    ts->groups_a = std::max(1, (8 * sms + RS) / (2 * RS));
+    ts->groups_b = std::max(1, (8 * sms + RS / 2) / RS);
     DGFS_CUDA(cudaMalloc(&ts->err, sizeof(int)));
     DGFS_CUDA(cudaMemset(ts->err, 0, sizeof(int)));
     // axes along which the design direction has no component: the translate
@@ -1023,9 +1024,9 @@ dgfs_status tc_autotune(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaSt
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plan->device);
     struct Cand { int chunk, rsb, ga, gb; };
     std::vector<Cand> cands;
-    const int chunks[] = {ts->chunk_max, std::min(ts->chunk_max, 8), std::min(ts->chunk_max, 4)};
-    const int rsbs[] = {std::min(RS, 4), std::min(RS, 8), std::min(RS, 16)};
-    const int waves[] = {2, 4, 8};
+    const int chunks[] = {ts->chunk_max, std::min(ts->chunk_max, 8)};
+    const int rsbs[] = {std::min(RS, 2), std::min(RS, 4), std::min(RS, 8), std::min(RS, 16)};
+    const int waves[] = {4, 8, 16};
     for (int c : chunks)
         for (int r : rsbs)
             for (int w : waves) {
