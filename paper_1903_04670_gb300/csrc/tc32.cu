@@ -62,6 +62,7 @@ struct TcState {
     int tuned = 0;
     uint8_t *idmask = nullptr;  // [RS] bit d set when sigma_{s,d} == 0 (T_d is the identity; x and y are skipped)
     int skip_identity = 1;
+    int ws_a = 0;  // 1: warp-specialised plane stage A (an autotuner choice where it fits)
 };
 
 struct TcArgs {
@@ -388,6 +389,217 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs 
         });
     }
     cta_teardown(tslot, NCOL, ok, a.err);
+}
+
+// ------------------------------------------------- stage A, warp-specialised
+// The same plane stage with its three kinds of work on separate warpgroups of
+// one CTA, so that the tensor core works on one item while the CUDA cores
+// prepare the next and drain the previous:
+//   WG0 (load):      f tile -> split -> A_z[slot]; its thread 0 issues the
+//                    z-pass into TMEM D1[slot];
+//   WG1 (transpose): D1[slot] -> in-plane transpose -> A_y; its thread 0
+//                    issues the y-pass into D2[slot] (sigma_y = 0: D1 goes
+//                    straight to global memory instead);
+//   WG2 (store):     D2[slot] -> A' / B' in global memory.
+// Two slots for A_z, D1, D2 and one A_y; every handoff is an mbarrier
+// (full: the MMA's commit or the producer; empty: the consumer) waited on
+// with a bound.  A role whose wait expires raises a CTA-wide abort flag that
+// the other roles' waits observe; each wait is followed by a vote over the
+// role's 128 threads, so a role always leaves its loop as a whole.
+template <int N, int FMT> struct WsA {
+    static constexpr int NT = Fmt<FMT>::NT;
+    static constexpr int KR = FMT == 1 ? (N + 15) / 16 * 16 : N;
+    static constexpr int AZB = tcfmt::atoms_b(KR * Fmt<FMT>::ESZ) * kRows * 128;  // one term of A_z
+    static constexpr int AB = tcfmt::abytes<FMT>(N), IC = tcfmt::img_c<FMT>(N), IR = tcfmt::img_r<FMT>(N);
+    static constexpr size_t BYTES = 1024 + (size_t)NT * (IR + IC) + 2 * (size_t)NT * AZB + (size_t)NT * AB;
+    static constexpr bool OK = BYTES <= kSmemMax && N >= 16;
+};
+
+// bounded wait that also gives up when another role has aborted
+__device__ __forceinline__ bool ws_wait(uint64_t *mbar, uint32_t parity, volatile int *abort)
+{
+    for (long it = 0; it < kWaitLimit; it += 64) {
+        if (mbar_wait(mbar, parity, 64)) return true;
+        if (*abort) return false;
+    }
+    return false;
+}
+
+template <int N, int FMT>
+__global__ void __launch_bounds__(3 * kRows, 1) k_stage_a_ws(TcArgs a)
+{
+    using W = WsA<N, FMT>;
+    constexpr int NT = W::NT, AB = W::AB, IR = W::IR, IC = W::IC, AZB = W::AZB, KR = W::KR;
+    constexpr int G = kRows / N, KC = 2 * N, NO = 2 * N, NG = (N + G - 1) / G, NN = N * N;
+    constexpr int FPT = (G * NN / 4 + kRows - 1) / kRows;
+    constexpr uint32_t NCOL = pow2_cols(4 * NO);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = align1024(smem_raw);
+    uint8_t *Bz = sm, *By = sm + NT * IR;
+    uint8_t *AZ0 = sm + NT * (IR + IC);  // slot s at AZ0 + s * NT * AZB
+    uint8_t *AY = AZ0 + 2 * NT * AZB;
+    // [0] images, [1..2] az_empty, [3..4] d1_full, [5..6] d1_empty, [7] ay_empty,
+    // [8..9] d2_full, [10..11] d2_empty, [12..13] drain of the two issuing threads
+    __shared__ uint64_t mb[14];
+    __shared__ uint32_t tslot;
+    __shared__ int abort_flag;
+    uint64_t *az_empty = mb + 1, *d1_full = mb + 3, *d1_empty = mb + 5, *ay_empty = mb + 7, *d2_full = mb + 8,
+             *d2_empty = mb + 10, *drain = mb + 12;
+    const int role = threadIdx.x / kRows, t = threadIdx.x % kRows, bar = 1 + role;
+    const int rs = blockIdx.y, side = blockIdx.z;
+    const long n = a.n;
+    const int items = a.Ec * NG;
+    const bool ident_y = a.idmask && (a.idmask[rs] & 2);
+    if (threadIdx.x == 0) abort_flag = 0;
+    cta_setup(&tslot, NCOL, mb, 14);
+    const uint32_t tb = tslot, tl = lane_base(tb);  // D1[s]: tb + s NO, D2[s]: tb + (2 + s) NO
+    volatile int *abort_p = &abort_flag;
+    uint32_t ph_img = 0;
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&mb[0], NT * (IR + IC));
+        copy_terms(Bz, IR, timg_at<FMT>(a.timg, N, rs, side, 2), IC, IR, NT, &mb[0]);
+        copy_terms(By, IC, timg_at<FMT>(a.timg, N, rs, side, 1), IC, IC, NT, &mb[0]);
+    }
+    bool ok = wait_copy_cta(&mb[0], ph_img);
+    const int sp = side == 0 ? a.p : a.q;
+    const int g = t / N, yl = t % N;
+    auto fail = [&]() {
+        ok = false;
+        *abort_p = 1;
+    };
+
+    if (role == 0 && ok) {
+        // ---------------------------------------------------------- load
+        float4 pf[FPT];
+        auto prefetch = [&](int it) {
+            const int e = it / NG, x0 = (it % NG) * G, nval = min(G, N - x0);
+            const float4 *fs =
+                reinterpret_cast<const float4 *>(a.f + ((long)(a.pt0 + e) * a.S + sp) * n + (long)x0 * NN);
+#pragma unroll
+            for (int j = 0; j < FPT; ++j) {
+                const int i = t + kRows * j;
+                pf[j] = (4 * i < nval * NN) ? fs[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        };
+        int it = blockIdx.x;
+        if (it < items) prefetch(it);
+        for (int j = 0; it < items; ++j, it += gridDim.x) {
+            const int slot = j & 1;
+            const uint32_t use = (uint32_t)(j >> 1) & 1u;
+            const int x0 = (it % NG) * G, nval = min(G, N - x0);
+            uint8_t *AZ = AZ0 + slot * NT * AZB;
+            // every wait is followed by a vote, so that the role's threads leave together
+            if (!pbar_and(bar, ws_wait(&az_empty[slot], use ^ 1u, abort_p) && !*abort_p)) { fail(); break; }
+#pragma unroll
+            for (int jj = 0; jj < FPT; ++jj) {
+                const int i = t + kRows * jj;
+                if (4 * i < nval * NN) tcfmt::st_f4<FMT>(AZ, AZB, (4 * i) / N, (4 * i) % N, pf[jj]);
+            }
+            if constexpr (KR > N) {
+                if (t < nval * N)
+#pragma unroll
+                    for (int term = 0; term < NT; ++term)
+#pragma unroll
+                        for (int e0 = N; e0 < KR; e0 += 8)
+                            *reinterpret_cast<uint4 *>(AZ + term * AZB + sw128_off(t, e0 * Fmt<FMT>::ESZ, kRows)) =
+                                make_uint4(0u, 0u, 0u, 0u);
+            }
+            if (it + (int)gridDim.x < items) prefetch(it + gridDim.x);
+            fence_proxy_async();
+            if (!pbar_and(bar, !*abort_p)) { fail(); break; }
+            if (t == 0) {
+                if (!ws_wait(&d1_empty[slot], use ^ 1u, abort_p)) {
+                    fail();
+                } else {
+                    fence_after();
+                    tcfmt::gemm<FMT>(tb + slot * NO, AZ, AZB, Bz, IR, NO, KR, a.nterms);
+                    commit(&d1_full[slot]);
+                    commit(&az_empty[slot]);
+                }
+            }
+        }
+        if (t == 0) {  // every z-pass issued by this thread has completed
+            commit(&drain[0]);
+            if (!mbar_wait(&drain[0], 0, kWaitLimit)) ok = false;
+        }
+    } else if (role == 1 && ok) {
+        // ---------------------------------------------------- transpose
+        int it = blockIdx.x;
+        for (int j = 0; it < items; ++j, it += gridDim.x) {
+            const int slot = j & 1;
+            const uint32_t use = (uint32_t)(j >> 1) & 1u;
+            const int e = it / NG, x0 = (it % NG) * G, nval = min(G, N - x0);
+            if (!pbar_and(bar, ws_wait(&d1_full[slot], use, abort_p) && !*abort_p)) { fail(); break; }
+            fence_after();
+            if (ident_y) {
+                // sigma_y = 0: T_y = I, row t = (g, y) holds A'(x0+g, y, z') for all z'
+                float2 *dst =
+                    (side == 0 ? a.Ap : a.Bq) + ((long)e * a.RS + rs) * n + (long)(x0 + g) * NN + yl * N;
+                tmem_visit<NO>(tl + slot * NO, [&](int c0, const float *v) {
+                    if (t < nval * N) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            *reinterpret_cast<float4 *>(dst + c0 / 2 + 2 * q) =
+                                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    }
+                });
+                fence_before();
+                pbar(bar);
+                if (t == 0) mbar_arrive(&d1_empty[slot]);
+                continue;
+            }
+            if (!pbar_and(bar, ws_wait(ay_empty, ((uint32_t)j & 1u) ^ 1u, abort_p) && !*abort_p)) { fail(); break; }
+            tmem_visit<NO>(tl + slot * NO, [&](int c0, const float *v) {
+                if (t < nval * N) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        tcfmt::st_c<FMT>(AY, AB, g * N + c0 / 2 + q, yl, v[2 * q], v[2 * q + 1]);
+                }
+            });
+            fence_before();
+            fence_proxy_async();
+            pbar(bar);
+            if (t == 0) {
+                mbar_arrive(&d1_empty[slot]);
+                if (!ws_wait(&d2_empty[slot], use ^ 1u, abort_p)) {
+                    fail();
+                } else {
+                    fence_after();
+                    tcfmt::gemm<FMT>(tb + (2 + slot) * NO, AY, AB, By, IC, NO, KC, a.nterms);
+                    commit(&d2_full[slot]);
+                    commit(ay_empty);
+                }
+            }
+        }
+        if (t == 0) {
+            commit(&drain[1]);
+            if (!mbar_wait(&drain[1], 0, kWaitLimit)) ok = false;
+        }
+    } else if (role == 2 && ok && !ident_y) {
+        // -------------------------------------------------------- store
+        int it = blockIdx.x;
+        for (int j = 0; it < items; ++j, it += gridDim.x) {
+            const int slot = j & 1;
+            const uint32_t use = (uint32_t)(j >> 1) & 1u;
+            const int e = it / NG, x0 = (it % NG) * G, nval = min(G, N - x0);
+            if (!pbar_and(bar, ws_wait(&d2_full[slot], use, abort_p) && !*abort_p)) { fail(); break; }
+            fence_after();
+            // row t = (g, z'): y' values -> global [x][y'][z']
+            float2 *dstp =
+                (side == 0 ? a.Ap : a.Bq) + ((long)e * a.RS + rs) * n + (long)(x0 + g) * NN + (yl & ~1);
+            tmem_visit<NO>(tl + (2 + slot) * NO, [&](int c0, const float *v) {
+                float2 h[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) h[q] = make_float2(v[2 * q], v[2 * q + 1]);
+                store_pair<8>(dstp + (long)(c0 / 2) * N, h, N, t < nval * N);
+            });
+            fence_before();
+            pbar(bar);
+            if (t == 0) mbar_arrive(&d2_empty[slot]);
+        }
+    }
+    if (*abort_p) ok = false;
+    cta_teardown(tslot, NCOL, __syncthreads_and(ok ? 1 : 0) != 0, a.err);
 }
 
 // ------------------------------------------------------------------ stage B
@@ -834,7 +1046,10 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
                 a.Ec = Ec;
                 {
                     ProfScope ps(plan, "tc_stage_a", st);
-                    k_stage_a<N, FMT><<<dim3(ts->groups_a, RS, 2), kRows * NPipes<N, FMT>::A, SM::A, st>>>(a);
+                    if (WsA<N, FMT>::OK && ts->ws_a)
+                        k_stage_a_ws<N, FMT><<<dim3(ts->groups_a, RS, 2), 3 * kRows, WsA<N, FMT>::BYTES, st>>>(a);
+                    else
+                        k_stage_a<N, FMT><<<dim3(ts->groups_a, RS, 2), kRows * NPipes<N, FMT>::A, SM::A, st>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
                 {
@@ -865,6 +1080,9 @@ dgfs_status set_smem_attrs()
 {
     using SM = Smem<N, FMT>;
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_a<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::A));
+    if constexpr (WsA<N, FMT>::OK)
+        DGFS_CUDA(cudaFuncSetAttribute(k_stage_a_ws<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)WsA<N, FMT>::BYTES));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_b<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_c<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::C));
     return DGFS_OK;
@@ -1022,20 +1240,23 @@ dgfs_status tc_autotune(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaSt
     const int RS = plan->Nrho * plan->M;
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plan->device);
-    struct Cand { int chunk, rsb, ga, gb; };
+    struct Cand { int chunk, rsb, ga, gb, ws; };
     std::vector<Cand> cands;
+    const bool ws_fits = plan->N == 16 || plan->N == 24 || plan->N == 32;  // WsA<N, FMT>::OK
     const int chunks[] = {ts->chunk_max, std::min(ts->chunk_max, 8)};
     const int rsbs[] = {std::min(RS, 2), std::min(RS, 4), std::min(RS, 8), std::min(RS, 16)};
     const int waves[] = {4, 8, 16};
     for (int c : chunks)
         for (int r : rsbs)
-            for (int w : waves) {
-                const Cand k{c, std::min(r, ts->rsb_max), std::max(1, (w * sms + RS) / (2 * RS)),
-                             std::max(1, (w * sms + RS / 2) / RS)};
-                bool dup = false;
-                for (auto &o : cands) dup |= o.chunk == k.chunk && o.rsb == k.rsb && o.ga == k.ga && o.gb == k.gb;
-                if (!dup) cands.push_back(k);
-            }
+            for (int w : waves)
+                for (int ws = 0; ws < (ws_fits ? 2 : 1); ++ws) {
+                    const Cand k{c, std::min(r, ts->rsb_max), std::max(1, (w * sms + RS) / (2 * RS)),
+                                 std::max(1, (w * sms + RS / 2) / RS), ws};
+                    bool dup = false;
+                    for (auto &o : cands)
+                        dup |= o.chunk == k.chunk && o.rsb == k.rsb && o.ga == k.ga && o.gb == k.gb && o.ws == k.ws;
+                    if (!dup) cands.push_back(k);
+                }
     cudaEvent_t e0, e1;
     DGFS_CUDA(cudaEventCreate(&e0));
     DGFS_CUDA(cudaEventCreate(&e1));
@@ -1048,6 +1269,7 @@ dgfs_status tc_autotune(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaSt
         ts->rsb = k.rsb;
         ts->groups_a = k.ga;
         ts->groups_b = k.gb;
+        ts->ws_a = k.ws;
         status = tc_collide(plan, P, f, Q, st);
         if (status != DGFS_OK) break;
         double t = 1e300;

@@ -43,10 +43,19 @@ template <int FMT> __host__ __device__ constexpr int abytes(int N) { return atom
 template <int FMT> __host__ __device__ constexpr int img_c(int N) { return atoms_b(2 * N * Fmt<FMT>::ESZ) * 2 * N * 128; }
 template <int FMT> __host__ __device__ constexpr int img_r(int N) { return atoms_b(N * Fmt<FMT>::ESZ) * 2 * N * 128; }
 
+// x rounded to TF32 (10 mantissa bits), to nearest with ties away from zero:
+// add half a TF32 unit to the magnitude bits and clear the 13 low bits.  The
+// same bits as cvt.rna.tf32.f32 for every finite x, on the full-rate integer
+// pipe (the split runs for every operand element the CUDA cores write).
+__device__ __forceinline__ float tf32_round(float x)
+{
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
 __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo)
 {
-    hi = tf32_rna(x);
-    lo = tf32_rna(x - hi);
+    hi = tf32_round(x);
+    lo = tf32_round(x - hi);
 }
 
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &b0, __nv_bfloat16 &b1, __nv_bfloat16 &b2)

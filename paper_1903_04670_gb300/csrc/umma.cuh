@@ -77,6 +77,11 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
 // Waits for the phase with the given parity to complete; gives up after
 // `limit` polls (each poll may suspend briefly) and returns false.
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, long limit)
