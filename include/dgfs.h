@@ -242,6 +242,17 @@ dgfs_status dgfs_graph_destroy(dgfs_graph graph);
 dgfs_status dgfs_plan_autotune(dgfs_plan plan, int P, const void *f_dev, void *Q_dev, void *stream,
                                double *best_ms);
 
+/* Tensor-core plans: choose the kernel of the first plane stage (T_z, T_y),
+ * the one contraction stage with alternative implementations:
+ *   0  two 128-thread pipelines per CTA, each thread one operand row (default);
+ *   1  warp-specialised: load, transpose and store warpgroups hand items on
+ *      through double-buffered shared memory and TMEM (N = 16, 24, 32);
+ *   2  256-thread pipelines, two threads per operand row (N = 16, 32, 48).
+ * All give the same results to rounding; dgfs_plan_autotune times those that
+ * fit and keeps the fastest.  Errors: EINVAL, EUNSUPPORTED (FP64 plan, or the
+ * variant does not fit N). */
+dgfs_status dgfs_plan_set_kernel_variant(dgfs_plan plan, int variant);
+
 /* Number of the library's kernels launched since the plan was created
  * (host-side counter of launches enqueued by dgfs_* calls on this plan). */
 dgfs_status dgfs_plan_launch_count(dgfs_plan plan, long long *count);

@@ -381,6 +381,12 @@ dgfs_status dgfs_collide(dgfs_plan plan, int P, const void *f_dev, void *Q_dev, 
     return tc_collide(plan, P, f_dev, Q_dev, s);
 }
 
+dgfs_status dgfs_plan_set_kernel_variant(dgfs_plan plan, int variant)
+{
+    if (!plan) return DGFS_EINVAL;
+    return tc_set_variant(plan, variant);
+}
+
 dgfs_status dgfs_plan_set_collapse(dgfs_plan plan, int enable)
 {
     if (!plan) return DGFS_EINVAL;

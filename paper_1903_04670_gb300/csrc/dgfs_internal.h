@@ -125,6 +125,7 @@ dgfs_status tc_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStr
 size_t tc_workspace_bytes(const dgfs_plan_s *plan);
 dgfs_status tc_check(dgfs_plan_s *plan);
 bool tc_supports_collapse(const dgfs_plan_s *plan);
+dgfs_status tc_set_variant(dgfs_plan_s *plan, int variant);
 dgfs_status tc_selftest_wait(dgfs_plan_s *plan, int expire, cudaStream_t st);
 void tc_info(const dgfs_plan_s *plan, double *info);
 dgfs_status tc_autotune(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st, double *best_ms);

@@ -62,7 +62,7 @@ struct TcState {
     int tuned = 0;
     uint8_t *idmask = nullptr;  // [RS] bit d set when sigma_{s,d} == 0 (T_d is the identity; x and y are skipped)
     int skip_identity = 1;
-    int ws_a = 0;  // 1: warp-specialised plane stage A (an autotuner choice where it fits)
+    int ws_a = 0;  // stage A variant: 0 two-pipeline, 1 warp-specialised, 2 two threads per row (autotuner)
 };
 
 struct TcArgs {
@@ -382,6 +382,156 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs 
         // row t = (g, z'): y' values -> global [x][y'][z']
         float2 *dstp = (side == 0 ? a.Ap : a.Bq) + ((long)e * a.RS + rs) * n + (long)(x0 + g) * NN + (yl & ~1);
         tmem_visit<NO>(tl + NO, [&](int c0, const float *v) {
+            float2 h[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) h[j] = make_float2(v[2 * j], v[2 * j + 1]);
+            store_pair<8>(dstp + (long)(c0 / 2) * N, h, N, t < nval * N);
+        });
+    }
+    cta_teardown(tslot, NCOL, ok, a.err);
+}
+
+// ------------------------------------------- stage A, two threads per row
+// The plane stage with 256-thread pipelines: the two threads of a row split
+// its columns (TMEM lanes are shared by warps w and w + 4), halving the work
+// and registers per thread so that twice the warps fit on an SM.
+template <int COUNT>
+__device__ __forceinline__ void pbar_n(int id)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(COUNT) : "memory");
+}
+
+template <int COUNT>
+__device__ __forceinline__ bool pbar_and_n(int id, bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)(v ? 1 : 0)), "r"(id), "n"(COUNT)
+        : "memory");
+    return r != 0;
+}
+
+template <int COUNT, typename F>
+__device__ __forceinline__ bool run_mma_n(uint64_t *mbar, uint32_t &phase, int bar_id, F issue)
+{
+    fence_proxy_async();
+    fence_before();
+    pbar_n<COUNT>(bar_id);
+    fence_after();
+    if ((threadIdx.x % COUNT) == 0) {
+        issue();
+        commit(mbar);
+    }
+    const bool ok = mbar_wait(mbar, phase, kWaitLimit);
+    phase ^= 1u;
+    const bool all = pbar_and_n<COUNT>(bar_id, ok);
+    fence_after();
+    return all;
+}
+
+template <int N, int FMT> struct A2 {
+    static constexpr int NP = NPipes<N, FMT>::A;
+    static constexpr bool OK = Smem<N, FMT>::RES_A && (2 * N) % 32 == 0 && NP * 2 * kRows <= 1024;
+};
+
+template <int N, int FMT>
+__global__ void __launch_bounds__(2 * kRows * NPipes<N, FMT>::A, 1) k_stage_a2(TcArgs a)
+{
+    using SM = Smem<N, FMT>;
+    constexpr int NP = NPipes<N, FMT>::A, NT = SM::NT, AB = SM::AB, IR = SM::IR, IC = SM::IC;
+    constexpr int PT = 2 * kRows;  // threads per pipeline
+    constexpr int G = kRows / N, KC = 2 * N, NO = 2 * N, NH = N, NG = (N + G - 1) / G;  // NH: columns per thread
+    constexpr int KR = FMT == 1 ? (N + 15) / 16 * 16 : N;
+    constexpr int NN = N * N;
+    constexpr int FPT = (G * NN / 4 + PT - 1) / PT;  // float4 per thread for one group
+    constexpr uint32_t NCOL = pow2_cols(NP * 2 * NO);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = align1024(smem_raw);
+    const int pp = threadIdx.x / PT, tt = threadIdx.x % PT, t = tt % kRows, hf = tt / kRows, bar = 1 + pp;
+    uint8_t *Bz = sm;
+    uint8_t *By = Bz + NT * IR;
+    uint8_t *A0 = sm + NT * (IR + IC) + pp * NT * AB;
+    __shared__ uint64_t mb[NP + 1];
+    __shared__ uint32_t tslot;
+    const int rs = blockIdx.y, side = blockIdx.z;
+    const long n = a.n;
+    const int items = a.Ec * NG;
+    const bool ident_y = a.idmask && (a.idmask[rs] & 2);
+    cta_setup(&tslot, NCOL, mb, NP + 1);
+    const uint32_t tb = tslot + pp * 2 * NO, tl = lane_base(tb) + hf * NH;  // this thread's column half
+    uint32_t ph_mma = 0, ph_cp = 0;
+    const int sp = side == 0 ? a.p : a.q;
+    const int g = t / N, yl = t % N;
+    float4 pf[FPT];
+    auto prefetch = [&](int it) {
+        const int e = it / NG, x0 = (it % NG) * G, nval = min(G, N - x0);
+        const float4 *fs =
+            reinterpret_cast<const float4 *>(a.f + ((long)(a.pt0 + e) * a.S + sp) * n + (long)x0 * NN);
+#pragma unroll
+        for (int j = 0; j < FPT; ++j) {
+            const int i = tt + PT * j;
+            pf[j] = (4 * i < nval * NN) ? fs[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    const int stride = gridDim.x * NP;
+    int it = blockIdx.x * NP + pp;
+    if (it < items) prefetch(it);
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&mb[NP], NT * (IR + IC));
+        copy_terms(Bz, IR, timg_at<FMT>(a.timg, N, rs, side, 2), IC, IR, NT, &mb[NP]);
+        copy_terms(By, IC, timg_at<FMT>(a.timg, N, rs, side, 1), IC, IC, NT, &mb[NP]);
+    }
+    bool ok = wait_copy_cta(&mb[NP], ph_cp);
+    for (; it < items && ok; it += stride) {
+        const int e = it / NG, x0 = (it % NG) * G, nval = min(G, N - x0);
+#pragma unroll
+        for (int j = 0; j < FPT; ++j) {
+            const int i = tt + PT * j;
+            if (4 * i < nval * NN) tcfmt::st_f4<FMT>(A0, AB, (4 * i) / N, (4 * i) % N, pf[j]);
+        }
+        if constexpr (KR > N) {  // zero the pad of the row (first thread of the row)
+            if (hf == 0 && t < nval * N)
+#pragma unroll
+                for (int term = 0; term < NT; ++term)
+#pragma unroll
+                    for (int e0 = N; e0 < KR; e0 += 8)
+                        *reinterpret_cast<uint4 *>(A0 + term * AB + sw128_off(t, e0 * Fmt<FMT>::ESZ, kRows)) =
+                            make_uint4(0u, 0u, 0u, 0u);
+        }
+        if (it + stride < items) prefetch(it + stride);
+        ok = run_mma_n<PT>(&mb[pp], ph_mma, bar, [&] { tcfmt::gemm<FMT>(tb, A0, AB, Bz, IR, NO, KR, a.nterms); });
+        if (!ok) break;
+        if (ident_y) {
+            float2 *dst = (side == 0 ? a.Ap : a.Bq) + ((long)e * a.RS + rs) * n + (long)(x0 + g) * NN + yl * N +
+                          hf * (NH / 2);
+            tmem_visit<NH>(tl, [&](int c0, const float *v) {
+                if (t < nval * N) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        *reinterpret_cast<float4 *>(dst + c0 / 2 + 2 * j) =
+                            make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                }
+            });
+            continue;
+        }
+        // transpose within each plane: row (g, y) holds z' -> rows (g, z'), K = y
+        tmem_visit<NH>(tl, [&](int c0, const float *v) {
+            if (t < nval * N) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    tcfmt::st_c<FMT>(A0, AB, g * N + hf * (NH / 2) + c0 / 2 + j, yl, v[2 * j], v[2 * j + 1]);
+            }
+        });
+        ok = run_mma_n<PT>(&mb[pp], ph_mma, bar,
+                           [&] { tcfmt::gemm<FMT>(tb + NO, A0, AB, By, IC, NO, KC, a.nterms); });
+        if (!ok) break;
+        // row t = (g, z'): this thread's half of the y' values -> global [x][y'][z']
+        float2 *dstp = (side == 0 ? a.Ap : a.Bq) + ((long)e * a.RS + rs) * n + (long)(x0 + g) * NN + (yl & ~1) +
+                       (long)hf * (NH / 2) * N;
+        tmem_visit<NH>(tl + NO, [&](int c0, const float *v) {
             float2 h[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) h[j] = make_float2(v[2 * j], v[2 * j + 1]);
@@ -1046,8 +1196,10 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
                 a.Ec = Ec;
                 {
                     ProfScope ps(plan, "tc_stage_a", st);
-                    if (WsA<N, FMT>::OK && ts->ws_a)
+                    if (WsA<N, FMT>::OK && ts->ws_a == 1)
                         k_stage_a_ws<N, FMT><<<dim3(ts->groups_a, RS, 2), 3 * kRows, WsA<N, FMT>::BYTES, st>>>(a);
+                    else if (A2<N, FMT>::OK && ts->ws_a == 2)
+                        k_stage_a2<N, FMT><<<dim3(ts->groups_a, RS, 2), 2 * kRows * NPipes<N, FMT>::A, SM::A, st>>>(a);
                     else
                         k_stage_a<N, FMT><<<dim3(ts->groups_a, RS, 2), kRows * NPipes<N, FMT>::A, SM::A, st>>>(a);
                 }
@@ -1083,6 +1235,8 @@ dgfs_status set_smem_attrs()
     if constexpr (WsA<N, FMT>::OK)
         DGFS_CUDA(cudaFuncSetAttribute(k_stage_a_ws<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)WsA<N, FMT>::BYTES));
+    if constexpr (A2<N, FMT>::OK)
+        DGFS_CUDA(cudaFuncSetAttribute(k_stage_a2<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::A));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_b<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_c<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::C));
     return DGFS_OK;
@@ -1243,13 +1397,15 @@ dgfs_status tc_autotune(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaSt
     struct Cand { int chunk, rsb, ga, gb, ws; };
     std::vector<Cand> cands;
     const bool ws_fits = plan->N == 16 || plan->N == 24 || plan->N == 32;  // WsA<N, FMT>::OK
+    const bool a2_fits = plan->N == 16 || plan->N == 32 || plan->N == 48;  // A2<N, FMT>::OK
     const int chunks[] = {ts->chunk_max, std::min(ts->chunk_max, 8)};
     const int rsbs[] = {std::min(RS, 2), std::min(RS, 4), std::min(RS, 8), std::min(RS, 16)};
     const int waves[] = {4, 8, 16};
     for (int c : chunks)
         for (int r : rsbs)
             for (int w : waves)
-                for (int ws = 0; ws < (ws_fits ? 2 : 1); ++ws) {
+                for (int ws = 0; ws < 3; ++ws) {
+                    if ((ws == 1 && !ws_fits) || (ws == 2 && !a2_fits)) continue;
                     const Cand k{c, std::min(r, ts->rsb_max), std::max(1, (w * sms + RS) / (2 * RS)),
                                  std::max(1, (w * sms + RS / 2) / RS), ws};
                     bool dup = false;
@@ -1326,6 +1482,26 @@ dgfs_status tc_selftest_wait(dgfs_plan_s *plan, int expire, cudaStream_t st)
 
 // the plane stage sums the tiles of a radial node's directions (stage C)
 bool tc_supports_collapse(const dgfs_plan_s *) { return true; }
+
+// Select the plane-stage-A kernel (0 two-pipeline, 1 warp-specialised, 2 two
+// threads per row); the autotuner times all that fit.
+dgfs_status tc_set_variant(dgfs_plan_s *plan, int variant)
+{
+    TcState *ts = reinterpret_cast<TcState *>(plan->tc);
+    if (!ts) {
+        set_error("dgfs_plan_set_kernel_variant: only tensor-core plans have kernel variants");
+        return DGFS_EUNSUPPORTED;
+    }
+    const int N = plan->N;
+    const bool fits = variant == 0 || (variant == 1 && (N == 16 || N == 24 || N == 32)) ||
+                      (variant == 2 && (N == 16 || N == 32 || N == 48));
+    if (!fits) {
+        set_error("dgfs_plan_set_kernel_variant: variant not available for this N");
+        return variant < 0 || variant > 2 ? DGFS_EINVAL : DGFS_EUNSUPPORTED;
+    }
+    ts->ws_a = variant;
+    return DGFS_OK;
+}
 
 dgfs_status tc_check(dgfs_plan_s *plan)
 {

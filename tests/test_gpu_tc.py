@@ -169,3 +169,35 @@ def test_split_bf16_c2_and_n48():
     prob = O.Problem(N, L, 6, 3, [1.0, 2.0], pairs)
     Qo, _ = prob.pair(0, 1).collide(f[0, 0], f[0, 1])
     assert _rel(Qg[0, 0, 1], Qo) < TOL_BF16X3
+
+
+@pytest.mark.parametrize("prec", ["fp32_tc", "bf16x3"])
+@pytest.mark.parametrize("N,M,Nrho,S,P,variant", [
+    (16, 12, 3, 2, 3, 1), (24, 6, 3, 2, 2, 1), (32, 12, 2, 2, 2, 1),
+    (16, 6, 3, 3, 2, 2), (32, 12, 2, 2, 2, 2), (48, 6, 2, 2, 1, 2),
+])
+def test_stage_a_kernel_variants(prec, N, M, Nrho, S, P, variant):
+    """Every plane-stage-A kernel the autotuner may pick gives the same
+    operator (vs the oracle) and the same result as the default kernel to
+    rounding; variants that do not fit N are refused."""
+    rng = np.random.default_rng(N * 10 + variant)
+    masses = [1.0, 2.0, 4.0][:S]
+    pairs = W.pair_params([0.81, 0.75, 0.7][:S], [1.0, 1.4, 1.2][:S], [1.0, 1.2, 0.9][:S])
+    L = N / 3.2
+    f = np.stack([np.stack([W.two_maxwellians(rng, N, L, m) for m in masses]) for _ in range(P)])
+    pb = dict(N=N, L=L, M=M, Nrho=Nrho, masses=masses, pairs=pairs)
+    plan = B.Plan(N, L, M, Nrho, masses, pairs, prec, P)
+    fd = torch.from_numpy(f).to("cuda", torch.float32)
+    Q0 = plan.collide(fd).double().cpu().numpy()
+    plan.set_kernel_variant(variant)
+    Qv = plan.collide(fd).double().cpu().numpy()
+    plan.check()
+    Qo = _oracle(pb, f)
+    tol = TOL_TC if prec == "fp32_tc" else 1e-3
+    assert np.abs(Qv - Qo).max() <= tol * np.abs(Qo).max()
+    assert np.abs(Qv - Q0).max() <= 1e-6 * np.abs(Qo).max()
+    other = {1: 48, 2: 24}[variant]
+    plan2 = B.Plan(other, other / 3.2, 6, 2, masses, pairs, prec, 1)
+    with pytest.raises(B.DgfsError) as e:
+        plan2.set_kernel_variant(variant)
+    assert e.value.status == 5
