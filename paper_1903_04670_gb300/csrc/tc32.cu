@@ -545,12 +545,13 @@ __global__ void __launch_bounds__(2 * kRows * NPipes<N, FMT>::A, 1) k_stage_a2(T
 // The same plane stage with its three kinds of work on separate warpgroups of
 // one CTA, so that the tensor core works on one item while the CUDA cores
 // prepare the next and drain the previous:
-//   WG0 (load):      f tile -> split -> A_z[slot]; its thread 0 issues the
-//                    z-pass into TMEM D1[slot];
-//   WG1 (transpose): D1[slot] -> in-plane transpose -> A_y; its thread 0
-//                    issues the y-pass into D2[slot] (sigma_y = 0: D1 goes
-//                    straight to global memory instead);
-//   WG2 (store):     D2[slot] -> A' / B' in global memory.
+//   WG0 (load):         f tile -> split -> A_z[slot]; its thread 0 issues the
+//                       z-pass into TMEM D1[slot];
+//   WG1, WG2 (transpose): D1[slot] -> in-plane transpose -> A_y, each half of
+//                       the columns; the first thread issues the y-pass into
+//                       D2[slot] (sigma_y = 0: D1 goes straight to global
+//                       memory instead);
+//   WG3 (store):        D2[slot] -> A' / B' in global memory.
 // Two slots for A_z, D1, D2 and one A_y; every handoff is an mbarrier
 // (full: the MMA's commit or the producer; empty: the consumer) waited on
 // with a bound.  A role whose wait expires raises a CTA-wide abort flag that
@@ -562,7 +563,7 @@ template <int N, int FMT> struct WsA {
     static constexpr int AZB = tcfmt::atoms_b(KR * Fmt<FMT>::ESZ) * kRows * 128;  // one term of A_z
     static constexpr int AB = tcfmt::abytes<FMT>(N), IC = tcfmt::img_c<FMT>(N), IR = tcfmt::img_r<FMT>(N);
     static constexpr size_t BYTES = 1024 + (size_t)NT * (IR + IC) + 2 * (size_t)NT * AZB + (size_t)NT * AB;
-    static constexpr bool OK = BYTES <= kSmemMax && N >= 16;
+    static constexpr bool OK = BYTES <= kSmemMax && N >= 16 && N % 16 == 0;
 };
 
 // bounded wait that also gives up when another role has aborted
@@ -576,11 +577,11 @@ __device__ __forceinline__ bool ws_wait(uint64_t *mbar, uint32_t parity, volatil
 }
 
 template <int N, int FMT>
-__global__ void __launch_bounds__(3 * kRows, 1) k_stage_a_ws(TcArgs a)
+__global__ void __launch_bounds__(4 * kRows, 1) k_stage_a_ws(TcArgs a)
 {
     using W = WsA<N, FMT>;
     constexpr int NT = W::NT, AB = W::AB, IR = W::IR, IC = W::IC, AZB = W::AZB, KR = W::KR;
-    constexpr int G = kRows / N, KC = 2 * N, NO = 2 * N, NG = (N + G - 1) / G, NN = N * N;
+    constexpr int G = kRows / N, KC = 2 * N, NO = 2 * N, NH = N, NG = (N + G - 1) / G, NN = N * N;
     constexpr int FPT = (G * NN / 4 + kRows - 1) / kRows;
     constexpr uint32_t NCOL = pow2_cols(4 * NO);
     extern __shared__ uint8_t smem_raw[];
@@ -595,7 +596,9 @@ __global__ void __launch_bounds__(3 * kRows, 1) k_stage_a_ws(TcArgs a)
     __shared__ int abort_flag;
     uint64_t *az_empty = mb + 1, *d1_full = mb + 3, *d1_empty = mb + 5, *ay_empty = mb + 7, *d2_full = mb + 8,
              *d2_empty = mb + 10, *drain = mb + 12;
-    const int role = threadIdx.x / kRows, t = threadIdx.x % kRows, bar = 1 + role;
+    // roles: 0 load, 1 and 2 transpose (column halves, one 256-thread barrier), 3 store
+    const int wg = threadIdx.x / kRows, t = threadIdx.x % kRows;
+    const int role = wg == 0 ? 0 : wg == 3 ? 2 : 1, hf = wg - 1, bar = 1 + role;
     const int rs = blockIdx.y, side = blockIdx.z;
     const long n = a.n;
     const int items = a.Ec * NG;
@@ -679,13 +682,13 @@ __global__ void __launch_bounds__(3 * kRows, 1) k_stage_a_ws(TcArgs a)
             const int slot = j & 1;
             const uint32_t use = (uint32_t)(j >> 1) & 1u;
             const int e = it / NG, x0 = (it % NG) * G, nval = min(G, N - x0);
-            if (!pbar_and(bar, ws_wait(&d1_full[slot], use, abort_p) && !*abort_p)) { fail(); break; }
+            if (!pbar_and_n<2 * kRows>(bar, ws_wait(&d1_full[slot], use, abort_p) && !*abort_p)) { fail(); break; }
             fence_after();
             if (ident_y) {
                 // sigma_y = 0: T_y = I, row t = (g, y) holds A'(x0+g, y, z') for all z'
-                float2 *dst =
-                    (side == 0 ? a.Ap : a.Bq) + ((long)e * a.RS + rs) * n + (long)(x0 + g) * NN + yl * N;
-                tmem_visit<NO>(tl + slot * NO, [&](int c0, const float *v) {
+                float2 *dst = (side == 0 ? a.Ap : a.Bq) + ((long)e * a.RS + rs) * n + (long)(x0 + g) * NN +
+                              yl * N + hf * (NH / 2);
+                tmem_visit<NH>(tl + slot * NO + hf * NH, [&](int c0, const float *v) {
                     if (t < nval * N) {
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
@@ -694,22 +697,25 @@ __global__ void __launch_bounds__(3 * kRows, 1) k_stage_a_ws(TcArgs a)
                     }
                 });
                 fence_before();
-                pbar(bar);
-                if (t == 0) mbar_arrive(&d1_empty[slot]);
+                pbar_n<2 * kRows>(bar);
+                if (hf == 0 && t == 0) mbar_arrive(&d1_empty[slot]);
                 continue;
             }
-            if (!pbar_and(bar, ws_wait(ay_empty, ((uint32_t)j & 1u) ^ 1u, abort_p) && !*abort_p)) { fail(); break; }
-            tmem_visit<NO>(tl + slot * NO, [&](int c0, const float *v) {
+            if (!pbar_and_n<2 * kRows>(bar, ws_wait(ay_empty, ((uint32_t)j & 1u) ^ 1u, abort_p) && !*abort_p)) {
+                fail();
+                break;
+            }
+            tmem_visit<NH>(tl + slot * NO + hf * NH, [&](int c0, const float *v) {
                 if (t < nval * N) {
 #pragma unroll
                     for (int q = 0; q < 8; ++q)
-                        tcfmt::st_c<FMT>(AY, AB, g * N + c0 / 2 + q, yl, v[2 * q], v[2 * q + 1]);
+                        tcfmt::st_c<FMT>(AY, AB, g * N + hf * (NH / 2) + c0 / 2 + q, yl, v[2 * q], v[2 * q + 1]);
                 }
             });
             fence_before();
             fence_proxy_async();
-            pbar(bar);
-            if (t == 0) {
+            pbar_n<2 * kRows>(bar);
+            if (hf == 0 && t == 0) {
                 mbar_arrive(&d1_empty[slot]);
                 if (!ws_wait(&d2_empty[slot], use ^ 1u, abort_p)) {
                     fail();
@@ -721,7 +727,7 @@ __global__ void __launch_bounds__(3 * kRows, 1) k_stage_a_ws(TcArgs a)
                 }
             }
         }
-        if (t == 0) {
+        if (hf == 0 && t == 0) {
             commit(&drain[1]);
             if (!mbar_wait(&drain[1], 0, kWaitLimit)) ok = false;
         }
@@ -1197,7 +1203,7 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
                 {
                     ProfScope ps(plan, "tc_stage_a", st);
                     if (WsA<N, FMT>::OK && ts->ws_a == 1)
-                        k_stage_a_ws<N, FMT><<<dim3(ts->groups_a, RS, 2), 3 * kRows, WsA<N, FMT>::BYTES, st>>>(a);
+                        k_stage_a_ws<N, FMT><<<dim3(ts->groups_a, RS, 2), 4 * kRows, WsA<N, FMT>::BYTES, st>>>(a);
                     else if (A2<N, FMT>::OK && ts->ws_a == 2)
                         k_stage_a2<N, FMT><<<dim3(ts->groups_a, RS, 2), 2 * kRows * NPipes<N, FMT>::A, SM::A, st>>>(a);
                     else
@@ -1396,7 +1402,7 @@ dgfs_status tc_autotune(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaSt
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plan->device);
     struct Cand { int chunk, rsb, ga, gb, ws; };
     std::vector<Cand> cands;
-    const bool ws_fits = plan->N == 16 || plan->N == 24 || plan->N == 32;  // WsA<N, FMT>::OK
+    const bool ws_fits = plan->N == 16 || plan->N == 32;  // WsA<N, FMT>::OK
     const bool a2_fits = plan->N == 16 || plan->N == 32 || plan->N == 48;  // A2<N, FMT>::OK
     const int chunks[] = {ts->chunk_max, std::min(ts->chunk_max, 8)};
     const int rsbs[] = {std::min(RS, 2), std::min(RS, 4), std::min(RS, 8), std::min(RS, 16)};
@@ -1493,7 +1499,7 @@ dgfs_status tc_set_variant(dgfs_plan_s *plan, int variant)
         return DGFS_EUNSUPPORTED;
     }
     const int N = plan->N;
-    const bool fits = variant == 0 || (variant == 1 && (N == 16 || N == 24 || N == 32)) ||
+    const bool fits = variant == 0 || (variant == 1 && (N == 16 || N == 32)) ||
                       (variant == 2 && (N == 16 || N == 32 || N == 48));
     if (!fits) {
         set_error("dgfs_plan_set_kernel_variant: variant not available for this N");

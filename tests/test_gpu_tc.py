@@ -173,7 +173,7 @@ def test_split_bf16_c2_and_n48():
 
 @pytest.mark.parametrize("prec", ["fp32_tc", "bf16x3"])
 @pytest.mark.parametrize("N,M,Nrho,S,P,variant", [
-    (16, 12, 3, 2, 3, 1), (24, 6, 3, 2, 2, 1), (32, 12, 2, 2, 2, 1),
+    (16, 12, 3, 2, 3, 1), (32, 6, 3, 3, 1, 1), (32, 12, 2, 2, 2, 1),
     (16, 6, 3, 3, 2, 2), (32, 12, 2, 2, 2, 2), (48, 6, 2, 2, 1, 2),
 ])
 def test_stage_a_kernel_variants(prec, N, M, Nrho, S, P, variant):
