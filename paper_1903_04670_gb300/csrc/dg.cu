@@ -53,7 +53,7 @@ struct DgCoef {
 
 __device__ __forceinline__ double cx_of(long v, int N, double L)
 {
-    const int ix = (int)(v / ((long)N * N));
+    const int ix = (int)((uint32_t)v / (uint32_t)(N * N));  // n = N^3 < 2^31
     return -L + (ix + 0.5) * (2.0 * L / N);
 }
 
@@ -112,8 +112,10 @@ __global__ void k_dg(const T *f, const T *Q, const T *f0, T *out, DgCoef cf, con
 {
     const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long)Ne * S * n) return;
-    const long v = gid % n;
-    const int p = (int)((gid / n) % S), e = (int)(gid / (n * S));
+    // 32-bit index arithmetic: Ne S n < 2^31 (checked when the DG object is created)
+    const uint32_t g32 = (uint32_t)gid, n32 = (uint32_t)n, ps = g32 / n32;
+    const long v = g32 - ps * n32;
+    const int p = (int)(ps % (uint32_t)S), e = (int)(ps / (uint32_t)S);
     const double cx = cx_of(v, N, L);
     auto at = [&](int node) { return ((long)node * S + p) * n + v; };
     double u[K];
@@ -403,7 +405,7 @@ dgfs_status dgfs_dg_create(dgfs_dg *out, dgfs_plan plan, int Ne, int K, double x
     if (!out) return DGFS_EINVAL;
     *out = nullptr;
     if (!plan || !walls || Ne < 1 || K < 1 || K > kMaxK || !(x1 > x0) || plan->S > 4 ||
-        (long)Ne * K > plan->max_points) {
+        (long)Ne * K > plan->max_points || (long)Ne * K * plan->S * plan->N * plan->N * plan->N >= (1L << 31)) {
         set_error("dgfs_dg_create: bad plan, walls, Ne, K (1..5), interval or Ne*K > max_points");
         return DGFS_EINVAL;
     }
