@@ -37,6 +37,7 @@ extern "C" {
 
 typedef struct dgfs_plan_s *dgfs_plan;
 typedef struct dgfs_graph_s *dgfs_graph;
+typedef struct dgfs_batch_s *dgfs_batch;
 typedef struct dgfs_dg_s *dgfs_dg;
 
 typedef enum {
@@ -231,6 +232,36 @@ dgfs_status dgfs_graph_kernel_count(dgfs_graph graph, long long *count);
 
 /* Release a graph (synchronises its device).  NULL is accepted. */
 dgfs_status dgfs_graph_destroy(dgfs_graph graph);
+
+/* Batched work list over uneven instances (several plans with their own N,
+ * S, M, N_rho, precision and point counts), the launch-level form of the
+ * batching over independent problems (Sec. 3.3: every spatial point and
+ * species pair is one evaluation of Algorithm 2).  Instance i evaluates
+ * Q^(pq) of f_dev[i] ([P[i]][S][N^3] on the plan's device, 16-byte aligned for
+ * tensor-core plans) into Q_dev[i] ([P[i]][S][S][N^3]) exactly as
+ * dgfs_collide would; with dt != 0 each launch then applies
+ * dgfs_relax_step(plans[i], P[i], f_dev[i], Q_dev[i], dt).  The tensor-core
+ * instances that share N and the operand format run their stages together:
+ * round k launches each stage once over the k-th (species pair, chunk of
+ * points) job of every such instance, each CTA finding its job in a device
+ * table; FP64 instances run their own collision call.  The pointers are fixed
+ * at creation (their contents may change between launches); plans must be
+ * distinct, on one device, and not used elsewhere while the batch runs.  A plan
+ * whose launch configuration changes afterwards (dgfs_plan_autotune,
+ * dgfs_plan_set_kernel_variant, dgfs_plan_set_collapse) makes the batch stale:
+ * dgfs_batch_launch then returns EINVAL and a new batch is needed.  Stage A
+ * runs its default kernel variant in a batch.  *out receives the batch.
+ * Errors: EINVAL (bad or repeated instance, misaligned f), ENOMEM, ECUDA,
+ * EUNSUPPORTED. */
+dgfs_status dgfs_batch_create(int count, const dgfs_plan *plans, const int *P, void *const *f_dev,
+                              void *const *Q_dev, double dt, dgfs_batch *out);
+
+/* Enqueue one pass of the batch on `stream` (asynchronous; capturable into a
+ * CUDA graph).  Errors: EINVAL (NULL or stale batch), ECUDA. */
+dgfs_status dgfs_batch_launch(dgfs_batch batch, void *stream);
+
+/* Release a batch (synchronises its device).  NULL is accepted. */
+dgfs_status dgfs_batch_destroy(dgfs_batch batch);
 
 /* Autotuner for tensor-core plans: times candidate launch configurations
  * (points per launch, (r, s) blocks of the accumulation stage, CTA counts of

@@ -64,6 +64,9 @@ def lib():
             "dgfs_graph_launch": (i, [_P, _P]),
             "dgfs_graph_kernel_count": (i, [_P, ctypes.POINTER(ll)]),
             "dgfs_graph_destroy": (i, [_P]),
+            "dgfs_batch_create": (i, [i, _P, _P, _P, _P, d, ctypes.POINTER(_P)]),
+            "dgfs_batch_launch": (i, [_P, _P]),
+            "dgfs_batch_destroy": (i, [_P]),
             "dgfs_plan_autotune": (i, [_P, i, _P, _P, _P, ctypes.POINTER(d)]),
             "dgfs_plan_profile_read": (i, [_P, i, _P, _P, _P, ctypes.POINTER(i)]),
             "dgfs_plan_set_collapse": (i, [_P, i]),
@@ -253,6 +256,28 @@ def dgfs_graph_kernel_count(g):
 
 def dgfs_graph_destroy(g):
     _check(lib().dgfs_graph_destroy(g), "dgfs_graph_destroy")
+
+
+def dgfs_batch_create(plans, Ps, fs, Qs, dt=0.0):
+    """plans: list of distinct plan handles; fs, Qs: lists of device tensors
+    (their addresses are fixed in the batch)."""
+    k = len(plans)
+    ph = (_P * k)(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in plans])
+    pp = (ctypes.c_int * k)(*[int(x) for x in Ps])
+    fp = (_P * k)(*[t.data_ptr() for t in fs])
+    qp = (_P * k)(*[t.data_ptr() for t in Qs])
+    b = _P()
+    _check(lib().dgfs_batch_create(k, ctypes.cast(ph, _P), ctypes.cast(pp, _P), ctypes.cast(fp, _P),
+                                   ctypes.cast(qp, _P), float(dt), ctypes.byref(b)), "dgfs_batch_create")
+    return b
+
+
+def dgfs_batch_launch(b, stream=None):
+    _check(lib().dgfs_batch_launch(b, _stream(stream)), "dgfs_batch_launch")
+
+
+def dgfs_batch_destroy(b):
+    _check(lib().dgfs_batch_destroy(b), "dgfs_batch_destroy")
 
 
 def dgfs_plan_autotune(h, P, f, Q, stream=None):

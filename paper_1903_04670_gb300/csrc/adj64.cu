@@ -375,12 +375,6 @@ __global__ void k_omega_reduce(double *domega, int pair, const double *dots, con
 
 constexpr int kAdjThreads = 64;
 
-#define DGFS_TRY(x)                   \
-    do {                              \
-        dgfs_status s_ = (x);         \
-        if (s_ != DGFS_OK) return s_; \
-    } while (0)
-
 template <int N, int AXIS, int MODE>
 dgfs_status alaunch(dgfs_plan_s *plan, dim3 grid, const AdjArgs &a, cudaStream_t st)
 {

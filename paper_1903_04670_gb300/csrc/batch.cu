@@ -5,6 +5,9 @@
 //    collision calls (and optional relaxation steps) of a batch of uneven
 //    instances, i.e. several plans with different N, S, M, N_rho and point
 //    counts, replayed with a single launch,
+//  - dgfs_batch_create / _launch / _destroy: a batched work list over uneven
+//    instances; each tensor-core stage runs as one launch over the jobs of
+//    all instances that share N and the operand format,
 //  - dgfs_plan_autotune: times candidate launch configurations of a
 //    tensor-core plan on the caller's data and keeps the fastest.
 #include <algorithm>
@@ -56,6 +59,17 @@ struct dgfs_graph_s {
     cudaStream_t capture_stream = nullptr;
     int device = 0;
     long long kernels = 0;
+};
+
+struct dgfs_batch_s {
+    std::vector<dgfs_plan_s *> plans;
+    std::vector<unsigned> gens;  // config_gen of each plan at creation
+    std::vector<int> P;
+    std::vector<const void *> f;
+    std::vector<void *> Q;
+    double dt = 0.0;
+    void *tc = nullptr;  // tensor-core work list (tc32.cu), null without TC plans
+    int device = 0;
 };
 
 using namespace dgfs;
@@ -129,6 +143,89 @@ dgfs_status dgfs_graph_capture(int count, const dgfs_plan *plans, const int *P, 
         return st;
     }
     *out = g;
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_batch_create(int count, const dgfs_plan *plans, const int *P, void *const *f_dev,
+                              void *const *Q_dev, double dt, dgfs_batch *out)
+{
+    if (!out || count < 1 || !plans || !P || !f_dev || !Q_dev) {
+        set_error("dgfs_batch_create: bad arguments");
+        return DGFS_EINVAL;
+    }
+    *out = nullptr;
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i] || !f_dev[i] || !Q_dev[i] || P[i] < 1 || P[i] > plans[i]->max_points ||
+            plans[i]->device != plans[0]->device) {
+            set_error("dgfs_batch_create: bad instance (plan, pointers, P, or plans on different devices)");
+            return DGFS_EINVAL;
+        }
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) {
+                set_error("dgfs_batch_create: a plan appears twice (each instance needs its own workspace)");
+                return DGFS_EINVAL;
+            }
+    }
+    dgfs_status st = plan_entry_check(plans[0]);
+    if (st != DGFS_OK) return st;
+    dgfs_batch_s *b = new (std::nothrow) dgfs_batch_s();
+    if (!b) return DGFS_ENOMEM;
+    b->device = plans[0]->device;
+    b->dt = dt;
+    std::vector<dgfs_plan_s *> tcp;
+    std::vector<int> tcP;
+    std::vector<void *> tcf, tcQ;
+    for (int i = 0; i < count; ++i) {
+        b->plans.push_back(plans[i]);
+        b->gens.push_back(plans[i]->config_gen);
+        b->P.push_back(P[i]);
+        b->f.push_back(f_dev[i]);
+        b->Q.push_back(Q_dev[i]);
+        if (plans[i]->prec != DGFS_FP64) {
+            tcp.push_back(plans[i]);
+            tcP.push_back(P[i]);
+            tcf.push_back(f_dev[i]);
+            tcQ.push_back(Q_dev[i]);
+        }
+    }
+    if (!tcp.empty()) {
+        st = tc_batch_build((int)tcp.size(), tcp.data(), tcP.data(), tcf.data(), tcQ.data(), &b->tc);
+        if (st != DGFS_OK) {
+            delete b;
+            return st;
+        }
+    }
+    *out = b;
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_batch_launch(dgfs_batch b, void *stream)
+{
+    if (!b) return DGFS_EINVAL;
+    for (size_t i = 0; i < b->plans.size(); ++i)
+        if (b->plans[i]->config_gen != b->gens[i]) {
+            set_error("dgfs_batch_launch: a plan's launch configuration changed after the batch was created");
+            return DGFS_EINVAL;
+        }
+    dgfs_status st = plan_entry_check(b->plans[0]);
+    if (st != DGFS_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    for (size_t i = 0; i < b->plans.size(); ++i)
+        if (b->plans[i]->prec == DGFS_FP64) DGFS_TRY(fp64_collide(b->plans[i], b->P[i], b->f[i], b->Q[i], s));
+    if (b->tc) DGFS_TRY(tc_batch_launch(b->tc, s));
+    if (b->dt != 0.0)
+        for (size_t i = 0; i < b->plans.size(); ++i)
+            DGFS_TRY(relax_step(b->plans[i], b->P[i], const_cast<void *>(b->f[i]), b->Q[i], b->dt, s));
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_batch_destroy(dgfs_batch b)
+{
+    if (!b) return DGFS_OK;
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    tc_batch_free(b->tc);
+    delete b;
     return DGFS_OK;
 }
 

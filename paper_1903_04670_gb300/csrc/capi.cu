@@ -396,6 +396,7 @@ dgfs_status dgfs_plan_set_collapse(dgfs_plan plan, int enable)
         return DGFS_EUNSUPPORTED;
     }
     plan->collapse = enable ? 1 : 0;
+    plan->config_gen++;
     return DGFS_OK;
 }
 

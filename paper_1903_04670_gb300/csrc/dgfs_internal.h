@@ -61,6 +61,9 @@ struct dgfs_plan_s {
     void *tc = nullptr;
     // 1: sum over design directions before the forward transforms (VHS only)
     int collapse = 0;
+    // bumped whenever the launch configuration changes (collapse, kernel
+    // variant, autotuning); a batch built on an older configuration is stale
+    unsigned config_gen = 0;
     // per-kernel CUDA-event profiler (capi.cu), null unless enabled
     void *prof = nullptr;
 };
@@ -82,6 +85,12 @@ dgfs_status cuda_status(cudaError_t e, const char *what);
         (plan)->launches++;                                                \
         cudaError_t e_ = cudaGetLastError();                               \
         if (e_ != cudaSuccess) return ::dgfs::cuda_status(e_, "kernel launch"); \
+    } while (0)
+
+#define DGFS_TRY(x)                   \
+    do {                              \
+        dgfs_status s_ = (x);         \
+        if (s_ != DGFS_OK) return s_; \
     } while (0)
 
 size_t elem_size(const dgfs_plan_s *plan);
@@ -126,6 +135,10 @@ size_t tc_workspace_bytes(const dgfs_plan_s *plan);
 dgfs_status tc_check(dgfs_plan_s *plan);
 bool tc_supports_collapse(const dgfs_plan_s *plan);
 dgfs_status tc_set_variant(dgfs_plan_s *plan, int variant);
+dgfs_status tc_batch_build(int count, dgfs_plan_s *const *plans, const int *P, void *const *f, void *const *Q,
+                           void **out);
+dgfs_status tc_batch_launch(void *batch, cudaStream_t st);
+void tc_batch_free(void *batch);
 dgfs_status tc_selftest_wait(dgfs_plan_s *plan, int expire, cudaStream_t st);
 void tc_info(const dgfs_plan_s *plan, double *info);
 dgfs_status tc_autotune(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st, double *best_ms);

@@ -296,12 +296,6 @@ dgfs_status launch_herm(dgfs_plan_s *plan, const PassArgs &a, int N, int E, cuda
     return DGFS_OK;
 }
 
-#define DGFS_TRY(x)                              \
-    do {                                         \
-        dgfs_status s_ = (x);                    \
-        if (s_ != DGFS_OK) return s_;            \
-    } while (0)
-
 // ws: scratch of at least fp64_scratch_bytes(plan, Fcap, E) bytes, laid out as
 // F [Fcap][S][n] | GA [E][RS][n] | GB [E][RS][n] | QG [E][n] | G2 [E][n]; Fcap >= P.
 template <int N>

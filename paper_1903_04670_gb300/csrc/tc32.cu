@@ -272,7 +272,7 @@ template <int N, int FMT> struct Smem {
 // (real input), an in-plane transpose through shared memory, y-pass, result A'
 // or B' to global.
 template <int N, int FMT>
-__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs a)
+__device__ __forceinline__ void k_stage_a_body(const TcArgs &a, const uint3 bid, const uint3 gdim)
 {
     using SM = Smem<N, FMT>;
     constexpr int NP = NPipes<N, FMT>::A, NT = SM::NT, AB = SM::AB, IR = SM::IR, IC = SM::IC;
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs 
     uint8_t *A0 = sm + (RESIDENT ? NT * (IR + IC) : NT * IC) + pp * NT * AB;
     __shared__ uint64_t mb[NP + 1];  // [0, NP): MMA per pipeline, NP: copies
     __shared__ uint32_t tslot;
-    const int rs = blockIdx.y, side = blockIdx.z;
+    const int rs = bid.y, side = bid.z;
     const long n = a.n;
     const int items = a.Ec * NG;
     const bool ident_y = a.idmask && (a.idmask[rs] & 2);
@@ -319,8 +319,8 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs 
             pf[j] = (4 * i < nval * NN) ? fs[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     };
-    const int stride = gridDim.x * NP;
-    int it = blockIdx.x * NP + pp;
+    const int stride = gdim.x * NP;
+    int it = bid.x * NP + pp;
     if (it < items) prefetch(it);
     bool ok = true;
     if (RESIDENT) {
@@ -389,6 +389,12 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs 
         });
     }
     cta_teardown(tslot, NCOL, ok, a.err);
+}
+
+template <int N, int FMT>
+__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs a)
+{
+    k_stage_a_body<N, FMT>(a, blockIdx, dim3(gridDim.x, gridDim.y, gridDim.z));
 }
 
 // ------------------------------------------- stage A, two threads per row
@@ -764,7 +770,7 @@ __global__ void __launch_bounds__(4 * kRows, 1) k_stage_a_ws(TcArgs a)
 // contraction); each of its NP pipelines loops over items (point e, tile of
 // 128 (y, z) pencils): H = F_x ((T^p_x A') . (T^q_x B')).
 template <int N, int FMT>
-__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b(TcArgs a)
+__device__ __forceinline__ void k_stage_b_body(const TcArgs &a, const uint3 bid, const uint3 gdim)
 {
     using SM = Smem<N, FMT>;
     constexpr int NP = NPipes<N, FMT>::B, NT = SM::NT, AB = SM::AB, IC = SM::IC;
@@ -778,7 +784,7 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b(TcArgs 
     uint8_t *A0 = B0 + (RESIDENT ? 3 : 1) * NT * IC + pp * NT * AB;
     __shared__ uint64_t mb[NP + 1];
     __shared__ uint32_t tslot;
-    const int rs = blockIdx.y;
+    const int rs = bid.y;
     const long n = a.n;
     const int items = a.Ec * NT_TILES;
     const bool ident_x = a.idmask && (a.idmask[rs] & 1);
@@ -801,8 +807,8 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b(TcArgs 
     auto load_pencil = [&](float4 *raw, const float2 *src, bool valid) {
         load_pair_raw<N>(raw, src - (t & 1), NN, valid);
     };
-    const int stride = gridDim.x * NP;
-    int it = blockIdx.x * NP + pp;
+    const int stride = gdim.x * NP;
+    int it = bid.x * NP + pp;
     if (it < items) {
         const int e = it / NT_TILES, p0 = (it % NT_TILES) * kRows;
         load_pencil(pa_raw, a.Ap + ((long)e * a.RS + rs) * n + p0 + t, p0 + t < NN);
@@ -903,13 +909,19 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b(TcArgs 
     cta_teardown(tslot, NCOL, ok, a.err);
 }
 
+template <int N, int FMT>
+__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b(TcArgs a)
+{
+    k_stage_b_body<N, FMT>(a, blockIdx, dim3(gridDim.x, gridDim.y, gridDim.z));
+}
+
 // ------------------------------------------------------------------ stage C
 // grid (plane groups, ceil(RSB / NP), Ec).  Each pipeline owns one block of
 // (r, s) and, for every (r, s) of it, computes t3 = F_y F_z H on the tensor
 // cores and QG_part += w_rs b_rs . t3 in registers; the next (r, s)'s H tile
 // is prefetched into registers meanwhile.
 template <int N, int FMT>
-__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::C, 1) k_stage_c(TcArgs a)
+__device__ __forceinline__ void k_stage_c_body(const TcArgs &a, const uint3 bid, const uint3 gdim)
 {
     using SM = Smem<N, FMT>;
     constexpr int NP = NPipes<N, FMT>::C, NT = SM::NT, AB = SM::AB, IC = SM::IC;
@@ -924,7 +936,7 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::C, 1) k_stage_c(TcArgs 
     uint8_t *A0 = Bf + NT * IC + pp * NT * AB;
     __shared__ uint64_t mb[NP + 1];
     __shared__ uint32_t tslot;
-    const int x0 = blockIdx.x * G, rb = blockIdx.y * NP + pp, e = blockIdx.z;
+    const int x0 = bid.x * G, rb = bid.y * NP + pp, e = bid.z;
     const int nval = min(G, N - x0);
     const long n = a.n;
     cta_setup(&tslot, NCOL, mb, NP + 1);
@@ -1061,7 +1073,66 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::C, 1) k_stage_c(TcArgs 
     cta_teardown(tslot, NCOL, ok, a.err);
 }
 
+template <int N, int FMT>
+__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::C, 1) k_stage_c(TcArgs a)
+{
+    k_stage_c_body<N, FMT>(a, blockIdx, dim3(gridDim.x, gridDim.y, gridDim.z));
+}
+
 // ------------------------------------------------- partial sums of the gain
+// ------------------------------------------------------- batched work list
+// One launch of a stage kernel over the jobs (instance, pair, chunk of points)
+// of several plans with the same N and operand format: CTA b belongs to the
+// job whose first CTA is the largest start <= b, and runs that job's kernel
+// body with its own block index and grid.
+struct JobGrid {
+    uint32_t start, gx, gy, gz;
+};
+
+__device__ __forceinline__ int find_job(const JobGrid *g, int njobs, uint32_t b)
+{
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (g[mid].start <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint3 job_block(const JobGrid &g, uint32_t b)
+{
+    const uint32_t l = b - g.start;
+    return make_uint3(l % g.gx, (l / g.gx) % g.gy, l / (g.gx * g.gy));
+}
+
+template <int N, int FMT>
+__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1)
+    k_stage_a_batch(const TcArgs *jobs, const JobGrid *grids, int njobs)
+{
+    const int j = find_job(grids, njobs, blockIdx.x);
+    const JobGrid g = grids[j];
+    k_stage_a_body<N, FMT>(jobs[j], job_block(g, blockIdx.x), make_uint3(g.gx, g.gy, g.gz));
+}
+
+template <int N, int FMT>
+__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1)
+    k_stage_b_batch(const TcArgs *jobs, const JobGrid *grids, int njobs)
+{
+    const int j = find_job(grids, njobs, blockIdx.x);
+    const JobGrid g = grids[j];
+    k_stage_b_body<N, FMT>(jobs[j], job_block(g, blockIdx.x), make_uint3(g.gx, g.gy, g.gz));
+}
+
+template <int N, int FMT>
+__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::C, 1)
+    k_stage_c_batch(const TcArgs *jobs, const JobGrid *grids, int njobs)
+{
+    const int j = find_job(grids, njobs, blockIdx.x);
+    const JobGrid g = grids[j];
+    k_stage_c_body<N, FMT>(jobs[j], job_block(g, blockIdx.x), make_uint3(g.gx, g.gy, g.gz));
+}
+
 // QG64[pt0 + e][k] = sum_rb QGp[e][rb][k]  (FP32 partials summed in FP64)
 __global__ void k_sum_partials(double2 *QG64, const float2 *QGp, int rsb, long n, int pt0, int E)
 {
@@ -1141,94 +1212,129 @@ __global__ void k_to_f32(float2 *dst, const double2 *src, long count)
 
 unsigned nblk(long total, int t) { return (unsigned)((total + t - 1) / t); }
 
-#define DGFS_TRY(x)                   \
-    do {                              \
-        dgfs_status s_ = (x);         \
-        if (s_ != DGFS_OK) return s_; \
-    } while (0)
+// Workspace of a tensor-core plan:
+//   F64 [maxP][S][n] d2 | QG64, G2 [maxP][n] d2 | Ap, Bq, H [Emax][RS][n] f2 | QGp [Emax][RSBmax][n] f2
+struct TcWs {
+    double2 *F64, *QG64, *G2;
+    float2 *Ap, *Bq, *H, *QGp;
+};
 
-template <int N, int FMT>
-dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaStream_t st)
+TcWs ws_of(const dgfs_plan_s *plan)
 {
-    using SM = Smem<N, FMT>;
-    TcState *ts = reinterpret_cast<TcState *>(plan->tc);
-    const int S = plan->S, RS = plan->Nrho * plan->M;
-    const long n = (long)N * N * N;
-    const int E = ts->chunk;
-    // accumulation blocks of (r, s); with the sigma collapse every block holds whole radial nodes
-    const int RSB = plan->collapse ? (plan->Nrho + (plan->Nrho + ts->rsb - 1) / ts->rsb - 1) /
-                                         ((plan->Nrho + ts->rsb - 1) / ts->rsb)
-                                   : ts->rsb;
-    // workspace: F64 [maxP][S][n] d2 | QG64, G2 [maxP][n] d2 | Ap, Bq, H [Emax][RS][n] f2 | QGp [Emax][RSBmax][n] f2
-    double2 *F64 = reinterpret_cast<double2 *>(plan->ws);
-    double2 *QG64 = F64 + (long)plan->max_points * S * n;
-    double2 *G2 = QG64 + (long)plan->max_points * n;
-    float2 *Ap = reinterpret_cast<float2 *>(G2 + (long)plan->max_points * n);
-    float2 *Bq = Ap + (long)ts->chunk_max * RS * n;
-    float2 *H = Bq + (long)ts->chunk_max * RS * n;
-    float2 *QGp = H + (long)ts->chunk_max * RS * n;
+    const TcState *ts = reinterpret_cast<const TcState *>(plan->tc);
+    const long n = (long)plan->N * plan->N * plan->N, RS = (long)plan->Nrho * plan->M;
+    TcWs w;
+    w.F64 = reinterpret_cast<double2 *>(plan->ws);
+    w.QG64 = w.F64 + (long)plan->max_points * plan->S * n;
+    w.G2 = w.QG64 + (long)plan->max_points * n;
+    w.Ap = reinterpret_cast<float2 *>(w.G2 + (long)plan->max_points * n);
+    w.Bq = w.Ap + (long)ts->chunk_max * RS * n;
+    w.H = w.Bq + (long)ts->chunk_max * RS * n;
+    w.QGp = w.H + (long)ts->chunk_max * RS * n;
+    return w;
+}
 
+// accumulation blocks of (r, s); with the sigma collapse every block holds whole radial nodes
+int rs_blocks(const dgfs_plan_s *plan)
+{
+    const TcState *ts = reinterpret_cast<const TcState *>(plan->tc);
+    if (!plan->collapse) return ts->rsb;
+    const int per = (plan->Nrho + ts->rsb - 1) / ts->rsb;
+    return (plan->Nrho + per - 1) / per;
+}
+
+// Arguments of one job: species pair (p, q), points [pt0, pt0 + Ec).
+TcArgs job_args(const dgfs_plan_s *plan, const void *f, int p, int q, int pt0, int Ec)
+{
+    const TcState *ts = reinterpret_cast<const TcState *>(plan->tc);
+    const TcWs w = ws_of(plan);
+    const int RS = plan->Nrho * plan->M, RSB = rs_blocks(plan);
+    const PairTables &pt = plan->pairs[p * plan->S + q];
     TcArgs a{};
-    a.n = n;
-    a.S = S;
+    a.n = (long)plan->N * plan->N * plan->N;
+    a.S = plan->S;
     a.RS = RS;
     a.nterms = ts->nterms;
     a.rsb = RSB;
     a.rs_per_block = plan->collapse ? plan->M * ((plan->Nrho + ts->rsb - 1) / ts->rsb) : (RS + RSB - 1) / RSB;
     a.collapse_M = plan->collapse ? plan->M : 1;
     a.f = reinterpret_cast<const float *>(f);
-    a.Ap = Ap;
-    a.Bq = Bq;
-    a.H = H;
-    a.QGp = QGp;
+    a.Ap = w.Ap;
+    a.Bq = w.Bq;
+    a.H = w.H;
+    a.QGp = w.QGp;
     a.Fimg = ts->Fimg;
     a.err = ts->err;
+    a.p = p;
+    a.q = q;
+    a.timg = reinterpret_cast<const uint8_t *>(pt.tmat);
+    a.b32 = pt.b32;
+    a.w = pt.w;
+    a.idmask = ts->skip_identity ? ts->idmask : nullptr;
+    a.pt0 = pt0;
+    a.Ec = Ec;
+    return a;
+}
+
+// Grids of the three stage kernels for one job.
+template <int N, int FMT>
+void job_grids(const dgfs_plan_s *plan, int Ec, dim3 &gA, dim3 &gB, dim3 &gC)
+{
+    const TcState *ts = reinterpret_cast<const TcState *>(plan->tc);
+    const int RS = plan->Nrho * plan->M, RSB = rs_blocks(plan);
+    constexpr int G = kRows / N;
+    gA = dim3(ts->groups_a, RS, 2);
+    gB = dim3(ts->groups_b, RS);
+    gC = dim3((N + G - 1) / G, (RSB + NPipes<N, FMT>::C - 1) / NPipes<N, FMT>::C, Ec);
+}
+
+template <int N, int FMT>
+dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaStream_t st)
+{
+    using SM = Smem<N, FMT>;
+    TcState *ts = reinterpret_cast<TcState *>(plan->tc);
+    const int S = plan->S;
+    const long n = (long)N * N * N;
+    const int E = ts->chunk, RSB = rs_blocks(plan);
+    const TcWs w = ws_of(plan);
 
     // FP64 forward transforms of f for the loss term (step 1 of Algorithm 2)
-    DGFS_TRY(fp64_forward(plan, P, f, F64, st));
-    constexpr int G = kRows / N;
+    DGFS_TRY(fp64_forward(plan, P, f, w.F64, st));
     for (int p = 0; p < S; ++p)
         for (int q = 0; q < S; ++q) {
-            const PairTables &pt = plan->pairs[p * S + q];
-            a.p = p;
-            a.q = q;
-            a.timg = reinterpret_cast<const uint8_t *>(pt.tmat);
-            a.b32 = pt.b32;
-            a.w = pt.w;
-            a.idmask = ts->skip_identity ? ts->idmask : nullptr;
             for (int pt0 = 0; pt0 < P; pt0 += E) {
                 const int Ec = std::min(E, P - pt0);
-                a.pt0 = pt0;
-                a.Ec = Ec;
+                const TcArgs a = job_args(plan, f, p, q, pt0, Ec);
+                dim3 gA, gB, gC;
+                job_grids<N, FMT>(plan, Ec, gA, gB, gC);
                 {
                     ProfScope ps(plan, "tc_stage_a", st);
                     if (WsA<N, FMT>::OK && ts->ws_a == 1)
-                        k_stage_a_ws<N, FMT><<<dim3(ts->groups_a, RS, 2), 4 * kRows, WsA<N, FMT>::BYTES, st>>>(a);
+                        k_stage_a_ws<N, FMT><<<gA, 4 * kRows, WsA<N, FMT>::BYTES, st>>>(a);
                     else if (A2<N, FMT>::OK && ts->ws_a == 2)
-                        k_stage_a2<N, FMT><<<dim3(ts->groups_a, RS, 2), 2 * kRows * NPipes<N, FMT>::A, SM::A, st>>>(a);
+                        k_stage_a2<N, FMT><<<gA, 2 * kRows * NPipes<N, FMT>::A, SM::A, st>>>(a);
                     else
-                        k_stage_a<N, FMT><<<dim3(ts->groups_a, RS, 2), kRows * NPipes<N, FMT>::A, SM::A, st>>>(a);
+                        k_stage_a<N, FMT><<<gA, kRows * NPipes<N, FMT>::A, SM::A, st>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
                 {
                     ProfScope ps(plan, "tc_stage_b", st);
-                    k_stage_b<N, FMT><<<dim3(ts->groups_b, RS), kRows * NPipes<N, FMT>::B, SM::B, st>>>(a);
+                    k_stage_b<N, FMT><<<gB, kRows * NPipes<N, FMT>::B, SM::B, st>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
                 {
                     ProfScope ps(plan, "tc_stage_c", st);
-                    k_stage_c<N, FMT><<<dim3((N + G - 1) / G, (RSB + NPipes<N, FMT>::C - 1) / NPipes<N, FMT>::C, Ec),
-                                        kRows * NPipes<N, FMT>::C, SM::C, st>>>(a);
+                    k_stage_c<N, FMT><<<gC, kRows * NPipes<N, FMT>::C, SM::C, st>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
                 {
                     ProfScope ps(plan, "tc_sum_partials", st);
-                    k_sum_partials<<<nblk((long)Ec * n, 256), 256, 0, st>>>(QG64, QGp, RSB, n, pt0, Ec);
+                    k_sum_partials<<<nblk((long)Ec * n, 256), 256, 0, st>>>(w.QG64, w.QGp, RSB, n, pt0, Ec);
                 }
                 DGFS_LAUNCHED(plan);
             }
             // step 10 in FP64 for this pair over all points
-            DGFS_TRY(fp64_finish(plan, p, q, P, QG64, G2, F64, f, Qout, st));
+            DGFS_TRY(fp64_finish(plan, p, q, P, w.QG64, w.G2, w.F64, f, Qout, st));
         }
     return DGFS_OK;
 }
@@ -1245,7 +1351,112 @@ dgfs_status set_smem_attrs()
         DGFS_CUDA(cudaFuncSetAttribute(k_stage_a2<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::A));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_b<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_c<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::C));
+    DGFS_CUDA(cudaFuncSetAttribute(k_stage_a_batch<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::A));
+    DGFS_CUDA(cudaFuncSetAttribute(k_stage_b_batch<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B));
+    DGFS_CUDA(cudaFuncSetAttribute(k_stage_c_batch<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::C));
     return DGFS_OK;
+}
+
+// ------------------------------------------------------------ batches
+// A batch holds, per (N, operand format) group of tensor-core plans, rounds of
+// jobs: round k runs the k-th job (species pair, chunk of points) of every
+// plan of the group, each stage as one launch over all of them.  The FP64
+// forward transforms, partial sums and finishing passes stay per plan.
+struct BatchJob {
+    dgfs_plan_s *plan;
+    int p, q, pt0, Ec, P;
+    bool last;  // last chunk of its pair: the finish follows
+    const void *f;
+    void *Q;
+};
+
+struct BatchRound {
+    std::vector<BatchJob> jobs;
+    TcArgs *args = nullptr;               // device [njobs]
+    JobGrid *gA = nullptr, *gB = nullptr, *gC = nullptr;  // device [njobs]
+    uint32_t ctasA = 0, ctasB = 0, ctasC = 0;
+};
+
+struct BatchGroup {
+    int N = 0, fmt = 0;
+    std::vector<BatchRound> rounds;
+};
+
+template <int N, int FMT>
+dgfs_status round_build(BatchRound &r)
+{
+    const int nj = (int)r.jobs.size();
+    std::vector<TcArgs> args(nj);
+    std::vector<JobGrid> ga(nj), gb(nj), gc(nj);
+    for (int j = 0; j < nj; ++j) {
+        const BatchJob &b = r.jobs[j];
+        args[j] = job_args(b.plan, b.f, b.p, b.q, b.pt0, b.Ec);
+        dim3 A, Bd, C;
+        job_grids<N, FMT>(b.plan, b.Ec, A, Bd, C);
+        ga[j] = JobGrid{r.ctasA, A.x, A.y, A.z};
+        gb[j] = JobGrid{r.ctasB, Bd.x, Bd.y, Bd.z};
+        gc[j] = JobGrid{r.ctasC, C.x, C.y, C.z};
+        r.ctasA += A.x * A.y * A.z;
+        r.ctasB += Bd.x * Bd.y * Bd.z;
+        r.ctasC += C.x * C.y * C.z;
+    }
+    DGFS_CUDA(cudaMalloc(&r.args, sizeof(TcArgs) * nj));
+    DGFS_CUDA(cudaMalloc(&r.gA, sizeof(JobGrid) * nj * 3));
+    r.gB = r.gA + nj;
+    r.gC = r.gB + nj;
+    DGFS_CUDA(cudaMemcpy(r.args, args.data(), sizeof(TcArgs) * nj, cudaMemcpyHostToDevice));
+    DGFS_CUDA(cudaMemcpy(r.gA, ga.data(), sizeof(JobGrid) * nj, cudaMemcpyHostToDevice));
+    DGFS_CUDA(cudaMemcpy(r.gB, gb.data(), sizeof(JobGrid) * nj, cudaMemcpyHostToDevice));
+    DGFS_CUDA(cudaMemcpy(r.gC, gc.data(), sizeof(JobGrid) * nj, cudaMemcpyHostToDevice));
+    return DGFS_OK;
+}
+
+template <int N, int FMT>
+dgfs_status round_launch(const BatchRound &r, cudaStream_t st)
+{
+    using SM = Smem<N, FMT>;
+    dgfs_plan_s *lead = r.jobs[0].plan;  // launch counting and profiling
+    const int nj = (int)r.jobs.size();
+    {
+        ProfScope ps(lead, "tc_stage_a", st);
+        k_stage_a_batch<N, FMT><<<r.ctasA, kRows * NPipes<N, FMT>::A, SM::A, st>>>(r.args, r.gA, nj);
+    }
+    DGFS_LAUNCHED(lead);
+    {
+        ProfScope ps(lead, "tc_stage_b", st);
+        k_stage_b_batch<N, FMT><<<r.ctasB, kRows * NPipes<N, FMT>::B, SM::B, st>>>(r.args, r.gB, nj);
+    }
+    DGFS_LAUNCHED(lead);
+    {
+        ProfScope ps(lead, "tc_stage_c", st);
+        k_stage_c_batch<N, FMT><<<r.ctasC, kRows * NPipes<N, FMT>::C, SM::C, st>>>(r.args, r.gC, nj);
+    }
+    DGFS_LAUNCHED(lead);
+    for (const BatchJob &b : r.jobs) {
+        const TcWs w = ws_of(b.plan);
+        const long n = (long)N * N * N;
+        {
+            ProfScope ps(b.plan, "tc_sum_partials", st);
+            k_sum_partials<<<nblk((long)b.Ec * n, 256), 256, 0, st>>>(w.QG64, w.QGp, rs_blocks(b.plan), n, b.pt0,
+                                                                       b.Ec);
+        }
+        DGFS_LAUNCHED(b.plan);
+        if (b.last) DGFS_TRY(fp64_finish(b.plan, b.p, b.q, b.P, w.QG64, w.G2, w.F64, b.f, b.Q, st));
+    }
+    return DGFS_OK;
+}
+
+template <int FMT>
+dgfs_status round_dispatch(int N, BatchRound &r, bool build, cudaStream_t st)
+{
+    switch (N) {
+    case 8: return build ? round_build<8, FMT>(r) : round_launch<8, FMT>(r, st);
+    case 16: return build ? round_build<16, FMT>(r) : round_launch<16, FMT>(r, st);
+    case 24: return build ? round_build<24, FMT>(r) : round_launch<24, FMT>(r, st);
+    case 32: return build ? round_build<32, FMT>(r) : round_launch<32, FMT>(r, st);
+    case 48: return build ? round_build<48, FMT>(r) : round_launch<48, FMT>(r, st);
+    default: set_error("batch: N not supported by the tensor-core path"); return DGFS_EUNSUPPORTED;
+    }
 }
 
 template <int FMT>
@@ -1378,6 +1589,81 @@ size_t tc_workspace_bytes(const dgfs_plan_s *plan)
            sizeof(float2) * (3 * E * RS * n + E * RSB * n);
 }
 
+struct TcBatch {
+    std::vector<BatchGroup> groups;
+    std::vector<std::pair<dgfs_plan_s *, std::pair<int, const void *>>> forwards;  // (plan, (P, f)) per TC plan
+};
+
+void tc_batch_free(void *handle)
+{
+    TcBatch *b = reinterpret_cast<TcBatch *>(handle);
+    if (!b) return;
+    for (auto &g : b->groups)
+        for (auto &r : g.rounds) {
+            cudaFree(r.args);
+            cudaFree(r.gA);
+        }
+    delete b;
+}
+
+// Jobs of `count` tensor-core plans (distinct; each with its own f, Q and P)
+// grouped by (N, operand format) into rounds.
+dgfs_status tc_batch_build(int count, dgfs_plan_s *const *plans, const int *P, void *const *f, void *const *Q,
+                           void **out)
+{
+    TcBatch *b = new (std::nothrow) TcBatch;
+    if (!b) return DGFS_ENOMEM;
+    for (int i = 0; i < count; ++i) {
+        dgfs_plan_s *plan = plans[i];
+        const TcState *ts = reinterpret_cast<const TcState *>(plan->tc);
+        if (reinterpret_cast<uintptr_t>(f[i]) & 15) {
+            set_error("dgfs_batch_create: f must be 16-byte aligned for tensor-core plans");
+            tc_batch_free(b);
+            return DGFS_EINVAL;
+        }
+        b->forwards.push_back({plan, {P[i], f[i]}});
+        BatchGroup *g = nullptr;
+        for (auto &x : b->groups)
+            if (x.N == plan->N && x.fmt == ts->fmt) g = &x;
+        if (!g) {
+            b->groups.push_back(BatchGroup{});
+            g = &b->groups.back();
+            g->N = plan->N;
+            g->fmt = ts->fmt;
+        }
+        int k = 0;
+        for (int p = 0; p < plan->S; ++p)
+            for (int q = 0; q < plan->S; ++q)
+                for (int pt0 = 0; pt0 < P[i]; pt0 += ts->chunk, ++k) {
+                    if ((int)g->rounds.size() <= k) g->rounds.emplace_back();
+                    const int Ec = std::min(ts->chunk, P[i] - pt0);
+                    g->rounds[k].jobs.push_back(BatchJob{plan, p, q, pt0, Ec, P[i], pt0 + Ec >= P[i], f[i], Q[i]});
+                }
+    }
+    for (auto &g : b->groups)
+        for (auto &r : g.rounds) {
+            const dgfs_status st = g.fmt == 0 ? round_dispatch<0>(g.N, r, true, nullptr)
+                                              : round_dispatch<1>(g.N, r, true, nullptr);
+            if (st != DGFS_OK) {
+                tc_batch_free(b);
+                return st;
+            }
+        }
+    *out = b;
+    return DGFS_OK;
+}
+
+dgfs_status tc_batch_launch(void *handle, cudaStream_t st)
+{
+    TcBatch *b = reinterpret_cast<TcBatch *>(handle);
+    for (auto &fw : b->forwards)
+        DGFS_TRY(fp64_forward(fw.first, fw.second.first, fw.second.second, ws_of(fw.first).F64, st));
+    for (auto &g : b->groups)
+        for (auto &r : g.rounds)
+            DGFS_TRY(g.fmt == 0 ? round_dispatch<0>(g.N, r, false, st) : round_dispatch<1>(g.N, r, false, st));
+    return DGFS_OK;
+}
+
 dgfs_status tc_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st)
 {
     const TcState *ts = reinterpret_cast<const TcState *>(plan->tc);
@@ -1458,6 +1744,7 @@ dgfs_status tc_autotune(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaSt
     }
     *ts = bestcfg;
     ts->tuned = 1;
+    plan->config_gen++;
     if (best_ms) *best_ms = best;
     return tc_check(plan);
 }
@@ -1506,6 +1793,7 @@ dgfs_status tc_set_variant(dgfs_plan_s *plan, int variant)
         return variant < 0 || variant > 2 ? DGFS_EINVAL : DGFS_EUNSUPPORTED;
     }
     ts->ws_a = variant;
+    plan->config_gen++;
     return DGFS_OK;
 }
 

@@ -1,6 +1,8 @@
 """Batching and scheduling: one CUDA graph over uneven instances (different N,
-S, M, N_rho, precision and point counts) equals separate calls bit for bit;
-the homogeneous relaxation step; the autotuner keeps results within bounds."""
+S, M, N_rho, precision and point counts) equals separate calls bit for bit, and
+so does the batched work list (one launch per stage over the jobs of every
+instance with the same N and operand format); the homogeneous relaxation step;
+the autotuner keeps results within bounds."""
 import numpy as np
 import pytest
 import torch
@@ -12,10 +14,11 @@ from paper_1903_04670_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _instance(N, S, M, Nrho, P, prec, seed):
+def _instance(N, S, M, Nrho, P, prec, seed, vhs=False):
     rng = np.random.default_rng(seed)
     masses = [1.0, 2.0, 4.0][:S]
-    pairs = W.pair_params([0.81, 0.75, 0.7][:S], [1.0, 1.4, 1.2][:S], [1.0, 1.2, 0.9][:S])
+    alpha = [1.0, 1.0, 1.0] if vhs else [1.0, 1.4, 1.2]
+    pairs = W.pair_params([0.81, 0.75, 0.7][:S], alpha[:S], [1.0, 1.2, 0.9][:S])
     L = N / 3.2
     f = np.stack([np.stack([W.two_maxwellians(rng, N, L, m) for m in masses]) for _ in range(P)])
     plan = B.Plan(N, L, M, Nrho, masses, pairs, prec, P)
@@ -51,6 +54,80 @@ def test_graph_of_uneven_batch_equals_separate_calls(batch):
     for inst, Q, ref in zip(batch, Qs, refs):
         inst["plan"].check()
         assert torch.equal(Q, ref)
+
+
+@pytest.fixture(scope="module")
+def worklist():
+    # two groups of N = 16 FP32 tensor-core plans with different job counts
+    # (S^2 pairs), an N = 8 plan whose 30 points take two chunks (24 + 6), a
+    # VHS plan on the sigma-collapsed path, a BF16 group and an FP64 plan
+    return [
+        _instance(16, 2, 6, 8, 3, "fp32_tc", 11),
+        _instance(16, 3, 12, 4, 2, "fp32_tc", 12),
+        _instance(16, 2, 12, 3, 2, "fp32_tc", 13, vhs=True),
+        _instance(8, 2, 6, 4, 30, "fp32_tc", 14),
+        _instance(16, 1, 6, 4, 2, "bf16x3", 15),
+        _instance(8, 1, 12, 4, 2, "fp64", 16),
+    ]
+
+
+def test_batched_worklist_equals_separate_calls(worklist):
+    assert worklist[2]["plan"].info()["collapse"] == 1
+    refs = [inst["plan"].collide(inst["f"]).clone() for inst in worklist]
+    torch.cuda.synchronize()
+    Qs = [torch.full_like(r, float("nan")) for r in refs]
+    b = B.dgfs_batch_create([i["plan"]._h for i in worklist], [i["P"] for i in worklist],
+                            [i["f"] for i in worklist], Qs)
+    try:
+        for _ in range(2):
+            B.dgfs_batch_launch(b)
+        torch.cuda.synchronize()
+    finally:
+        B.dgfs_batch_destroy(b)
+    for inst, Q, ref in zip(worklist, Qs, refs):
+        inst["plan"].check()
+        assert torch.equal(Q, ref)
+
+
+def test_batched_worklist_with_relaxation_matches_graph(worklist):
+    sub = [worklist[0], worklist[3]]
+    dt = 0.01
+    f_b = [i["f"].clone() for i in sub]
+    f_g = [i["f"].clone() for i in sub]
+    Q_b = [torch.empty(i["P"], i["f"].shape[1], *i["f"].shape[1:], dtype=i["f"].dtype, device="cuda")
+           for i in sub]
+    Q_g = [torch.empty_like(q) for q in Q_b]
+    b = B.dgfs_batch_create([i["plan"]._h for i in sub], [i["P"] for i in sub], f_b, Q_b, dt=dt)
+    try:
+        B.dgfs_batch_launch(b)
+        B.dgfs_batch_launch(b)
+        torch.cuda.synchronize()
+    finally:
+        B.dgfs_batch_destroy(b)
+    g = B.dgfs_graph_capture([i["plan"]._h for i in sub], [i["P"] for i in sub], f_g, Q_g, dt=dt, steps=2)
+    try:
+        B.dgfs_graph_launch(g)
+        torch.cuda.synchronize()
+    finally:
+        B.dgfs_graph_destroy(g)
+    for a, c in zip(f_b, f_g):
+        assert torch.equal(a, c)
+
+
+def test_batch_rejects_repeated_plan_and_stale_configuration(worklist):
+    inst = worklist[0]
+    Q = torch.empty(inst["P"], 2, 2, 16, 16, 16, device="cuda")
+    with pytest.raises(B.DgfsError) as e:
+        B.dgfs_batch_create([inst["plan"]._h] * 2, [inst["P"]] * 2, [inst["f"]] * 2, [Q] * 2)
+    assert e.value.status == 1
+    b = B.dgfs_batch_create([inst["plan"]._h], [inst["P"]], [inst["f"]], [Q])
+    try:
+        inst["plan"].set_kernel_variant(0)
+        with pytest.raises(B.DgfsError) as e:
+            B.dgfs_batch_launch(b)
+        assert e.value.status == 1
+    finally:
+        B.dgfs_batch_destroy(b)
 
 
 def test_batch_instances_match_oracle(batch):
