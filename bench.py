@@ -307,6 +307,13 @@ def run_ours(args, rank, world):
         out["e2e"] = {"value": world * evals * rec["steps"] / tot, "unit": UNIT,
                       "h2d_bytes_per_step": int(fh.numel() * es), "d2h_bytes_per_step": int(Qh.numel() * es)}
 
+    # 256 uneven homogeneous relaxation problems (N in {24, 32, 48}, 2 or 3
+    # species, M in {6, 12}, N_rho in {8, 16}): one collision call plus one
+    # relaxation step of every problem per pass, run as separate calls, as a
+    # graph of those calls, and as the batched work list (eager and captured)
+    if not args.no_batch and main != "fp64" and world == 1:
+        out["uneven_batch"] = uneven_batch(B, W, torch, np, main, dev, flush, stream, plan, rec)
+
     # per-form throughput and error vs the oracle on a sampled subset of points
     sample_pts = [i for i in (0, 7, 15, 23) if i < P] if not args.quick else [0]
     Qo = None
@@ -334,6 +341,94 @@ def run_ours(args, rank, world):
             d["err_sample_points"] = sample_pts
         out["forms"][prec] = d
     return out
+
+
+def uneven_batch(B, W, torch, np, prec, dev, flush, stream, plan, rec):
+    """Timings of the batched work list on the uneven relaxation workload, and
+    the work list's own device cost on the benchmark call (one instance)."""
+    import collections
+
+    inst = W.relaxation_batch()
+    groups = collections.OrderedDict()
+    for x in inst:  # problems with equal parameters share a plan as its points
+        groups.setdefault((x["N"], tuple(x["masses"]), x["M"], x["Nrho"], x["alpha"]), []).append(x)
+    plans, fs, Qs = [], [], []
+    for xs in groups.values():
+        x = xs[0]
+        pl = B.Plan(x["N"], x["L"], x["M"], x["Nrho"], x["masses"], x["pairs"], prec, len(xs), dev)
+        fs.append(torch.from_numpy(np.concatenate([y["f"] for y in xs])).to("cuda", pl.dtype).contiguous())
+        Qs.append(torch.empty(len(xs), pl.S, pl.S, pl.N, pl.N, pl.N, dtype=pl.dtype, device="cuda"))
+        plans.append(pl)
+    evals = sum(f.shape[0] * pl.S * pl.S for pl, f in zip(plans, fs))
+    dt = 1e-3
+
+    def timed(fn, reps=5):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / reps
+
+    def separate():
+        for pl, f, Q in zip(plans, fs, Qs):
+            pl.collide(f, Q)
+            pl.relax_step(f, Q, dt)
+
+    def launches(fn):
+        n0 = sum(pl.launch_count() for pl in plans)
+        fn()
+        torch.cuda.synchronize()
+        return sum(pl.launch_count() for pl in plans) - n0
+
+    res = {"workload": "relaxation_batch: 256 homogeneous problems, N in {24, 32, 48}, 2 or 3 species "
+                       "(masses from {1, 2, 4}), M in {6, 12}, N_rho in {8, 16}, VHS or VSS, seeded "
+                       "two-Maxwellian data; one collision call + one relaxation step per problem per pass",
+           "instances": len(inst), "plans": len(plans), "evals_per_pass": evals, "precision": prec}
+    t = timed(separate)
+    res["separate_calls"] = {"ms_per_pass": t, "evals_per_s": evals / (t / 1e3), "launches": launches(separate)}
+    g = B.dgfs_graph_capture([pl._h for pl in plans], [f.shape[0] for f in fs], fs, Qs, dt=dt)
+    try:
+        t = timed(lambda: B.dgfs_graph_launch(g, stream))
+        res["graph_of_calls"] = {"ms_per_pass": t, "evals_per_s": evals / (t / 1e3),
+                                 "launches": B.dgfs_graph_kernel_count(g)}
+    finally:
+        B.dgfs_graph_destroy(g)
+    bt = B.Batch(plans, fs, Qs, dt)
+    try:
+        t = timed(lambda: bt.launch(stream))
+        res["batch"] = {"ms_per_pass": t, "evals_per_s": evals / (t / 1e3),
+                        "launches": launches(lambda: bt.launch(stream))}
+        cg = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream()
+        cs.wait_stream(stream)
+        with torch.cuda.graph(cg, stream=cs):
+            bt.launch(cs)
+        t = timed(cg.replay)
+        res["batch_graph"] = {"ms_per_pass": t, "evals_per_s": evals / (t / 1e3)}
+        del cg
+    finally:
+        bt.close()
+    for pl in plans:
+        pl.check()
+    del plans, fs, Qs
+    # device cost of the work list itself: the benchmark call as a batch of one
+    # instance against its plain launches (same kernels, default stage A variant)
+    plan.set_kernel_variant(0)
+    f, Q = rec["f"], rec["Q"]
+    t_plain = timed(lambda: plan.collide(f, Q), reps=10)
+    b1 = B.Batch([plan], [f], [Q])
+    try:
+        t_b1 = timed(lambda: b1.launch(stream), reps=10)
+    finally:
+        b1.close()
+    res["one_instance"] = {"plain_ms": t_plain, "batch_ms": t_b1, "overhead": t_b1 / t_plain - 1.0}
+    return res
 
 
 def tc_executed_flops(name, info, P, S, RS, sigma=None):
@@ -431,6 +526,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-dg", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true")

@@ -422,6 +422,32 @@ class Plan:
 
 
 # ------------------------------------------------------------ 1-D DG transport
+class Batch:
+    """A batched work list over distinct plans (dgfs_batch_create): `plans`
+    are Plan objects, fs and Qs device tensors whose addresses stay fixed."""
+
+    def __init__(self, plans, fs, Qs, dt=0.0):
+        self.plans, self.fs, self.Qs = list(plans), list(fs), list(Qs)
+        for pl, f in zip(self.plans, self.fs):
+            pl._check_f(f)
+        self._h = dgfs_batch_create([pl._h for pl in self.plans], [f.shape[0] for f in self.fs], self.fs,
+                                    self.Qs, dt)
+
+    def launch(self, stream=None):
+        dgfs_batch_launch(self._h, stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            dgfs_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def dgfs_dg_create(plan_h, Ne, K, x0, x1, walls):
     """walls: ((T_left, (ux, uy, uz)), (T_right, (ux, uy, uz)))."""
     import numpy as np

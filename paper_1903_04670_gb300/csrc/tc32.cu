@@ -33,6 +33,7 @@
 // flag, frees its TMEM and returns (reported as DGFS_ETIMEOUT by dgfs_plan_check).
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <vector>
 
 #include "dgfs_internal.h"
@@ -1089,12 +1090,22 @@ struct JobGrid {
     uint32_t start, gx, gy, gz;
 };
 
-__device__ __forceinline__ int find_job(const JobGrid *g, int njobs, uint32_t b)
+// Jobs of one batched launch, passed by value: the arguments then sit in the
+// constant bank like a plain launch's, instead of global memory that every
+// store of the kernel may alias.
+constexpr int kJobsPerLaunch = 48;
+struct JobTable {
+    TcArgs job[kJobsPerLaunch];
+    JobGrid grid[kJobsPerLaunch];
+    int njobs;
+};
+
+__device__ __forceinline__ int find_job(const JobTable &t, uint32_t b)
 {
-    int lo = 0, hi = njobs - 1;
+    int lo = 0, hi = t.njobs - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) / 2;
-        if (g[mid].start <= b) lo = mid;
+        if (t.grid[mid].start <= b) lo = mid;
         else hi = mid - 1;
     }
     return lo;
@@ -1107,30 +1118,27 @@ __device__ __forceinline__ uint3 job_block(const JobGrid &g, uint32_t b)
 }
 
 template <int N, int FMT>
-__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1)
-    k_stage_a_batch(const TcArgs *jobs, const JobGrid *grids, int njobs)
+__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a_batch(const __grid_constant__ JobTable t)
 {
-    const int j = find_job(grids, njobs, blockIdx.x);
-    const JobGrid g = grids[j];
-    k_stage_a_body<N, FMT>(jobs[j], job_block(g, blockIdx.x), make_uint3(g.gx, g.gy, g.gz));
+    const int j = find_job(t, blockIdx.x);
+    const JobGrid &g = t.grid[j];
+    k_stage_a_body<N, FMT>(t.job[j], job_block(g, blockIdx.x), make_uint3(g.gx, g.gy, g.gz));
 }
 
 template <int N, int FMT>
-__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1)
-    k_stage_b_batch(const TcArgs *jobs, const JobGrid *grids, int njobs)
+__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b_batch(const __grid_constant__ JobTable t)
 {
-    const int j = find_job(grids, njobs, blockIdx.x);
-    const JobGrid g = grids[j];
-    k_stage_b_body<N, FMT>(jobs[j], job_block(g, blockIdx.x), make_uint3(g.gx, g.gy, g.gz));
+    const int j = find_job(t, blockIdx.x);
+    const JobGrid &g = t.grid[j];
+    k_stage_b_body<N, FMT>(t.job[j], job_block(g, blockIdx.x), make_uint3(g.gx, g.gy, g.gz));
 }
 
 template <int N, int FMT>
-__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::C, 1)
-    k_stage_c_batch(const TcArgs *jobs, const JobGrid *grids, int njobs)
+__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::C, 1) k_stage_c_batch(const __grid_constant__ JobTable t)
 {
-    const int j = find_job(grids, njobs, blockIdx.x);
-    const JobGrid g = grids[j];
-    k_stage_c_body<N, FMT>(jobs[j], job_block(g, blockIdx.x), make_uint3(g.gx, g.gy, g.gz));
+    const int j = find_job(t, blockIdx.x);
+    const JobGrid &g = t.grid[j];
+    k_stage_c_body<N, FMT>(t.job[j], job_block(g, blockIdx.x), make_uint3(g.gx, g.gy, g.gz));
 }
 
 // QG64[pt0 + e][k] = sum_rb QGp[e][rb][k]  (FP32 partials summed in FP64)
@@ -1372,9 +1380,9 @@ struct BatchJob {
 
 struct BatchRound {
     std::vector<BatchJob> jobs;
-    TcArgs *args = nullptr;               // device [njobs]
-    JobGrid *gA = nullptr, *gB = nullptr, *gC = nullptr;  // device [njobs]
-    uint32_t ctasA = 0, ctasB = 0, ctasC = 0;
+    // per launch of at most kJobsPerLaunch jobs: the tables of stages A, B, C
+    std::vector<JobTable> tabs;
+    std::vector<uint32_t> ctas;
 };
 
 struct BatchGroup {
@@ -1386,28 +1394,30 @@ template <int N, int FMT>
 dgfs_status round_build(BatchRound &r)
 {
     const int nj = (int)r.jobs.size();
-    std::vector<TcArgs> args(nj);
-    std::vector<JobGrid> ga(nj), gb(nj), gc(nj);
-    for (int j = 0; j < nj; ++j) {
-        const BatchJob &b = r.jobs[j];
-        args[j] = job_args(b.plan, b.f, b.p, b.q, b.pt0, b.Ec);
-        dim3 A, Bd, C;
-        job_grids<N, FMT>(b.plan, b.Ec, A, Bd, C);
-        ga[j] = JobGrid{r.ctasA, A.x, A.y, A.z};
-        gb[j] = JobGrid{r.ctasB, Bd.x, Bd.y, Bd.z};
-        gc[j] = JobGrid{r.ctasC, C.x, C.y, C.z};
-        r.ctasA += A.x * A.y * A.z;
-        r.ctasB += Bd.x * Bd.y * Bd.z;
-        r.ctasC += C.x * C.y * C.z;
+    for (int j0 = 0; j0 < nj; j0 += kJobsPerLaunch) {
+        const int cnt = std::min(kJobsPerLaunch, nj - j0);
+        JobTable t[3];
+        uint32_t c[3] = {0, 0, 0};
+        for (int k = 0; k < 3; ++k) {
+            memset(&t[k], 0, sizeof(JobTable));
+            t[k].njobs = cnt;
+        }
+        for (int j = 0; j < cnt; ++j) {
+            const BatchJob &b = r.jobs[j0 + j];
+            const TcArgs a = job_args(b.plan, b.f, b.p, b.q, b.pt0, b.Ec);
+            dim3 g[3];
+            job_grids<N, FMT>(b.plan, b.Ec, g[0], g[1], g[2]);
+            for (int k = 0; k < 3; ++k) {
+                t[k].job[j] = a;
+                t[k].grid[j] = JobGrid{c[k], g[k].x, g[k].y, g[k].z};
+                c[k] += g[k].x * g[k].y * g[k].z;
+            }
+        }
+        for (int k = 0; k < 3; ++k) {
+            r.tabs.push_back(t[k]);
+            r.ctas.push_back(c[k]);
+        }
     }
-    DGFS_CUDA(cudaMalloc(&r.args, sizeof(TcArgs) * nj));
-    DGFS_CUDA(cudaMalloc(&r.gA, sizeof(JobGrid) * nj * 3));
-    r.gB = r.gA + nj;
-    r.gC = r.gB + nj;
-    DGFS_CUDA(cudaMemcpy(r.args, args.data(), sizeof(TcArgs) * nj, cudaMemcpyHostToDevice));
-    DGFS_CUDA(cudaMemcpy(r.gA, ga.data(), sizeof(JobGrid) * nj, cudaMemcpyHostToDevice));
-    DGFS_CUDA(cudaMemcpy(r.gB, gb.data(), sizeof(JobGrid) * nj, cudaMemcpyHostToDevice));
-    DGFS_CUDA(cudaMemcpy(r.gC, gc.data(), sizeof(JobGrid) * nj, cudaMemcpyHostToDevice));
     return DGFS_OK;
 }
 
@@ -1416,22 +1426,23 @@ dgfs_status round_launch(const BatchRound &r, cudaStream_t st)
 {
     using SM = Smem<N, FMT>;
     dgfs_plan_s *lead = r.jobs[0].plan;  // launch counting and profiling
-    const int nj = (int)r.jobs.size();
-    {
-        ProfScope ps(lead, "tc_stage_a", st);
-        k_stage_a_batch<N, FMT><<<r.ctasA, kRows * NPipes<N, FMT>::A, SM::A, st>>>(r.args, r.gA, nj);
+    for (size_t l = 0; l < r.tabs.size(); l += 3) {
+        {
+            ProfScope ps(lead, "tc_stage_a", st);
+            k_stage_a_batch<N, FMT><<<r.ctas[l], kRows * NPipes<N, FMT>::A, SM::A, st>>>(r.tabs[l]);
+        }
+        DGFS_LAUNCHED(lead);
+        {
+            ProfScope ps(lead, "tc_stage_b", st);
+            k_stage_b_batch<N, FMT><<<r.ctas[l + 1], kRows * NPipes<N, FMT>::B, SM::B, st>>>(r.tabs[l + 1]);
+        }
+        DGFS_LAUNCHED(lead);
+        {
+            ProfScope ps(lead, "tc_stage_c", st);
+            k_stage_c_batch<N, FMT><<<r.ctas[l + 2], kRows * NPipes<N, FMT>::C, SM::C, st>>>(r.tabs[l + 2]);
+        }
+        DGFS_LAUNCHED(lead);
     }
-    DGFS_LAUNCHED(lead);
-    {
-        ProfScope ps(lead, "tc_stage_b", st);
-        k_stage_b_batch<N, FMT><<<r.ctasB, kRows * NPipes<N, FMT>::B, SM::B, st>>>(r.args, r.gB, nj);
-    }
-    DGFS_LAUNCHED(lead);
-    {
-        ProfScope ps(lead, "tc_stage_c", st);
-        k_stage_c_batch<N, FMT><<<r.ctasC, kRows * NPipes<N, FMT>::C, SM::C, st>>>(r.args, r.gC, nj);
-    }
-    DGFS_LAUNCHED(lead);
     for (const BatchJob &b : r.jobs) {
         const TcWs w = ws_of(b.plan);
         const long n = (long)N * N * N;
@@ -1598,11 +1609,6 @@ void tc_batch_free(void *handle)
 {
     TcBatch *b = reinterpret_cast<TcBatch *>(handle);
     if (!b) return;
-    for (auto &g : b->groups)
-        for (auto &r : g.rounds) {
-            cudaFree(r.args);
-            cudaFree(r.gA);
-        }
     delete b;
 }
 

@@ -26,7 +26,7 @@ import numpy as np
 
 __all__ = [
     "CONFIGS", "velocity_grid", "maxwellian", "two_maxwellians", "perturbed_maxwellian",
-    "pair_params", "make_problem", "krook_wu_problem",
+    "pair_params", "make_problem", "krook_wu_problem", "relaxation_batch",
 ]
 
 
@@ -170,3 +170,25 @@ def krook_wu_problem(N, M, Nrho, m1=1.0, m2=1.0, L=12.0):
     bo = [lam[q][p] / (4.0 * math.pi * nn[q]) for p in range(2) for q in range(2)]
     pairs = pair_params([1.0, 1.0], [1.0, 1.0], [1.0, 1.0], beta_override=bo)
     return dict(N=N, L=L, M=M, Nrho=Nrho, masses=[m1, m2], pairs=pairs)
+
+
+def relaxation_batch(count=256, seed=6, L=8.0):
+    """`count` spatially homogeneous relaxation problems with uneven
+    parameters: N from {24, 32, 48}, 2 or 3 species with distinct masses from
+    {1, 2, 4}, M from {6, 12}, N_rho from {8, 16}, VHS (alpha = 1) or VSS
+    (alpha = 1.4) with omega = 0.81, and two-Maxwellian data per species.
+    Returns a list of dicts with the operator parameters and f of shape
+    [1][S][N][N][N]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        N = int(rng.choice([24, 32, 48]))
+        S = int(rng.choice([2, 3]))
+        masses = sorted(float(m) for m in rng.choice([1.0, 2.0, 4.0], size=S, replace=False))
+        M = int(rng.choice([6, 12]))
+        Nrho = int(rng.choice([8, 16]))
+        alpha = 1.0 if rng.uniform() < 0.5 else 1.4
+        pairs = pair_params([0.81] * S, [alpha] * S, [1.0 + 0.1 * j for j in range(S)])
+        f = np.stack([two_maxwellians(rng, N, L, m) for m in masses])[None]
+        out.append(dict(N=N, L=L, M=M, Nrho=Nrho, masses=masses, pairs=pairs, alpha=alpha, f=f))
+    return out
