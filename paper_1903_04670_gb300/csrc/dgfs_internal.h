@@ -123,8 +123,8 @@ dgfs_status fp64_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaS
 dgfs_status fp64_backward(dgfs_plan_s *plan, int P, const void *f, const void *dQ, void *df,
                           double *domega, int domega_on_host, cudaStream_t st);
 dgfs_status fp64_forward(dgfs_plan_s *plan, int P, const void *f, double2 *F, cudaStream_t st);
-dgfs_status fp64_finish(dgfs_plan_s *plan, int p, int q, int P, double2 *QG, double2 *G2, const double2 *F,
-                        const void *f, void *Q, cudaStream_t st);
+dgfs_status fp64_finish_pairs(dgfs_plan_s *plan, int P, double2 *QG, long pair_stride, const double2 *F,
+                              const void *f, void *Q, cudaStream_t st);
 // moments (fft64.cu)
 dgfs_status moments(dgfs_plan_s *plan, int P, const void *Q, double *out, cudaStream_t st);
 // tc32.cu

@@ -1221,9 +1221,10 @@ __global__ void k_to_f32(float2 *dst, const double2 *src, long count)
 unsigned nblk(long total, int t) { return (unsigned)((total + t - 1) / t); }
 
 // Workspace of a tensor-core plan:
-//   F64 [maxP][S][n] d2 | QG64, G2 [maxP][n] d2 | Ap, Bq, H [Emax][RS][n] f2 | QGp [Emax][RSBmax][n] f2
+//   F64 [maxP][S][n] d2 | QG64 [S*S][maxP][n] d2 | Ap, Bq, H [Emax][RS][n] f2 | QGp [Emax][RSBmax][n] f2
 struct TcWs {
-    double2 *F64, *QG64, *G2;
+    double2 *F64, *QG64;  // QG64: pair p S + q at QG64 + (p S + q) qg_stride
+    long qg_stride;
     float2 *Ap, *Bq, *H, *QGp;
 };
 
@@ -1234,8 +1235,8 @@ TcWs ws_of(const dgfs_plan_s *plan)
     TcWs w;
     w.F64 = reinterpret_cast<double2 *>(plan->ws);
     w.QG64 = w.F64 + (long)plan->max_points * plan->S * n;
-    w.G2 = w.QG64 + (long)plan->max_points * n;
-    w.Ap = reinterpret_cast<float2 *>(w.G2 + (long)plan->max_points * n);
+    w.qg_stride = (long)plan->max_points * n;
+    w.Ap = reinterpret_cast<float2 *>(w.QG64 + (long)plan->S * plan->S * w.qg_stride);
     w.Bq = w.Ap + (long)ts->chunk_max * RS * n;
     w.H = w.Bq + (long)ts->chunk_max * RS * n;
     w.QGp = w.H + (long)ts->chunk_max * RS * n;
@@ -1337,14 +1338,14 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
                 DGFS_LAUNCHED(plan);
                 {
                     ProfScope ps(plan, "tc_sum_partials", st);
-                    k_sum_partials<<<nblk((long)Ec * n, 256), 256, 0, st>>>(w.QG64, w.QGp, RSB, n, pt0, Ec);
+                    k_sum_partials<<<nblk((long)Ec * n, 256), 256, 0, st>>>(w.QG64 + (p * S + q) * w.qg_stride,
+                                                                           w.QGp, RSB, n, pt0, Ec);
                 }
                 DGFS_LAUNCHED(plan);
             }
-            // step 10 in FP64 for this pair over all points
-            DGFS_TRY(fp64_finish(plan, p, q, P, w.QG64, w.G2, w.F64, f, Qout, st));
         }
-    return DGFS_OK;
+    // step 10 in FP64 for every pair and point
+    return fp64_finish_pairs(plan, P, w.QG64, w.qg_stride, w.F64, f, Qout, st);
 }
 
 template <int N, int FMT>
@@ -1369,11 +1370,11 @@ dgfs_status set_smem_attrs()
 // A batch holds, per (N, operand format) group of tensor-core plans, rounds of
 // jobs: round k runs the k-th job (species pair, chunk of points) of every
 // plan of the group, each stage as one launch over all of them.  The FP64
-// forward transforms, partial sums and finishing passes stay per plan.
+// forward transforms, partial sums and finishing passes stay per plan; the
+// finishing passes run once per plan after the last round.
 struct BatchJob {
     dgfs_plan_s *plan;
     int p, q, pt0, Ec, P;
-    bool last;  // last chunk of its pair: the finish follows
     const void *f;
     void *Q;
 };
@@ -1448,11 +1449,10 @@ dgfs_status round_launch(const BatchRound &r, cudaStream_t st)
         const long n = (long)N * N * N;
         {
             ProfScope ps(b.plan, "tc_sum_partials", st);
-            k_sum_partials<<<nblk((long)b.Ec * n, 256), 256, 0, st>>>(w.QG64, w.QGp, rs_blocks(b.plan), n, b.pt0,
-                                                                       b.Ec);
+            k_sum_partials<<<nblk((long)b.Ec * n, 256), 256, 0, st>>>(
+                w.QG64 + (b.p * b.plan->S + b.q) * w.qg_stride, w.QGp, rs_blocks(b.plan), n, b.pt0, b.Ec);
         }
         DGFS_LAUNCHED(b.plan);
-        if (b.last) DGFS_TRY(fp64_finish(b.plan, b.p, b.q, b.P, w.QG64, w.G2, w.F64, b.f, b.Q, st));
     }
     return DGFS_OK;
 }
@@ -1596,13 +1596,20 @@ size_t tc_workspace_bytes(const dgfs_plan_s *plan)
     const long n = (long)plan->N * plan->N * plan->N;
     const long RS = (long)plan->Nrho * plan->M;
     const long E = ts ? ts->chunk_max : 1, RSB = ts ? ts->rsb_max : 1;
-    return sizeof(double2) * ((long)plan->max_points * (plan->S + 2) * n) +
+    return sizeof(double2) * ((long)plan->max_points * (plan->S + plan->S * plan->S) * n) +
            sizeof(float2) * (3 * E * RS * n + E * RSB * n);
 }
 
+struct BatchPlan {
+    dgfs_plan_s *plan;
+    int P;
+    const void *f;
+    void *Q;
+};
+
 struct TcBatch {
     std::vector<BatchGroup> groups;
-    std::vector<std::pair<dgfs_plan_s *, std::pair<int, const void *>>> forwards;  // (plan, (P, f)) per TC plan
+    std::vector<BatchPlan> plans;  // forward transforms before the rounds, finishing passes after them
 };
 
 void tc_batch_free(void *handle)
@@ -1627,7 +1634,7 @@ dgfs_status tc_batch_build(int count, dgfs_plan_s *const *plans, const int *P, v
             tc_batch_free(b);
             return DGFS_EINVAL;
         }
-        b->forwards.push_back({plan, {P[i], f[i]}});
+        b->plans.push_back(BatchPlan{plan, P[i], f[i], Q[i]});
         BatchGroup *g = nullptr;
         for (auto &x : b->groups)
             if (x.N == plan->N && x.fmt == ts->fmt) g = &x;
@@ -1643,7 +1650,7 @@ dgfs_status tc_batch_build(int count, dgfs_plan_s *const *plans, const int *P, v
                 for (int pt0 = 0; pt0 < P[i]; pt0 += ts->chunk, ++k) {
                     if ((int)g->rounds.size() <= k) g->rounds.emplace_back();
                     const int Ec = std::min(ts->chunk, P[i] - pt0);
-                    g->rounds[k].jobs.push_back(BatchJob{plan, p, q, pt0, Ec, P[i], pt0 + Ec >= P[i], f[i], Q[i]});
+                    g->rounds[k].jobs.push_back(BatchJob{plan, p, q, pt0, Ec, P[i], f[i], Q[i]});
                 }
     }
     for (auto &g : b->groups)
@@ -1662,11 +1669,14 @@ dgfs_status tc_batch_build(int count, dgfs_plan_s *const *plans, const int *P, v
 dgfs_status tc_batch_launch(void *handle, cudaStream_t st)
 {
     TcBatch *b = reinterpret_cast<TcBatch *>(handle);
-    for (auto &fw : b->forwards)
-        DGFS_TRY(fp64_forward(fw.first, fw.second.first, fw.second.second, ws_of(fw.first).F64, st));
+    for (const BatchPlan &bp : b->plans) DGFS_TRY(fp64_forward(bp.plan, bp.P, bp.f, ws_of(bp.plan).F64, st));
     for (auto &g : b->groups)
         for (auto &r : g.rounds)
             DGFS_TRY(g.fmt == 0 ? round_dispatch<0>(g.N, r, false, st) : round_dispatch<1>(g.N, r, false, st));
+    for (const BatchPlan &bp : b->plans) {
+        const TcWs w = ws_of(bp.plan);
+        DGFS_TRY(fp64_finish_pairs(bp.plan, bp.P, w.QG64, w.qg_stride, w.F64, bp.f, bp.Q, st));
+    }
     return DGFS_OK;
 }
 
