@@ -169,6 +169,7 @@ void free_plan(dgfs_plan_s *plan)
         cudaFree(pt.wlog);
         cudaFree(pt.b32);
         cudaFree(pt.c32);
+        cudaFree(pt.cdf);
         cudaFree(pt.tmat);
     }
     cudaFree(plan->twiddle);

@@ -31,6 +31,7 @@ struct PairTables {
     float2 *b32 = nullptr;     // [RS][n]
     float2 *c32 = nullptr;     // [n]
     float *tmat = nullptr;     // translate / DFT matrices, see tc32.cu
+    float4 *cdf = nullptr;     // [n] c as double-float (findf.cu)
 };
 
 }  // namespace dgfs
@@ -123,8 +124,10 @@ dgfs_status fp64_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaS
 dgfs_status fp64_backward(dgfs_plan_s *plan, int P, const void *f, const void *dQ, void *df,
                           double *domega, int domega_on_host, cudaStream_t st);
 dgfs_status fp64_forward(dgfs_plan_s *plan, int P, const void *f, double2 *F, cudaStream_t st);
-dgfs_status fp64_finish_pairs(dgfs_plan_s *plan, int P, double2 *QG, long pair_stride, const double2 *F,
-                              const void *f, void *Q, cudaStream_t st);
+dgfs_status df_forward(dgfs_plan_s *plan, int P, const float *f, float4 *F, const float4 *tw, cudaStream_t st);
+dgfs_status df_finish(dgfs_plan_s *plan, int P, float4 *G, long pair_stride, const float4 *F, const float *f,
+                      float *Q, const float4 *tw, cudaStream_t st);
+dgfs_status df_tables(dgfs_plan_s *plan, float4 **tw_out);
 // moments (fft64.cu)
 dgfs_status moments(dgfs_plan_s *plan, int P, const void *Q, double *out, cudaStream_t st);
 // tc32.cu

@@ -65,12 +65,6 @@ struct PassArgs {
     double beta, inv_n, inv_n2;
     void *Q;              // [P][S][S][n]
     const double2 *tw;
-    // finishing passes over all pairs at once (FIN1-FIN3 with all_pairs != 0):
-    // blockIdx.y = pair p S + q, the pairs' grids pair_stride apart in G2,
-    // c and beta per pair
-    int all_pairs;
-    long pair_stride;
-    double betas[16];
 };
 
 template <int N, int AXIS>
@@ -209,7 +203,7 @@ __global__ void __launch_bounds__(128) k_pass(PassArgs a)
         for (int k = 0; k < N; ++k) qg[pencil_off<N, AXIS>(pi, k)] = acc_s[k * T + t];
     } else if constexpr (MODE == FIN1 || MODE == FIN2) {
         // in-place inverse pass on Z = Herm(QG) + i Herm(c F_q) (see k_herm)
-        double2 *g2 = a.G2 + (long)blockIdx.y * a.pair_stride + (long)blockIdx.z * n;
+        double2 *g2 = a.G2 + (long)blockIdx.z * n;
 #pragma unroll
         for (int j = 0; j < N; ++j) v[j] = g2[pencil_off<N, AXIS>(pi, j)];
         fft<N, +1>(v, tw);
@@ -217,16 +211,15 @@ __global__ void __launch_bounds__(128) k_pass(PassArgs a)
         for (int k = 0; k < N; ++k) g2[pencil_off<N, AXIS>(pi, k)] = v[k];
     } else if constexpr (MODE == FIN3) {
         // last inverse pass: ifft3_u(Z) = Re ifft3_u(QG) + i Re ifft3_u(c F_q)
-        const int e = blockIdx.z, pr = blockIdx.y;
+        const int e = blockIdx.z;
         const int pt = a.pt0 + e;
-        const int p = a.all_pairs ? pr / a.S : a.p, q = a.all_pairs ? pr % a.S : a.q;
-        const double2 *g2 = a.G2 + (long)pr * a.pair_stride + (long)e * n;
+        const double2 *g2 = a.G2 + (long)e * n;
 #pragma unroll
         for (int j = 0; j < N; ++j) v[j] = g2[pencil_off<N, AXIS>(pi, j)];
         fft<N, +1>(v, tw);
-        const long fbase = ((long)pt * a.S + p) * n;
-        const long qbase = (((long)pt * a.S + p) * a.S + q) * n;
-        const double sc = (a.all_pairs ? a.betas[pr] : a.beta) * a.inv_n;
+        const long fbase = ((long)pt * a.S + a.p) * n;
+        const long qbase = (((long)pt * a.S + a.p) * a.S + a.q) * n;
+        const double sc = a.beta * a.inv_n;
         if (a.f32) {
             const float *fr = reinterpret_cast<const float *>(a.f) + fbase;
             float *Q = reinterpret_cast<float *>(a.Q) + qbase;
@@ -267,35 +260,6 @@ __global__ void k_herm(double2 *G2, const double2 *QG, const double2 *F, const d
     const double h1x = 0.5 * (a0.x + a1.x), h1y = 0.5 * (a0.y - a1.y);
     const double h2x = 0.5 * (l0.x + l1.x), h2y = 0.5 * (l0.y - l1.y);
     G2[e * n + k] = make_double2(h1x - h2y, h1y + h2x);
-}
-
-// k_herm for all pairs and points at once, in place: the thread of the
-// smaller index of each pair {k, -k mod N} forms both Z(k) and Z(-k), using
-// Herm X(-k) = conj(Herm X(k)).  QG: [S*S][.][n] (pairs pair_stride apart),
-// points 0..P-1; F: [P][S][n].
-struct PairPtrs {
-    const double2 *c[16];
-};
-
-__global__ void k_herm_pairs(double2 *QG, long pair_stride, const double2 *F, PairPtrs cs, int N, long n, int S,
-                             int P)
-{
-    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;  // over [S*S][P][n]
-    if (i >= (long)S * S * P * n) return;
-    const long k = i % n, pe = i / n;
-    const int e = (int)(pe % P), pr = (int)(pe / P);
-    const int kx = (int)(k / ((long)N * N)), ky = (int)((k / N) % N), kz = (int)(k % N);
-    const long mk = ((long)((N - kx) % N) * N + (N - ky) % N) * N + (N - kz) % N;
-    if (mk < k) return;
-    double2 *qg = QG + (long)pr * pair_stride + (long)e * n;
-    const double2 *Fq = F + ((long)e * S + pr % S) * n;
-    const double2 *c = cs.c[pr];
-    const double2 a0 = qg[k], a1 = qg[mk];
-    const double2 l0 = cmul(c[k], Fq[k]), l1 = cmul(c[mk], Fq[mk]);
-    const double h1x = 0.5 * (a0.x + a1.x), h1y = 0.5 * (a0.y - a1.y);
-    const double h2x = 0.5 * (l0.x + l1.x), h2y = 0.5 * (l0.y - l1.y);
-    qg[k] = make_double2(h1x - h2y, h1y + h2x);
-    if (mk != k) qg[mk] = make_double2(h1x + h2y, h2x - h1y);
 }
 
 constexpr int kThreads = 128;
@@ -426,44 +390,6 @@ dgfs_status forward_n(dgfs_plan_s *plan, int P, const void *f, double2 *F, cudaS
     return DGFS_OK;
 }
 
-// Step 10 of Algorithm 2 in FP64 for every pair at points [0, P):
-// Q = beta/n Re( ifft3_u(QG) - f_p ifft3_u(c F_q) ).  QG holds pair p S + q at
-// QG + (p S + q) pair_stride, [P][n] each, and is overwritten.
-template <int N>
-dgfs_status finish_pairs_n(dgfs_plan_s *plan, int P, double2 *QG, long pair_stride, const double2 *F,
-                           const void *f, void *Q, cudaStream_t st)
-{
-    const int S = plan->S;
-    PassArgs a{};
-    a.n = (long)N * N * N;
-    a.S = S;
-    a.pt0 = 0;
-    a.f = reinterpret_cast<const double *>(f);
-    a.f32 = plan->prec == DGFS_FP64 ? 0 : 1;
-    a.F = const_cast<double2 *>(F);
-    a.G2 = QG;
-    a.all_pairs = 1;
-    a.pair_stride = pair_stride;
-    PairPtrs cs{};
-    for (int pr = 0; pr < S * S; ++pr) {
-        cs.c[pr] = plan->pairs[pr].c;
-        a.betas[pr] = plan->pairs[pr].beta;
-    }
-    a.inv_n = 1.0 / (double)a.n;
-    a.Q = Q;
-    a.tw = plan->twiddle;
-    const long total = (long)S * S * P * a.n;
-    {
-        ProfScope ps(plan, "fp64_herm", st);
-        k_herm_pairs<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(QG, pair_stride, F, cs, N, a.n, S, P);
-    }
-    DGFS_LAUNCHED(plan);
-    DGFS_TRY((launch<N, 0, FIN1>(plan, dim3(1, S * S, P), a, st)));
-    DGFS_TRY((launch<N, 1, FIN2>(plan, dim3(1, S * S, P), a, st)));
-    DGFS_TRY((launch<N, 2, FIN3>(plan, dim3(1, S * S, P), a, st)));
-    return DGFS_OK;
-}
-
 // ------------------------------------------------------------------ moments
 template <typename T>
 __global__ void __launch_bounds__(256) k_moments(const T *Q, double *out, int N, double L, const double *mass_of_p,
@@ -549,22 +475,6 @@ dgfs_status fp64_forward(dgfs_plan_s *plan, int P, const void *f, double2 *F, cu
     case 32: return forward_n<32>(plan, P, f, F, st);
     case 48: return forward_n<48>(plan, P, f, F, st);
     default: set_error("N not supported by the FP64 forward transform"); return DGFS_EUNSUPPORTED;
-    }
-}
-
-dgfs_status fp64_finish_pairs(dgfs_plan_s *plan, int P, double2 *QG, long pair_stride, const double2 *F,
-                              const void *f, void *Q, cudaStream_t st)
-{
-    switch (plan->N) {
-    case 4: return finish_pairs_n<4>(plan, P, QG, pair_stride, F, f, Q, st);
-    case 6: return finish_pairs_n<6>(plan, P, QG, pair_stride, F, f, Q, st);
-    case 8: return finish_pairs_n<8>(plan, P, QG, pair_stride, F, f, Q, st);
-    case 12: return finish_pairs_n<12>(plan, P, QG, pair_stride, F, f, Q, st);
-    case 16: return finish_pairs_n<16>(plan, P, QG, pair_stride, F, f, Q, st);
-    case 24: return finish_pairs_n<24>(plan, P, QG, pair_stride, F, f, Q, st);
-    case 32: return finish_pairs_n<32>(plan, P, QG, pair_stride, F, f, Q, st);
-    case 48: return finish_pairs_n<48>(plan, P, QG, pair_stride, F, f, Q, st);
-    default: set_error("N not supported by the FP64 finishing passes"); return DGFS_EUNSUPPORTED;
     }
 }
 

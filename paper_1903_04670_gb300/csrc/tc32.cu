@@ -36,6 +36,7 @@
 #include <cstring>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "dgfs_internal.h"
 #include "tcfmt.cuh"
 #include "umma.cuh"
@@ -64,6 +65,7 @@ struct TcState {
     uint8_t *idmask = nullptr;  // [RS] bit d set when sigma_{s,d} == 0 (T_d is the identity; x and y are skipped)
     int skip_identity = 1;
     int ws_a = 0;  // stage A variant: 0 two-pipeline, 1 warp-specialised, 2 two threads per row (autotuner)
+    float4 *tw_df = nullptr;  // [N] exp(-2 pi i j / N) as double-float (findf.cu)
 };
 
 struct TcArgs {
@@ -1141,19 +1143,19 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::C, 1) k_stage_c_batch(c
     k_stage_c_body<N, FMT>(t.job[j], job_block(g, blockIdx.x), make_uint3(g.gx, g.gy, g.gz));
 }
 
-// QG64[pt0 + e][k] = sum_rb QGp[e][rb][k]  (FP32 partials summed in FP64)
-__global__ void k_sum_partials(double2 *QG64, const float2 *QGp, int rsb, long n, int pt0, int E)
+// QG[pt0 + e][k] = sum_rb QGp[e][rb][k]  (FP32 partials summed in double-float)
+__global__ void k_sum_partials(float4 *QG, const float2 *QGp, int rsb, long n, int pt0, int E)
 {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long)E * n) return;
     const long e = i / n, k = i % n;
-    double sx = 0.0, sy = 0.0;
+    dfl sx(0.f, 0.f), sy(0.f, 0.f);
     for (int rb = 0; rb < rsb; ++rb) {
         const float2 v = QGp[(e * rsb + rb) * n + k];
-        sx += v.x;
-        sy += v.y;
+        sx = add_f(sx, v.x);
+        sy = add_f(sy, v.y);
     }
-    QG64[(pt0 + e) * n + k] = make_double2(sx, sy);
+    st_dcx(QG + (pt0 + e) * n + k, dcx{sx, sy});
 }
 
 // ------------------------------------------------------ table preparation
@@ -1221,9 +1223,10 @@ __global__ void k_to_f32(float2 *dst, const double2 *src, long count)
 unsigned nblk(long total, int t) { return (unsigned)((total + t - 1) / t); }
 
 // Workspace of a tensor-core plan:
-//   F64 [maxP][S][n] d2 | QG64 [S*S][maxP][n] d2 | Ap, Bq, H [Emax][RS][n] f2 | QGp [Emax][RSBmax][n] f2
+//   F [maxP][S][n] | QG [S*S][maxP][n] (complex double-floats, float4) | Ap, Bq, H [Emax][RS][n] f2 |
+//   QGp [Emax][RSBmax][n] f2
 struct TcWs {
-    double2 *F64, *QG64;  // QG64: pair p S + q at QG64 + (p S + q) qg_stride
+    float4 *F, *QG;  // QG: pair p S + q at QG + (p S + q) qg_stride
     long qg_stride;
     float2 *Ap, *Bq, *H, *QGp;
 };
@@ -1233,10 +1236,10 @@ TcWs ws_of(const dgfs_plan_s *plan)
     const TcState *ts = reinterpret_cast<const TcState *>(plan->tc);
     const long n = (long)plan->N * plan->N * plan->N, RS = (long)plan->Nrho * plan->M;
     TcWs w;
-    w.F64 = reinterpret_cast<double2 *>(plan->ws);
-    w.QG64 = w.F64 + (long)plan->max_points * plan->S * n;
+    w.F = reinterpret_cast<float4 *>(plan->ws);
+    w.QG = w.F + (long)plan->max_points * plan->S * n;
     w.qg_stride = (long)plan->max_points * n;
-    w.Ap = reinterpret_cast<float2 *>(w.QG64 + (long)plan->S * plan->S * w.qg_stride);
+    w.Ap = reinterpret_cast<float2 *>(w.QG + (long)plan->S * plan->S * w.qg_stride);
     w.Bq = w.Ap + (long)ts->chunk_max * RS * n;
     w.H = w.Bq + (long)ts->chunk_max * RS * n;
     w.QGp = w.H + (long)ts->chunk_max * RS * n;
@@ -1307,8 +1310,8 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
     const int E = ts->chunk, RSB = rs_blocks(plan);
     const TcWs w = ws_of(plan);
 
-    // FP64 forward transforms of f for the loss term (step 1 of Algorithm 2)
-    DGFS_TRY(fp64_forward(plan, P, f, w.F64, st));
+    // forward transforms of f for the loss term (step 1 of Algorithm 2)
+    DGFS_TRY(df_forward(plan, P, reinterpret_cast<const float *>(f), w.F, ts->tw_df, st));
     for (int p = 0; p < S; ++p)
         for (int q = 0; q < S; ++q) {
             for (int pt0 = 0; pt0 < P; pt0 += E) {
@@ -1338,14 +1341,15 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
                 DGFS_LAUNCHED(plan);
                 {
                     ProfScope ps(plan, "tc_sum_partials", st);
-                    k_sum_partials<<<nblk((long)Ec * n, 256), 256, 0, st>>>(w.QG64 + (p * S + q) * w.qg_stride,
+                    k_sum_partials<<<nblk((long)Ec * n, 256), 256, 0, st>>>(w.QG + (p * S + q) * w.qg_stride,
                                                                            w.QGp, RSB, n, pt0, Ec);
                 }
                 DGFS_LAUNCHED(plan);
             }
         }
-    // step 10 in FP64 for every pair and point
-    return fp64_finish_pairs(plan, P, w.QG64, w.qg_stride, w.F64, f, Qout, st);
+    // step 10 for every pair and point
+    return df_finish(plan, P, w.QG, w.qg_stride, w.F, reinterpret_cast<const float *>(f),
+                     reinterpret_cast<float *>(Qout), ts->tw_df, st);
 }
 
 template <int N, int FMT>
@@ -1450,7 +1454,7 @@ dgfs_status round_launch(const BatchRound &r, cudaStream_t st)
         {
             ProfScope ps(b.plan, "tc_sum_partials", st);
             k_sum_partials<<<nblk((long)b.Ec * n, 256), 256, 0, st>>>(
-                w.QG64 + (b.p * b.plan->S + b.q) * w.qg_stride, w.QGp, rs_blocks(b.plan), n, b.pt0, b.Ec);
+                w.QG + (b.p * b.plan->S + b.q) * w.qg_stride, w.QGp, rs_blocks(b.plan), n, b.pt0, b.Ec);
         }
         DGFS_LAUNCHED(b.plan);
     }
@@ -1518,6 +1522,7 @@ dgfs_status build_images(dgfs_plan_s *plan, TcState *ts)
         k_to_f32<<<nblk(RS * n, 256), 256>>>(pt.b32, pt.b, RS * n);
         DGFS_LAUNCHED(plan);
     }
+    DGFS_TRY(df_tables(plan, &ts->tw_df));
     return dispatch_attrs<FMT>(N);
 }
 
@@ -1586,6 +1591,7 @@ void tc_release(dgfs_plan_s *plan)
     cudaFree(ts->Fimg);
     cudaFree(ts->err);
     cudaFree(ts->idmask);
+    cudaFree(ts->tw_df);
     delete ts;
     plan->tc = nullptr;
 }
@@ -1596,7 +1602,7 @@ size_t tc_workspace_bytes(const dgfs_plan_s *plan)
     const long n = (long)plan->N * plan->N * plan->N;
     const long RS = (long)plan->Nrho * plan->M;
     const long E = ts ? ts->chunk_max : 1, RSB = ts ? ts->rsb_max : 1;
-    return sizeof(double2) * ((long)plan->max_points * (plan->S + plan->S * plan->S) * n) +
+    return sizeof(float4) * ((long)plan->max_points * (plan->S + plan->S * plan->S) * n) +
            sizeof(float2) * (3 * E * RS * n + E * RSB * n);
 }
 
@@ -1669,13 +1675,18 @@ dgfs_status tc_batch_build(int count, dgfs_plan_s *const *plans, const int *P, v
 dgfs_status tc_batch_launch(void *handle, cudaStream_t st)
 {
     TcBatch *b = reinterpret_cast<TcBatch *>(handle);
-    for (const BatchPlan &bp : b->plans) DGFS_TRY(fp64_forward(bp.plan, bp.P, bp.f, ws_of(bp.plan).F64, st));
+    for (const BatchPlan &bp : b->plans) {
+        const TcState *ts = reinterpret_cast<const TcState *>(bp.plan->tc);
+        DGFS_TRY(df_forward(bp.plan, bp.P, reinterpret_cast<const float *>(bp.f), ws_of(bp.plan).F, ts->tw_df, st));
+    }
     for (auto &g : b->groups)
         for (auto &r : g.rounds)
             DGFS_TRY(g.fmt == 0 ? round_dispatch<0>(g.N, r, false, st) : round_dispatch<1>(g.N, r, false, st));
     for (const BatchPlan &bp : b->plans) {
         const TcWs w = ws_of(bp.plan);
-        DGFS_TRY(fp64_finish_pairs(bp.plan, bp.P, w.QG64, w.qg_stride, w.F64, bp.f, bp.Q, st));
+        const TcState *ts = reinterpret_cast<const TcState *>(bp.plan->tc);
+        DGFS_TRY(df_finish(bp.plan, bp.P, w.QG, w.qg_stride, w.F, reinterpret_cast<const float *>(bp.f),
+                           reinterpret_cast<float *>(bp.Q), ts->tw_df, st));
     }
     return DGFS_OK;
 }
