@@ -1718,7 +1718,8 @@ dgfs_status tc_autotune(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaSt
     const bool ws_fits = plan->N == 16 || plan->N == 32;  // WsA<N, FMT>::OK
     const bool a2_fits = plan->N == 16 || plan->N == 32 || plan->N == 48;  // A2<N, FMT>::OK
     const int chunks[] = {ts->chunk_max, std::min(ts->chunk_max, 8)};
-    const int rsbs[] = {std::min(RS, 2), std::min(RS, 4), std::min(RS, 8), std::min(RS, 16)};
+    const int rsbs[] = {std::min(RS, 2), std::min(RS, 4), std::min(RS, 6), std::min(RS, 8),
+                        std::min(RS, 12), std::min(RS, 16)};
     const int waves[] = {4, 8, 16};
     for (int c : chunks)
         for (int r : rsbs)
