@@ -168,7 +168,6 @@ void free_plan(dgfs_plan_s *plan)
         cudaFree(pt.w);
         cudaFree(pt.wlog);
         cudaFree(pt.b32);
-        cudaFree(pt.c32);
         cudaFree(pt.cdf);
         cudaFree(pt.tmat);
     }

@@ -29,7 +29,6 @@ struct PairTables {
     double *wlog = nullptr;    // [RS]  -2 ln(rho_r) w_r w_s
     // FP32 tensor-core form (built only for non-FP64 plans)
     float2 *b32 = nullptr;     // [RS][n]
-    float2 *c32 = nullptr;     // [n]
     float *tmat = nullptr;     // translate / DFT matrices, see tc32.cu
     float4 *cdf = nullptr;     // [n] c as double-float (findf.cu)
 };
