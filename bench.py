@@ -178,7 +178,8 @@ def run_ours(args, rank, world):
             plan.collide(f, Q)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b) for a, b in ev)
+        per_step = sorted(a.elapsed_time(b) for a, b in ev)
+        ms = sum(per_step)
         prof = plan.profile_read()
         plan.profile(False)
         launches = plan.launch_count() - n0
@@ -186,7 +187,9 @@ def run_ours(args, rank, world):
         if world > 1:
             ms = D.max_over_ranks(ms, device="cuda")
         value = world * evals * steps / (ms / 1e3)
+        pct = lambda q: per_step[min(len(per_step) - 1, int(round(q * (len(per_step) - 1))))]
         rec = {"value": value, "ms_per_step": ms / steps, "steps": steps, "launches": launches,
+               "step_ms_p10_p50_p90": [pct(0.1), pct(0.5), pct(0.9)],
                "profile": prof, "plan": plan, "f": f, "Q": Q, "clocks": clk}
         forms[prec] = rec
         if main is None:
@@ -208,6 +211,9 @@ def run_ours(args, rank, world):
                       "launch_parameters": "dgfs_plan_autotune before timing" if not args.no_tune else "defaults",
                       "parallelism": "replicas: every rank evaluates its own 96 (point, pair) operators"}}
 
+    if not args.no_peaks:
+        out["alu_peaks"] = alu_peaks(torch)
+
     # roofline of the dominant kernel (by summed event time)
     prof = rec["profile"]
     dom = max(prof.items(), key=lambda kv: kv[1][1])
@@ -216,9 +222,14 @@ def run_ours(args, rank, world):
     work = kernel_work(name, info, P, S, RS)
     avg_s = tot_ms / cnt / 1e3
     if name.startswith("fp64"):
-        peak = 1250.0  # GFLOP/s: nominal GB300 FP64 (no measured FP64 peak on this machine)
+        if "alu_peaks" in out:
+            peak = out["alu_peaks"]["fp64_gemm_tflops"] * 1e3
+            psrc = "measured FP64 GEMM (cuBLAS) on this GPU"
+        else:
+            peak = 1250.0  # GFLOP/s: nominal GB300 FP64
+            psrc = "nominal FP64 of the GB300 (1.25 TFLOP/s)"
         roof = {"bound": "alu", "achieved": work / avg_s / 1e9 if work else None, "peak": peak,
-                "unit": "GFLOP/s", "peak_source": "nominal FP64 of the GB300 (1.25 TFLOP/s)"}
+                "unit": "GFLOP/s", "peak_source": psrc}
     else:
         sigma = plan.pair_tables(0, 0, with_b=False)["sigma"]
         roof = tc_roofline(name, info, P, S, RS, avg_s, peaks, src, cnt / rec["steps"], sigma)
@@ -231,6 +242,7 @@ def run_ours(args, rank, world):
     out["roofline"] = roof
     out["kernels"] = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in prof.items()}
     out["gpu_launches"] = rec["launches"]
+    out["step_ms_p10_p50_p90"] = rec["step_ms_p10_p50_p90"]
     out["clocks"] = rec["clocks"]
 
     # the same call replayed from one CUDA graph: the host-side scheduling cost
@@ -326,9 +338,17 @@ def run_ours(args, rank, world):
         Qo = prob.collide_all(pb["f"], points=sample_pts)
         dt = time.perf_counter() - t0
         n_ev = len(sample_pts) * S * S
+        # one evaluation on one core: the single-thread figure
+        O.set_threads(1)
+        t1 = time.perf_counter()
+        prob.pair(0, 1).collide(pb["f"][0, 0], pb["f"][0, 1])
+        dt1 = time.perf_counter() - t1
+        O.set_threads(cores)
         out["cpu_baseline"] = {"value": n_ev / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": "%d points x %d pairs of the same workload (points %s), FP64, "
-                                         "tables excluded" % (len(sample_pts), S * S, sample_pts)}
+                                         "tables excluded" % (len(sample_pts), S * S, sample_pts),
+                               "single_thread_value": 1.0 / dt1,
+                               "single_thread_sample": "pair (0, 1) at point 0 on one core"}
     out["forms"] = {}
     for prec, r in forms.items():
         if "value" not in r:
@@ -340,6 +360,35 @@ def run_ours(args, rank, world):
             d["rel_err_vs_oracle"] = float(np.abs(Qg - Qo).max() / np.abs(Qo).max())
             d["err_sample_points"] = sample_pts
         out["forms"][prec] = d
+    return out
+
+
+def alu_peaks(torch):
+    """FP64 and FP32 (CUDA-core) GEMM throughput of the GPU through cuBLAS, as
+    the measured reference points for the SIMT passes (TF32 tensor cores off
+    for the FP32 figure).  Library kernels, reported beside the result only."""
+    out = {}
+    old = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for name, dt, n in (("fp64_gemm_tflops", torch.float64, 4096), ("fp32_simt_gemm_tflops", torch.float32, 8192)):
+            a = torch.randn(n, n, dtype=dt, device="cuda")
+            b = torch.randn(n, n, dtype=dt, device="cuda")
+            for _ in range(2):
+                torch.matmul(a, b)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 5
+            e0.record()
+            for _ in range(reps):
+                torch.matmul(a, b)
+            e1.record()
+            e1.synchronize()
+            out[name] = 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) / 1e3) / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+    out["source"] = "torch.matmul (cuBLAS) on this GPU, TF32 off"
     return out
 
 
@@ -386,9 +435,10 @@ def uneven_batch(B, W, torch, np, prec, dev, flush, stream, plan, rec):
         torch.cuda.synchronize()
         return sum(pl.launch_count() for pl in plans) - n0
 
-    res = {"workload": "relaxation_batch: 256 homogeneous problems, N in {24, 32, 48}, 2 or 3 species "
-                       "(masses from {1, 2, 4}), M in {6, 12}, N_rho in {8, 16}, VHS or VSS, seeded "
-                       "two-Maxwellian data; one collision call + one relaxation step per problem per pass",
+    res = {"workload": "relaxation_batch: 256 homogeneous problems, N in {24, 32, 48} with L = N/3.2, 2 or 3 "
+                       "species (masses from {1, 2, 4}), M in {6, 12}, N_rho in {8, 16}, VHS or VSS, seeded "
+                       "two-Maxwellian data (seed 5); one collision call + one relaxation step per problem "
+                       "per pass",
            "instances": len(inst), "plans": len(plans), "evals_per_pass": evals, "precision": prec}
     t = timed(separate)
     res["separate_calls"] = {"ms_per_pass": t, "evals_per_s": evals / (t / 1e3), "launches": launches(separate)}
@@ -527,6 +577,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-dg", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true")

@@ -172,10 +172,11 @@ def krook_wu_problem(N, M, Nrho, m1=1.0, m2=1.0, L=12.0):
     return dict(N=N, L=L, M=M, Nrho=Nrho, masses=[m1, m2], pairs=pairs)
 
 
-def relaxation_batch(count=256, seed=6, L=8.0):
+def relaxation_batch(count=256, seed=5):
     """`count` spatially homogeneous relaxation problems with uneven
-    parameters: N from {24, 32, 48}, 2 or 3 species with distinct masses from
-    {1, 2, 4}, M from {6, 12}, N_rho from {8, 16}, VHS (alpha = 1) or VSS
+    parameters: N from {24, 32, 48} on [-L, L]^3 with L = N / 3.2 (the grid
+    spacing of the 1-D slab workload), 2 or 3 species with distinct masses
+    from {1, 2, 4}, M from {6, 12}, N_rho from {8, 16}, VHS (alpha = 1) or VSS
     (alpha = 1.4) with omega = 0.81, and two-Maxwellian data per species.
     Returns a list of dicts with the operator parameters and f of shape
     [1][S][N][N][N]."""
@@ -183,6 +184,7 @@ def relaxation_batch(count=256, seed=6, L=8.0):
     out = []
     for i in range(count):
         N = int(rng.choice([24, 32, 48]))
+        L = N / 3.2
         S = int(rng.choice([2, 3]))
         masses = sorted(float(m) for m in rng.choice([1.0, 2.0, 4.0], size=S, replace=False))
         M = int(rng.choice([6, 12]))

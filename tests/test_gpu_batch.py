@@ -58,14 +58,17 @@ def test_graph_of_uneven_batch_equals_separate_calls(batch):
 
 @pytest.fixture(scope="module")
 def worklist():
-    # two groups of N = 16 FP32 tensor-core plans with different job counts
-    # (S^2 pairs), an N = 8 plan whose 30 points take two chunks (24 + 6), a
-    # VHS plan on the sigma-collapsed path, a BF16 group and an FP64 plan
+    # three N = 16 FP32 tensor-core plans with different job counts (S^2
+    # pairs), one of them VHS on the sigma-collapsed path; an N = 8 plan whose
+    # 30 points take two chunks (24 + 6); N = 24 (ragged 5-plane tiles) and
+    # N = 32 groups; a BF16 group and an FP64 plan
     return [
         _instance(16, 2, 6, 8, 3, "fp32_tc", 11),
         _instance(16, 3, 12, 4, 2, "fp32_tc", 12),
         _instance(16, 2, 12, 3, 2, "fp32_tc", 13, vhs=True),
         _instance(8, 2, 6, 4, 30, "fp32_tc", 14),
+        _instance(24, 3, 6, 4, 2, "fp32_tc", 17),
+        _instance(32, 2, 12, 8, 3, "fp32_tc", 18),
         _instance(16, 1, 6, 4, 2, "bf16x3", 15),
         _instance(8, 1, 12, 4, 2, "fp64", 16),
     ]
@@ -90,7 +93,7 @@ def test_batched_worklist_equals_separate_calls(worklist):
 
 
 def test_batched_worklist_with_relaxation_matches_graph(worklist):
-    sub = [worklist[0], worklist[3]]
+    sub = [worklist[0], worklist[3], worklist[4]]
     dt = 0.01
     f_b = [i["f"].clone() for i in sub]
     f_g = [i["f"].clone() for i in sub]
