@@ -498,6 +498,8 @@ def tc_executed_flops(name, info, P, S, RS, sigma=None):
     else:
         sg = [list(map(float, v)) for v in sigma]
         live = [sum(1 for v in sg if v[d] != 0.0) / len(sg) for d in range(3)]
+        if N > 32:  # stage A skips the z-pass only where a row's z-pencil fits its prefetch registers
+            live[2] = 1.0
     if name == "tc_stage_a":
         return S * S * P * planes * RS * 2 * (live[2] * gem(KR) + live[1] * gem(KC))
     if name == "tc_stage_b":

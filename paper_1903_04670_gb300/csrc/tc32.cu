@@ -298,6 +298,10 @@ __device__ __forceinline__ void k_stage_a_body(const TcArgs &a, const uint3 bid,
     const long n = a.n;
     const int items = a.Ec * NG;
     const bool ident_y = a.idmask && (a.idmask[rs] & 2);
+    // sigma_z = 0: T_z = I, so the y-pass operand is built from f directly; a
+    // thread then loads its own row's z-pencil (needs N / 4 <= FPT float4)
+    constexpr bool ZSKIP = N % 4 == 0 && N / 4 <= FPT;
+    const bool ident_z = ZSKIP && a.idmask && (a.idmask[rs] & 4);
     cta_setup(&tslot, NCOL, mb, NP + 1);
     const uint32_t tb = tslot + pp * 2 * NO, tl = lane_base(tb);
     uint32_t ph_mma = 0, ph_cp = 0;
@@ -316,6 +320,12 @@ __device__ __forceinline__ void k_stage_a_body(const TcArgs &a, const uint3 bid,
         const int e = it / NG, x0 = (it % NG) * G, nval = min(G, N - x0);
         const float4 *fs =
             reinterpret_cast<const float4 *>(a.f + ((long)(a.pt0 + e) * a.S + sp) * n + (long)x0 * NN);
+        if (ident_z) {  // row t = (g, y): f(x0 + g, y, z) for all z
+#pragma unroll
+            for (int j = 0; j < FPT; ++j)
+                pf[j] = (j < N / 4 && t < nval * N) ? fs[t * (N / 4) + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            return;
+        }
 #pragma unroll
         for (int j = 0; j < FPT; ++j) {
             const int i = t + kRows * j;
@@ -332,6 +342,33 @@ __device__ __forceinline__ void k_stage_a_body(const TcArgs &a, const uint3 bid,
     }
     for (; it < items && ok; it += stride) {
         const int e = it / NG, x0 = (it % NG) * G, nval = min(G, N - x0);
+        if (ident_z) {
+            if (ident_y) {
+                // sigma_y = sigma_z = 0: A'(x0+g, y, z) = f for all z
+                float4 *dst = reinterpret_cast<float4 *>((side == 0 ? a.Ap : a.Bq) + ((long)e * a.RS + rs) * n +
+                                                         (long)(x0 + g) * NN + yl * N);
+                if (t < nval * N) {
+#pragma unroll
+                    for (int j = 0; j < N / 4; ++j) {
+                        dst[2 * j] = make_float4(pf[j].x, 0.f, pf[j].y, 0.f);
+                        dst[2 * j + 1] = make_float4(pf[j].z, 0.f, pf[j].w, 0.f);
+                    }
+                }
+                if (it + stride < items) prefetch(it + stride);
+                continue;
+            }
+            // the y-pass operand, rows (g, z), K = y, straight from this row's f values
+            if (t < nval * N) {
+#pragma unroll
+                for (int j = 0; j < N / 4; ++j) {
+                    tcfmt::st_c<FMT>(A0, AB, g * N + 4 * j, yl, pf[j].x, 0.f);
+                    tcfmt::st_c<FMT>(A0, AB, g * N + 4 * j + 1, yl, pf[j].y, 0.f);
+                    tcfmt::st_c<FMT>(A0, AB, g * N + 4 * j + 2, yl, pf[j].z, 0.f);
+                    tcfmt::st_c<FMT>(A0, AB, g * N + 4 * j + 3, yl, pf[j].w, 0.f);
+                }
+            }
+            if (it + stride < items) prefetch(it + stride);
+        } else {
 #pragma unroll
         for (int j = 0; j < FPT; ++j) {
             const int i = t + kRows * j;
@@ -375,6 +412,7 @@ __device__ __forceinline__ void k_stage_a_body(const TcArgs &a, const uint3 bid,
                     tcfmt::st_c<FMT>(A0, AB, g * N + c0 / 2 + j, yl, v[2 * j], v[2 * j + 1]);
             }
         });
+        }  // z-pass
         if (!RESIDENT) {
             load_imgs(1);
             ok = wait_copy_pipe(&mb[NP], ph_cp, bar);
