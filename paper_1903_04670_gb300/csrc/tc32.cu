@@ -336,8 +336,8 @@ __device__ __forceinline__ void k_stage_a_body(const TcArgs &a, const uint3 bid,
     int it = bid.x * NP + pp;
     if (it < items) prefetch(it);
     bool ok = true;
-    if (RESIDENT) {
-        load_imgs(2);
+    if (RESIDENT && !(ident_z && ident_y)) {  // only the images this (r, s) uses
+        load_imgs(ident_z ? 1 : (ident_y ? 0 : 2));
         ok = wait_copy_cta(&mb[NP], ph_cp);
     }
     for (; it < items && ok; it += stride) {
