@@ -855,8 +855,9 @@ __device__ __forceinline__ void k_stage_b_body(const TcArgs &a, const uint3 bid,
         load_pencil(pa_raw, a.Ap + ((long)e * a.RS + rs) * n + p0 + t, p0 + t < NN);
     }
     bool ok = true;
-    if (RESIDENT) {
-        load_images(0, 3);
+    if (RESIDENT) {  // sigma_x = 0 needs only F
+        if (ident_x) load_images(2, 1);
+        else load_images(0, 3);
         ok = wait_copy_cta(&mb[NP], ph_cp);
     }
     for (; it < items && ok; it += stride) {
