@@ -512,7 +512,7 @@ def tc_executed_flops(name, info, P, S, RS, sigma=None):
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the stage kernels of the
 # 3xTF32 form at N = 32, M = 12, N_rho = 8 from one ncu capture on 8 points (one species
 # pair per launch); A', B' and H are per point, so the bytes scale with the points per launch.
-NCU_TRAFFIC_8PT = {"tc_stage_a": 353.8e6, "tc_stage_b": 576.9e6, "tc_stage_c": 229.9e6}
+NCU_TRAFFIC_8PT = {"tc_stage_a": 351.4e6, "tc_stage_b": 574.7e6, "tc_stage_c": 229.9e6}
 
 
 def ncu_traffic(name, P):
