@@ -80,7 +80,9 @@ typedef struct {
  *   masses     : host array [S] of non-dimensional masses (> 0).
  *   pairs      : host array [S*S], p-major.
  *   prec       : arithmetic of the collision path (see dgfs_precision).
- *   max_points : largest P any later call may pass (>= 1); sizes workspace.
+ *   max_points : largest P any later call may pass (1 <= max_points <= 65535,
+ *                the points are one grid dimension of the per-point passes);
+ *                sizes the workspace.
  *   device     : CUDA device ordinal.
  * Tables are generated on the device in FP64 (per pair: R_pq, quadratures,
  * phase vectors, b^(pq) with N_rho*M*n entries and c^(pq) with n entries).

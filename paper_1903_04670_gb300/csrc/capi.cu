@@ -247,8 +247,9 @@ dgfs_status dgfs_plan_create(dgfs_plan *out, int N, double L, int M, int N_rho, 
         return N < 2 ? DGFS_EINVAL : DGFS_EUNSUPPORTED;
     }
     if (!(L > 0.0) || !std::isfinite(L) || (M != 6 && M != 12) || N_rho < 1 || N_rho > 64 || S < 1 || S > 4 ||
-        max_points < 1 || !masses || !pairs) {
-        set_error("invalid plan arguments (L > 0, M in {6, 12}, 1 <= N_rho <= 64, 1 <= S <= 4, max_points >= 1)");
+        max_points < 1 || max_points > 65535 || !masses || !pairs) {
+        set_error("invalid plan arguments (L > 0, M in {6, 12}, 1 <= N_rho <= 64, 1 <= S <= 4, "
+                  "1 <= max_points <= 65535)");
         return DGFS_EINVAL;
     }
     if (prec != DGFS_FP64 && prec != DGFS_FP32_TC && prec != DGFS_TF32 && prec != DGFS_BF16X3) {

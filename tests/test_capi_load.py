@@ -51,6 +51,15 @@ def test_argument_errors_without_gpu():
     with pytest.raises(B.DgfsError) as e:
         B.dgfs_plan_create(8, 1.0, 7, 4, [1.0], [dict(omega=0.8, alpha=1.0, d=1.0)])
     assert e.value.status == 1
+    for mp in (0, 65536):  # the points are one grid dimension of the per-point passes
+        with pytest.raises(B.DgfsError) as e:
+            B.dgfs_plan_create(8, 1.0, 6, 4, [1.0], [dict(omega=0.8, alpha=1.0, d=1.0)], max_points=mp)
+        assert e.value.status == 1
     null = ctypes.c_void_p()
     assert B.lib().dgfs_collide(null, 1, None, None, None) == 1
     assert B.lib().dgfs_plan_destroy(null) == 0
+    # batches: NULL handles and empty instance lists are argument errors
+    out = ctypes.c_void_p()
+    assert B.lib().dgfs_batch_create(0, None, None, None, None, 0.0, ctypes.byref(out)) == 1
+    assert B.lib().dgfs_batch_launch(null, None) == 1
+    assert B.lib().dgfs_batch_destroy(null) == 0
