@@ -66,6 +66,10 @@ struct TcState {
     int skip_identity = 1;
     int ws_a = 0;  // stage A variant: 0 two-pipeline, 1 warp-specialised, 2 two threads per row (autotuner)
     float4 *tw_df = nullptr;  // [N] exp(-2 pi i j / N) as double-float (findf.cu)
+    // stage A of the next job runs on a second stream while stage C of the
+    // current one drains (it only has to wait for stage B to have read A', B')
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_entry = nullptr, ev_a = nullptr, ev_b = nullptr;
 };
 
 struct TcArgs {
@@ -1349,6 +1353,17 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
     const int E = ts->chunk, RSB = rs_blocks(plan);
     const TcWs w = ws_of(plan);
 
+    // Stage A runs on the plan's side stream: job k's stage A waits for job
+    // k-1's stage B (the last reader of A', B'), so it overlaps job k-1's
+    // stage C; stage B waits for stage A.  The first stage A waits for the
+    // caller's stream at entry, and every side-stream launch is joined back
+    // through the stage B that consumes it (graph capture sees a closed fork).
+    // (serial when the plan's per-kernel profiler is on, so that every kernel's
+    // event-bracketed time is its own)
+    cudaStream_t sa = plan->prof ? st : ts->side;
+    const bool fork = sa != st;
+    if (fork) DGFS_CUDA(cudaEventRecord(ts->ev_entry, st));
+    bool first = true;
     // forward transforms of f for the loss term (step 1 of Algorithm 2)
     DGFS_TRY(df_forward(plan, P, reinterpret_cast<const float *>(f), w.F, ts->tw_df, st));
     for (int p = 0; p < S; ++p)
@@ -1358,21 +1373,28 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
                 const TcArgs a = job_args(plan, f, p, q, pt0, Ec);
                 dim3 gA, gB, gC;
                 job_grids<N, FMT>(plan, Ec, gA, gB, gC);
+                if (fork) DGFS_CUDA(cudaStreamWaitEvent(sa, first ? ts->ev_entry : ts->ev_b, 0));
+                first = false;
                 {
-                    ProfScope ps(plan, "tc_stage_a", st);
+                    ProfScope ps(plan, "tc_stage_a", sa);
                     if (WsA<N, FMT>::OK && ts->ws_a == 1)
-                        k_stage_a_ws<N, FMT><<<gA, 4 * kRows, WsA<N, FMT>::BYTES, st>>>(a);
+                        k_stage_a_ws<N, FMT><<<gA, 4 * kRows, WsA<N, FMT>::BYTES, sa>>>(a);
                     else if (A2<N, FMT>::OK && ts->ws_a == 2)
-                        k_stage_a2<N, FMT><<<gA, 2 * kRows * NPipes<N, FMT>::A, SM::A, st>>>(a);
+                        k_stage_a2<N, FMT><<<gA, 2 * kRows * NPipes<N, FMT>::A, SM::A, sa>>>(a);
                     else
-                        k_stage_a<N, FMT><<<gA, kRows * NPipes<N, FMT>::A, SM::A, st>>>(a);
+                        k_stage_a<N, FMT><<<gA, kRows * NPipes<N, FMT>::A, SM::A, sa>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
+                if (fork) {
+                    DGFS_CUDA(cudaEventRecord(ts->ev_a, sa));
+                    DGFS_CUDA(cudaStreamWaitEvent(st, ts->ev_a, 0));
+                }
                 {
                     ProfScope ps(plan, "tc_stage_b", st);
                     k_stage_b<N, FMT><<<gB, kRows * NPipes<N, FMT>::B, SM::B, st>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
+                if (fork) DGFS_CUDA(cudaEventRecord(ts->ev_b, st));
                 {
                     ProfScope ps(plan, "tc_stage_c", st);
                     k_stage_c<N, FMT><<<gC, kRows * NPipes<N, FMT>::C, SM::C, st>>>(a);
@@ -1465,22 +1487,39 @@ dgfs_status round_build(BatchRound &r)
     return DGFS_OK;
 }
 
+// Stage A of a launch on a side stream, as in collide_n: it waits for the
+// previous launch's stage B (the last reader of A', B'), so it overlaps that
+// launch's stage C; stage B waits for it.
+struct Fork {
+    cudaStream_t sa;
+    cudaEvent_t ev_entry, ev_a, ev_b;
+    bool on, first;
+};
+
 template <int N, int FMT>
-dgfs_status round_launch(const BatchRound &r, cudaStream_t st)
+dgfs_status round_launch(const BatchRound &r, cudaStream_t st, Fork &fk)
 {
     using SM = Smem<N, FMT>;
     dgfs_plan_s *lead = r.jobs[0].plan;  // launch counting and profiling
+    const cudaStream_t sa = fk.on ? fk.sa : st;
     for (size_t l = 0; l < r.tabs.size(); l += 3) {
+        if (fk.on) DGFS_CUDA(cudaStreamWaitEvent(sa, fk.first ? fk.ev_entry : fk.ev_b, 0));
+        fk.first = false;
         {
-            ProfScope ps(lead, "tc_stage_a", st);
-            k_stage_a_batch<N, FMT><<<r.ctas[l], kRows * NPipes<N, FMT>::A, SM::A, st>>>(r.tabs[l]);
+            ProfScope ps(lead, "tc_stage_a", sa);
+            k_stage_a_batch<N, FMT><<<r.ctas[l], kRows * NPipes<N, FMT>::A, SM::A, sa>>>(r.tabs[l]);
         }
         DGFS_LAUNCHED(lead);
+        if (fk.on) {
+            DGFS_CUDA(cudaEventRecord(fk.ev_a, sa));
+            DGFS_CUDA(cudaStreamWaitEvent(st, fk.ev_a, 0));
+        }
         {
             ProfScope ps(lead, "tc_stage_b", st);
             k_stage_b_batch<N, FMT><<<r.ctas[l + 1], kRows * NPipes<N, FMT>::B, SM::B, st>>>(r.tabs[l + 1]);
         }
         DGFS_LAUNCHED(lead);
+        if (fk.on) DGFS_CUDA(cudaEventRecord(fk.ev_b, st));
         {
             ProfScope ps(lead, "tc_stage_c", st);
             k_stage_c_batch<N, FMT><<<r.ctas[l + 2], kRows * NPipes<N, FMT>::C, SM::C, st>>>(r.tabs[l + 2]);
@@ -1501,14 +1540,14 @@ dgfs_status round_launch(const BatchRound &r, cudaStream_t st)
 }
 
 template <int FMT>
-dgfs_status round_dispatch(int N, BatchRound &r, bool build, cudaStream_t st)
+dgfs_status round_dispatch(int N, BatchRound &r, bool build, cudaStream_t st, Fork *fk)
 {
     switch (N) {
-    case 8: return build ? round_build<8, FMT>(r) : round_launch<8, FMT>(r, st);
-    case 16: return build ? round_build<16, FMT>(r) : round_launch<16, FMT>(r, st);
-    case 24: return build ? round_build<24, FMT>(r) : round_launch<24, FMT>(r, st);
-    case 32: return build ? round_build<32, FMT>(r) : round_launch<32, FMT>(r, st);
-    case 48: return build ? round_build<48, FMT>(r) : round_launch<48, FMT>(r, st);
+    case 8: return build ? round_build<8, FMT>(r) : round_launch<8, FMT>(r, st, *fk);
+    case 16: return build ? round_build<16, FMT>(r) : round_launch<16, FMT>(r, st, *fk);
+    case 24: return build ? round_build<24, FMT>(r) : round_launch<24, FMT>(r, st, *fk);
+    case 32: return build ? round_build<32, FMT>(r) : round_launch<32, FMT>(r, st, *fk);
+    case 48: return build ? round_build<48, FMT>(r) : round_launch<48, FMT>(r, st, *fk);
     default: set_error("batch: N not supported by the tensor-core path"); return DGFS_EUNSUPPORTED;
     }
 }
@@ -1606,6 +1645,10 @@ dgfs_status tc_prepare(dgfs_plan_s *plan)
     ts->groups_b = std::max(1, (8 * sms + RS / 2) / RS);
     DGFS_CUDA(cudaMalloc(&ts->err, sizeof(int)));
     DGFS_CUDA(cudaMemset(ts->err, 0, sizeof(int)));
+    DGFS_CUDA(cudaStreamCreateWithFlags(&ts->side, cudaStreamNonBlocking));
+    DGFS_CUDA(cudaEventCreateWithFlags(&ts->ev_entry, cudaEventDisableTiming));
+    DGFS_CUDA(cudaEventCreateWithFlags(&ts->ev_a, cudaEventDisableTiming));
+    DGFS_CUDA(cudaEventCreateWithFlags(&ts->ev_b, cudaEventDisableTiming));
     // axes along which the design direction has no component: the translate
     // there is exp(i 0) = 1 in k-space, i.e. the identity, and is skipped
     {
@@ -1631,6 +1674,10 @@ void tc_release(dgfs_plan_s *plan)
     cudaFree(ts->err);
     cudaFree(ts->idmask);
     cudaFree(ts->tw_df);
+    if (ts->side) cudaStreamDestroy(ts->side);
+    if (ts->ev_entry) cudaEventDestroy(ts->ev_entry);
+    if (ts->ev_a) cudaEventDestroy(ts->ev_a);
+    if (ts->ev_b) cudaEventDestroy(ts->ev_b);
     delete ts;
     plan->tc = nullptr;
 }
@@ -1655,12 +1702,18 @@ struct BatchPlan {
 struct TcBatch {
     std::vector<BatchGroup> groups;
     std::vector<BatchPlan> plans;  // forward transforms before the rounds, finishing passes after them
+    cudaStream_t side = nullptr;   // stage A launches (see Fork)
+    cudaEvent_t ev_entry = nullptr, ev_a = nullptr, ev_b = nullptr;
 };
 
 void tc_batch_free(void *handle)
 {
     TcBatch *b = reinterpret_cast<TcBatch *>(handle);
     if (!b) return;
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->ev_entry) cudaEventDestroy(b->ev_entry);
+    if (b->ev_a) cudaEventDestroy(b->ev_a);
+    if (b->ev_b) cudaEventDestroy(b->ev_b);
     delete b;
 }
 
@@ -1700,13 +1753,21 @@ dgfs_status tc_batch_build(int count, dgfs_plan_s *const *plans, const int *P, v
     }
     for (auto &g : b->groups)
         for (auto &r : g.rounds) {
-            const dgfs_status st = g.fmt == 0 ? round_dispatch<0>(g.N, r, true, nullptr)
-                                              : round_dispatch<1>(g.N, r, true, nullptr);
+            const dgfs_status st = g.fmt == 0 ? round_dispatch<0>(g.N, r, true, nullptr, nullptr)
+                                              : round_dispatch<1>(g.N, r, true, nullptr, nullptr);
             if (st != DGFS_OK) {
                 tc_batch_free(b);
                 return st;
             }
         }
+    cudaError_t e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_entry, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_a, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_b, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        tc_batch_free(b);
+        return cuda_status(e, "batch stream and events");
+    }
     *out = b;
     return DGFS_OK;
 }
@@ -1714,13 +1775,19 @@ dgfs_status tc_batch_build(int count, dgfs_plan_s *const *plans, const int *P, v
 dgfs_status tc_batch_launch(void *handle, cudaStream_t st)
 {
     TcBatch *b = reinterpret_cast<TcBatch *>(handle);
+    // serial when a plan's per-kernel profiler is on (as in collide_n)
+    bool prof = false;
+    for (const BatchPlan &bp : b->plans) prof |= bp.plan->prof != nullptr;
+    Fork fk{b->side, b->ev_entry, b->ev_a, b->ev_b, !prof, true};
+    if (fk.on) DGFS_CUDA(cudaEventRecord(fk.ev_entry, st));
     for (const BatchPlan &bp : b->plans) {
         const TcState *ts = reinterpret_cast<const TcState *>(bp.plan->tc);
         DGFS_TRY(df_forward(bp.plan, bp.P, reinterpret_cast<const float *>(bp.f), ws_of(bp.plan).F, ts->tw_df, st));
     }
     for (auto &g : b->groups)
         for (auto &r : g.rounds)
-            DGFS_TRY(g.fmt == 0 ? round_dispatch<0>(g.N, r, false, st) : round_dispatch<1>(g.N, r, false, st));
+            DGFS_TRY(g.fmt == 0 ? round_dispatch<0>(g.N, r, false, st, &fk)
+                                : round_dispatch<1>(g.N, r, false, st, &fk));
     for (const BatchPlan &bp : b->plans) {
         const TcWs w = ws_of(bp.plan);
         const TcState *ts = reinterpret_cast<const TcState *>(bp.plan->tc);
