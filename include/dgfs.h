@@ -248,7 +248,8 @@ dgfs_status dgfs_graph_destroy(dgfs_graph graph);
  * points) job of every such instance, each CTA finding its job in a device
  * table; FP64 instances run their own collision call.  The pointers are fixed
  * at creation (their contents may change between launches); plans must be
- * distinct, on one device, and not used elsewhere while the batch runs.  A plan
+ * distinct, on one device, not used elsewhere while the batch runs, and
+ * destroyed only after the batch.  A plan
  * whose launch configuration changes afterwards (dgfs_plan_autotune,
  * dgfs_plan_set_kernel_variant, dgfs_plan_set_collapse) makes the batch stale:
  * dgfs_batch_launch then returns EINVAL and a new batch is needed.  Stage A
