@@ -428,8 +428,12 @@ class Batch:
 
     def __init__(self, plans, fs, Qs, dt=0.0):
         self.plans, self.fs, self.Qs = list(plans), list(fs), list(Qs)
-        for pl, f in zip(self.plans, self.fs):
-            pl._check_f(f)
+        if not (len(self.plans) == len(self.fs) == len(self.Qs)):
+            raise ValueError("plans, fs and Qs must have the same length")
+        for pl, f, Q in zip(self.plans, self.fs, self.Qs):
+            P = pl._check_f(f)
+            if not (Q.is_cuda and Q.dtype == pl.dtype and Q.is_contiguous() and Q.numel() == P * pl.S * pl.S * pl.n):
+                raise ValueError("Q must be a contiguous %s CUDA tensor of shape [P][S][S][N][N][N]" % pl.dtype)
         self._h = dgfs_batch_create([pl._h for pl in self.plans], [f.shape[0] for f in self.fs], self.fs,
                                     self.Qs, dt)
 
