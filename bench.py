@@ -340,7 +340,11 @@ def run_ours(args, rank, world):
     # relaxation step of every problem per pass, run as separate calls, as a
     # graph of those calls, and as the batched work list (eager and captured)
     if not args.no_batch and main != "fp64" and world == 1:
-        out["uneven_batch"] = uneven_batch(B, W, torch, np, main, dev, flush, stream, plan, rec)
+        try:
+            out["uneven_batch"] = uneven_batch(B, W, torch, np, main, dev, flush, stream, plan, rec)
+        except (B.DgfsError, ValueError, RuntimeError) as e:  # reported; the headline line still prints
+            out["uneven_batch"] = {"error": str(e)}
+            torch.cuda.synchronize()
 
     # per-form throughput and error vs the oracle on a sampled subset of points
     sample_pts = [i for i in (0, 7, 15, 23) if i < P] if not args.quick else [0]
