@@ -13,7 +13,15 @@ Prints ONE JSON line (rank 0).  Fields beyond the base contract:
                CUDA-event duration inside the timed region,
   cpu_baseline the FP64 oracle timed on this host's cores on a bounded sample,
   e2e          the same metric through the host-buffer C-ABI call,
-  clocks       nvidia-smi samples taken during the timed region.
+  clocks       nvidia-smi samples taken during the timed region,
+  step_ms_p10_p50_p90  the spread of the timed steps,
+  kernels      per-kernel CUDA-event times from a profiled pass after the timed
+               region (the library then issues its launches in one stream),
+  alu_peaks    cuBLAS FP64 and FP32 (TF32 off) GEMM rates of this GPU,
+  graph        the same call replayed from one CUDA graph,
+  dg_step      one SSP-RK3 step of the 1-D DG heat-transfer slab,
+  uneven_batch 256 uneven relaxation problems: separate calls, a graph of them,
+               and the batched work list (eager and captured).
 
 --impl reference times the FP64 CPU oracle (the only reference that exists:
 the paper publishes no code) on a bounded sample of the same workload.
