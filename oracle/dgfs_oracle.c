@@ -46,7 +46,10 @@
  * Gauss-Legendre exactness, design exactness, Funk-Hecke vs direct
  * quadrature, Knudsen numbers of Table 2, brute-force Galerkin sum of Eq. 7,
  * Krook-Wu closed form, equilibrium, conservation, symmetries, dot-product
- * test of the adjoint, finite differences in omega).  The absolute accuracy
+ * test of the adjoint, finite differences in omega, the loss term against an
+ * independent quadrature of the truncated collision frequency for omega != 1
+ * (pins the radial weight rho^{gamma+2}), moments of shifted Maxwellians
+ * against their closed forms).  The absolute accuracy
  * of the VSS (alpha != 1) operator is only constrained indirectly
  * (equilibrium, conservation trends): "parity unpinned" for that property.
  */
