@@ -420,14 +420,16 @@ def alu_peaks(torch):
     return out
 
 
-def uneven_batch(B, W, torch, np, prec, dev, flush, stream, plan, rec):
-    """Timings of the batched work list on the uneven relaxation workload, and
-    the work list's own device cost on the benchmark call (one instance)."""
+def uneven_plans(B, W, torch, np, prec, dev, count=256):
+    """The uneven relaxation workload as plans: problems with equal parameters
+    share one plan as its points.  Returns (groups, plans, fs, Qs), groups[i]
+    being the list of problems (dicts of workloads.relaxation_batch) whose
+    data fs[i] holds, in order."""
     import collections
 
-    inst = W.relaxation_batch()
+    inst = W.relaxation_batch(count)
     groups = collections.OrderedDict()
-    for x in inst:  # problems with equal parameters share a plan as its points
+    for x in inst:
         groups.setdefault((x["N"], tuple(x["masses"]), x["M"], x["Nrho"], x["alpha"]), []).append(x)
     plans, fs, Qs = [], [], []
     for xs in groups.values():
@@ -436,10 +438,17 @@ def uneven_batch(B, W, torch, np, prec, dev, flush, stream, plan, rec):
         fs.append(torch.from_numpy(np.concatenate([y["f"] for y in xs])).to("cuda", pl.dtype).contiguous())
         Qs.append(torch.empty(len(xs), pl.S, pl.S, pl.N, pl.N, pl.N, dtype=pl.dtype, device="cuda"))
         plans.append(pl)
+    return list(groups.values()), plans, fs, Qs
+
+
+def uneven_batch(B, W, torch, np, prec, dev, flush, stream, plan, rec, count=256, reps=5):
+    """Timings of the batched work list on the uneven relaxation workload, and
+    the work list's own device cost on the benchmark call (one instance)."""
+    _, plans, fs, Qs = uneven_plans(B, W, torch, np, prec, dev, count)
     evals = sum(f.shape[0] * pl.S * pl.S for pl, f in zip(plans, fs))
     dt = 1e-3
 
-    def timed(fn, reps=5):
+    def timed(fn, reps=reps):
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
@@ -463,11 +472,11 @@ def uneven_batch(B, W, torch, np, prec, dev, flush, stream, plan, rec):
         torch.cuda.synchronize()
         return sum(pl.launch_count() for pl in plans) - n0
 
-    res = {"workload": "relaxation_batch: 256 homogeneous problems, N in {24, 32, 48} with L = N/3.2, 2 or 3 "
+    res = {"workload": "relaxation_batch: %d homogeneous problems, N in {24, 32, 48} with L = N/3.2, 2 or 3 "
                        "species (masses from {1, 2, 4}), M in {6, 12}, N_rho in {8, 16}, VHS or VSS, seeded "
                        "two-Maxwellian data (seed 5); one collision call + one relaxation step per problem "
-                       "per pass",
-           "instances": len(inst), "plans": len(plans), "evals_per_pass": evals, "precision": prec}
+                       "per pass" % count,
+           "instances": count, "plans": len(plans), "evals_per_pass": evals, "precision": prec}
     t = timed(separate)
     res["separate_calls"] = {"ms_per_pass": t, "evals_per_s": evals / (t / 1e3), "launches": launches(separate)}
     g = B.dgfs_graph_capture([pl._h for pl in plans], [f.shape[0] for f in fs], fs, Qs, dt=dt)
@@ -499,10 +508,10 @@ def uneven_batch(B, W, torch, np, prec, dev, flush, stream, plan, rec):
     # instance against its plain launches (same kernels, default stage A variant)
     plan.set_kernel_variant(0)
     f, Q = rec["f"], rec["Q"]
-    t_plain = timed(lambda: plan.collide(f, Q), reps=10)
+    t_plain = timed(lambda: plan.collide(f, Q), reps=2 * reps)
     b1 = B.Batch([plan], [f], [Q])
     try:
-        t_b1 = timed(lambda: b1.launch(stream), reps=10)
+        t_b1 = timed(lambda: b1.launch(stream), reps=2 * reps)
     finally:
         b1.close()
     res["one_instance"] = {"plain_ms": t_plain, "batch_ms": t_b1, "overhead": t_b1 / t_plain - 1.0}

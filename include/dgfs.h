@@ -150,7 +150,10 @@ dgfs_status dgfs_collide_host(dgfs_plan plan, int P, const void *f_host, void *Q
  * routine.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept per device together with
+ *    the id of the context it was found in; after cudaDeviceReset the next
+ *    call runs in a new context and looks the address up again (make that
+ *    call, too, outside a stream capture).
  *  - All calls on a device share the one array: calls that may overlap on the
  *    GPU (other streams, other host threads) race and must be serialised by the
  *    caller.  Nothing in the array needs to start at zero.
@@ -388,6 +391,31 @@ dgfs_status dgfs_dg_rhs_halo(dgfs_dg dg, const void *f_dev, const void *Q_dev, v
 dgfs_status dgfs_dg_stage(dgfs_dg dg, const void *f_in_dev, const void *f0_dev, void *out_dev, double a0, double a1,
                           double dt, int with_collisions, const double *halo_left_dev,
                           const double *halo_right_dev, void *stream);
+
+/* Peak issue rate of the tensor cores on `device` (instrumentation for the
+ * roofline, no counterpart in the paper): one CTA per SM issues `iters`
+ * back-to-back tcgen05 MMAs of shape M = 128, N = 256 from zeroed shared-memory
+ * operands into TMEM; kind 0 = kind::tf32 (K = 8 per MMA, the peak of the
+ * TF32-split forms), kind 1 = kind::f16 with BF16 operands (K = 16, the peak
+ * of the split-BF16 form).  *tflops = 2 M N K iters SMs / (best of three
+ * timed launches, CUDA events).  Synchronous; allocates 4 bytes.
+ * 64 <= iters <= 65536.  Errors: EINVAL, ECUDA, ETIMEOUT. */
+dgfs_status dgfs_probe_mma_rate(int device, int kind, int iters, double *tflops);
+
+/* Host-side fault injection for the library's own allocations
+ * (instrumentation, no counterpart in the paper).  After
+ * dgfs_debug_fail_alloc(n), n > 0, the n-th allocation the library makes from
+ * then on -- a device allocation or one of its host objects (plan, tensor-core
+ * state, batch, graph, DG object) -- reports failure without allocating; the
+ * call that made it returns DGFS_ENOMEM, sets its output handle to NULL and
+ * releases what it had allocated.  The hook then switches itself off; n = 0
+ * switches it off at once.  Process-wide, not thread-safe against concurrent
+ * creation calls.  No GPU fault is involved: the failure is decided on the
+ * host before the allocation routine would run.
+ * dgfs_debug_live_allocations: device allocations the library holds now
+ * (plans, batches, DG objects and per-call workspaces not yet released). */
+void dgfs_debug_fail_alloc(int n);
+long long dgfs_debug_live_allocations(void);
 
 /* Static strings; never NULL. */
 const char *dgfs_status_string(dgfs_status s);

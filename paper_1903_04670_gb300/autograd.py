@@ -32,6 +32,12 @@ class CollisionOperator:
         passed with requires_grad to receive dL/d omega."""
         if omega is None:
             omega = self.omega
+        elif tuple(omega.shape) != (self.S, self.S) or not torch.equal(
+                omega.detach().to(self.omega.device, torch.float64), self.omega):
+            # the plans' tables are built for fixed omega: a different value would
+            # give Q at the plan's omega and a gradient that looks valid
+            raise ValueError("omega must equal the plan's VHS/VSS exponents %s; build a new "
+                             "CollisionOperator for other values" % self.omega.cpu().tolist())
         return _Collide.apply(f, omega, self)
 
 

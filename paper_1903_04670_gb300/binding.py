@@ -84,6 +84,9 @@ def lib():
             "dgfs_status_string": (ctypes.c_char_p, [i]),
             "dgfs_last_error": (ctypes.c_char_p, []),
             "dgfs_version": (ctypes.c_char_p, []),
+            "dgfs_probe_mma_rate": (i, [i, i, i, ctypes.POINTER(d)]),
+            "dgfs_debug_fail_alloc": (None, [i]),
+            "dgfs_debug_live_allocations": (ll, []),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -120,6 +123,23 @@ def _stream(stream):
 
 
 # ------------------------------------------------------------ C-named wrappers
+def dgfs_probe_mma_rate(device=0, kind="tf32", iters=4096):
+    """Measured tcgen05 issue rate (TFLOP/s) of kind 'tf32' or 'bf16' MMAs, M = 128, N = 256, all SMs."""
+    v = ctypes.c_double(0.0)
+    k = {"tf32": 0, "bf16": 1}[kind] if isinstance(kind, str) else int(kind)
+    _check(lib().dgfs_probe_mma_rate(int(device), k, int(iters), ctypes.byref(v)), "dgfs_probe_mma_rate")
+    return float(v.value)
+
+
+def dgfs_debug_fail_alloc(n):
+    """Host-side fault injection: the n-th allocation of the library from now fails (0: off)."""
+    lib().dgfs_debug_fail_alloc(int(n))
+
+
+def dgfs_debug_live_allocations():
+    return int(lib().dgfs_debug_live_allocations())
+
+
 def dgfs_version():
     return lib().dgfs_version().decode()
 

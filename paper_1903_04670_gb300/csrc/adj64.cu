@@ -413,7 +413,7 @@ dgfs_status backward_n(dgfs_plan_s *plan, int P, const void *f, const void *dQ, 
         // the adjoint needs more than the forward's workspace: allocate for this call
         E = 1;
         need = fixed + per_eval;
-        DGFS_CUDA(cudaMallocAsync(&own, need, st));
+        DGFS_CUDA(dev_malloc_async(&own, need, st));
         ws = own;
     }
     char *base = reinterpret_cast<char *>(ws);
@@ -496,7 +496,7 @@ dgfs_status backward_n(dgfs_plan_s *plan, int P, const void *f, const void *dQ, 
                                   domega_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
         if (domega_on_host) DGFS_CUDA(cudaStreamSynchronize(st));
     }
-    if (own) DGFS_CUDA(cudaFreeAsync(own, st));
+    if (own) DGFS_CUDA(dev_free_async(own, st));
     return DGFS_OK;
 }
 

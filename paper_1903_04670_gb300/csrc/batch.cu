@@ -104,8 +104,11 @@ dgfs_status dgfs_graph_capture(int count, const dgfs_plan *plans, const int *P, 
     }
     dgfs_status st = plan_entry_check(plans[0]);
     if (st != DGFS_OK) return st;
-    dgfs_graph_s *g = new (std::nothrow) dgfs_graph_s();
-    if (!g) return DGFS_ENOMEM;
+    dgfs_graph_s *g = host_new<dgfs_graph_s>();
+    if (!g) {
+        set_error("dgfs_graph_capture: out of host memory");
+        return DGFS_ENOMEM;
+    }
     g->device = plans[0]->device;
     cudaError_t e = cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -168,8 +171,11 @@ dgfs_status dgfs_batch_create(int count, const dgfs_plan *plans, const int *P, v
     }
     dgfs_status st = plan_entry_check(plans[0]);
     if (st != DGFS_OK) return st;
-    dgfs_batch_s *b = new (std::nothrow) dgfs_batch_s();
-    if (!b) return DGFS_ENOMEM;
+    dgfs_batch_s *b = host_new<dgfs_batch_s>();
+    if (!b) {
+        set_error("dgfs_batch_create: out of host memory");
+        return DGFS_ENOMEM;
+    }
     b->device = plans[0]->device;
     b->dt = dt;
     std::vector<dgfs_plan_s *> tcp;

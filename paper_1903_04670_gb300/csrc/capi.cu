@@ -3,6 +3,7 @@
 // quadrature, spherical designs, beta^(pq)), dispatch to the FP64 and
 // tensor-core paths, host-buffer variant, moments and introspection.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -24,6 +25,55 @@ dgfs_status cuda_status(cudaError_t e, const char *what)
 }
 
 size_t elem_size(const dgfs_plan_s *plan) { return plan->prec == DGFS_FP64 ? sizeof(double) : sizeof(float); }
+
+// ------------------------------------------------- allocation accounting
+namespace {
+std::atomic<long long> g_live_device_allocs{0};
+std::atomic<int> g_fail_countdown{0};  // > 0: that many allocations from now, the last one fails
+}  // namespace
+
+bool alloc_fault_injected()
+{
+    int c = g_fail_countdown.load();
+    while (c > 0)
+        if (g_fail_countdown.compare_exchange_weak(c, c - 1)) return c == 1;
+    return false;
+}
+
+cudaError_t dev_malloc_raw(void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (alloc_fault_injected()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) g_live_device_allocs++;
+    return e;
+}
+
+cudaError_t dev_malloc_async_raw(void **p, size_t bytes, cudaStream_t st)
+{
+    *p = nullptr;
+    if (alloc_fault_injected()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e == cudaSuccess) g_live_device_allocs++;
+    return e;
+}
+
+cudaError_t dev_free(void *p)
+{
+    if (!p) return cudaSuccess;
+    g_live_device_allocs--;
+    return cudaFree(p);
+}
+
+cudaError_t dev_free_async(void *p, cudaStream_t st)
+{
+    if (!p) return cudaSuccess;
+    g_live_device_allocs--;
+    return cudaFreeAsync(p, st);
+}
+
+long long live_device_allocations() { return g_live_device_allocs.load(); }
+void set_fail_countdown(int n) { g_fail_countdown.store(n > 0 ? n : 0); }
 
 // ------------------------------------------------------------- profiler
 namespace {
@@ -161,22 +211,22 @@ void free_plan(dgfs_plan_s *plan)
     prof_free(plan);
     tc_release(plan);
     for (auto &pt : plan->pairs) {
-        cudaFree(pt.b);
-        cudaFree(pt.c);
-        cudaFree(pt.c_om);
-        cudaFree(pt.phase);
-        cudaFree(pt.w);
-        cudaFree(pt.wlog);
-        cudaFree(pt.b32);
-        cudaFree(pt.cdf);
-        cudaFree(pt.tmat);
+        dev_free(pt.b);
+        dev_free(pt.c);
+        dev_free(pt.c_om);
+        dev_free(pt.phase);
+        dev_free(pt.w);
+        dev_free(pt.wlog);
+        dev_free(pt.b32);
+        dev_free(pt.cdf);
+        dev_free(pt.tmat);
     }
-    cudaFree(plan->twiddle);
-    cudaFree(plan->quad_dev);
-    cudaFree(plan->masses_dev);
-    cudaFree(plan->ws);
-    cudaFree(plan->stage_f);
-    cudaFree(plan->stage_Q);
+    dev_free(plan->twiddle);
+    dev_free(plan->quad_dev);
+    dev_free(plan->masses_dev);
+    dev_free(plan->ws);
+    dev_free(plan->stage_f);
+    dev_free(plan->stage_Q);
     delete plan;
 }
 
@@ -218,6 +268,10 @@ using namespace dgfs;
 extern "C" {
 
 const char *dgfs_version(void) { return "dgfs-gb300 0.1 (sm_103a)"; }
+
+void dgfs_debug_fail_alloc(int n) { set_fail_countdown(n); }
+
+long long dgfs_debug_live_allocations(void) { return live_device_allocations(); }
 
 const char *dgfs_status_string(dgfs_status s)
 {
@@ -277,8 +331,11 @@ dgfs_status dgfs_plan_create(dgfs_plan *out, int N, double L, int M, int N_rho, 
     }
     DGFS_CUDA(cudaSetDevice(device));
 
-    dgfs_plan_s *plan = new (std::nothrow) dgfs_plan_s();
-    if (!plan) return DGFS_ENOMEM;
+    dgfs_plan_s *plan = host_new<dgfs_plan_s>();
+    if (!plan) {
+        set_error("dgfs_plan_create: out of host memory");
+        return DGFS_ENOMEM;
+    }
     plan->N = N;
     plan->L = L;
     plan->M = M;
@@ -322,7 +379,7 @@ dgfs_status dgfs_plan_create(dgfs_plan *out, int N, double L, int M, int N_rho, 
 
     dgfs_status st = build_tables(plan);
     if (st == DGFS_OK) {
-        cudaError_t e = cudaMalloc(&plan->masses_dev, sizeof(double) * S);
+        cudaError_t e = dev_malloc(&plan->masses_dev, sizeof(double) * S);
         if (e == cudaSuccess) e = cudaMemcpy(plan->masses_dev, masses, sizeof(double) * S, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) st = cuda_status(e, "masses");
     }
@@ -338,14 +395,14 @@ dgfs_status dgfs_plan_create(dgfs_plan *out, int N, double L, int M, int N_rho, 
         } else {
             plan->ws_bytes = tc_workspace_bytes(plan);
         }
-        cudaError_t e = cudaMalloc(&plan->ws, plan->ws_bytes);
+        cudaError_t e = dev_malloc(&plan->ws, plan->ws_bytes);
         if (e != cudaSuccess) st = cuda_status(e, "workspace");
     }
     if (st == DGFS_OK) {
         const long n = (long)N * N * N;
         const size_t es = elem_size(plan);
-        cudaError_t e = cudaMalloc(&plan->stage_f, es * (size_t)max_points * S * n);
-        if (e == cudaSuccess) e = cudaMalloc(&plan->stage_Q, es * (size_t)max_points * S * S * n);
+        cudaError_t e = dev_malloc(&plan->stage_f, es * (size_t)max_points * S * n);
+        if (e == cudaSuccess) e = dev_malloc(&plan->stage_Q, es * (size_t)max_points * S * S * n);
         if (e != cudaSuccess) st = cuda_status(e, "staging buffers");
     }
     if (st == DGFS_OK) {

@@ -312,11 +312,11 @@ dgfs_status dg_stage(dgfs_dg_s *dg, const void *f_in, const void *f0, void *out,
 void dg_free(dgfs_dg_s *dg)
 {
     if (!dg) return;
-    cudaFree(dg->Mw);
-    cudaFree(dg->wsum);
-    cudaFree(dg->f1);
-    cudaFree(dg->f2);
-    cudaFree(dg->Q);
+    dev_free(dg->Mw);
+    dev_free(dg->wsum);
+    dev_free(dg->f1);
+    dev_free(dg->f2);
+    dev_free(dg->Q);
     delete dg;
 }
 
@@ -383,13 +383,13 @@ dgfs_status dg_build(dgfs_dg_s *dg)
         }
     }
     DGFS_CUDA(cudaSetDevice(plan->device));
-    DGFS_CUDA(cudaMalloc(&dg->Mw, sizeof(double) * Mw.size()));
+    DGFS_CUDA(dev_malloc(&dg->Mw, sizeof(double) * Mw.size()));
     DGFS_CUDA(cudaMemcpy(dg->Mw, Mw.data(), sizeof(double) * Mw.size(), cudaMemcpyHostToDevice));
-    DGFS_CUDA(cudaMalloc(&dg->wsum, sizeof(double) * 2 * S * kWallChunks));
+    DGFS_CUDA(dev_malloc(&dg->wsum, sizeof(double) * 2 * S * kWallChunks));
     const size_t es = elem_size(plan);
-    DGFS_CUDA(cudaMalloc(&dg->f1, es * dg->P * S * n));
-    DGFS_CUDA(cudaMalloc(&dg->f2, es * dg->P * S * n));
-    DGFS_CUDA(cudaMalloc(&dg->Q, es * dg->P * S * S * n));
+    DGFS_CUDA(dev_malloc(&dg->f1, es * dg->P * S * n));
+    DGFS_CUDA(dev_malloc(&dg->f2, es * dg->P * S * n));
+    DGFS_CUDA(dev_malloc(&dg->Q, es * dg->P * S * S * n));
     return DGFS_OK;
 }
 
@@ -416,8 +416,11 @@ dgfs_status dgfs_dg_create(dgfs_dg *out, dgfs_plan plan, int Ne, int K, double x
             return DGFS_EINVAL;
         }
     }
-    dgfs_dg_s *dg = new (std::nothrow) dgfs_dg_s;
-    if (!dg) return DGFS_ENOMEM;
+    dgfs_dg_s *dg = host_new<dgfs_dg_s>();
+    if (!dg) {
+        set_error("dgfs_dg_create: out of host memory");
+        return DGFS_ENOMEM;
+    }
     dg->plan = plan;
     dg->Ne = Ne;
     dg->K = K;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -94,6 +95,26 @@ dgfs_status cuda_status(cudaError_t e, const char *what);
     } while (0)
 
 size_t elem_size(const dgfs_plan_s *plan);
+
+// Allocations of the library (capi.cu).  Device memory goes through
+// dev_malloc / dev_free (and the stream-ordered pair), which count the live
+// allocations; the library's host objects through host_new.  Both honour the
+// host-side allocation-failure hook (dgfs_debug_fail_alloc): the allocation
+// it selects reports failure without allocating.
+bool alloc_fault_injected();
+cudaError_t dev_malloc_raw(void **p, size_t bytes);
+cudaError_t dev_malloc_async_raw(void **p, size_t bytes, cudaStream_t st);
+cudaError_t dev_free(void *p);
+cudaError_t dev_free_async(void *p, cudaStream_t st);
+template <typename T> inline cudaError_t dev_malloc(T **p, size_t bytes)
+{
+    return dev_malloc_raw(reinterpret_cast<void **>(p), bytes);
+}
+template <typename T> inline cudaError_t dev_malloc_async(T **p, size_t bytes, cudaStream_t st)
+{
+    return dev_malloc_async_raw(reinterpret_cast<void **>(p), bytes, st);
+}
+template <typename T> inline T *host_new() { return alloc_fault_injected() ? nullptr : new (std::nothrow) T(); }
 
 // Brackets one kernel launch with CUDA events on its stream when the plan's
 // profiler is on (dgfs_plan_profile); no-op otherwise.

@@ -225,12 +225,12 @@ dgfs_status df_tables(dgfs_plan_s *plan, float4 **tw_out)
 {
     const long n = (long)plan->N * plan->N * plan->N;
     for (auto &pt : plan->pairs) {
-        DGFS_CUDA(cudaMalloc(&pt.cdf, sizeof(float4) * n));
+        DGFS_CUDA(dev_malloc(&pt.cdf, sizeof(float4) * n));
         plan->table_bytes += sizeof(float4) * n;
         k_to_df<<<(unsigned)((n + 255) / 256), 256>>>(pt.cdf, pt.c, n);
         DGFS_LAUNCHED(plan);
     }
-    DGFS_CUDA(cudaMalloc(tw_out, sizeof(float4) * plan->N));
+    DGFS_CUDA(dev_malloc(tw_out, sizeof(float4) * plan->N));
     k_to_df<<<1, 64>>>(*tw_out, plan->twiddle, plan->N);
     DGFS_LAUNCHED(plan);
     return DGFS_OK;

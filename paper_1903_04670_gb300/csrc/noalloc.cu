@@ -14,7 +14,13 @@
 // loads this library holds its kNoAllocScratchBytes until the process exits.
 // Host code cannot use the array's name as a device address, so the device
 // address is looked up with cudaGetSymbolAddress once per device, with that
-// device current, on the first call made on that device.
+// device current, on the first call made on that device.  The address belongs
+// to the device's context: after cudaDeviceReset the library's module is
+// loaded again in a new context and the array may sit elsewhere, so the
+// cached address is keyed on the context's unique id and looked up again when
+// the current context is a different one.
+#include <cuda.h>  // driver types only; the entry points are resolved through the runtime
+
 #include <cstdio>
 #include <mutex>
 
@@ -30,6 +36,36 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 std::mutex g_setup_mutex;
 void *g_scratch_addr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};  // context id the address belongs to
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current context (never reused within a
+// process), or 0 when the driver cannot report it.  Caller holds the mutex.
+unsigned long long current_context_id()
+{
+    static bool resolved = false;
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!resolved) {
+        resolved = true;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", reinterpret_cast<void **>(&get_current), 12000,
+                                             cudaEnableDefault, &q1) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess)
+            get_current = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", reinterpret_cast<void **>(&get_id), 12000,
+                                             cudaEnableDefault, &q2) != cudaSuccess ||
+            q2 != cudaDriverEntryPointSuccess)
+            get_id = nullptr;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS)
+        return id;
+    return 0;
+}
 
 // Device address of the scratch array on `device` (which must be current).
 dgfs_status scratch_address(int device, void **out)
@@ -39,11 +75,13 @@ dgfs_status scratch_address(int device, void **out)
         return DGFS_EINVAL;
     }
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[device]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_addr[device] || ctx == 0 || ctx != g_scratch_ctx[device]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return cuda_status(e, "cudaGetSymbolAddress(noalloc scratch)");
         g_scratch_addr[device] = p;
+        g_scratch_ctx[device] = ctx;
     }
     *out = g_scratch_addr[device];
     return DGFS_OK;

@@ -178,19 +178,31 @@ unsigned blocks_for(long total, int threads) { return (unsigned)((total + thread
 
 }  // namespace
 
+dgfs_status build_pair_tables(dgfs_plan_s *plan, int *d_over);
+
 dgfs_status build_tables(dgfs_plan_s *plan)
 {
-    const int N = plan->N, M = plan->M, Nrho = plan->Nrho, RS = Nrho * M;
-    const long n = (long)N * N * N;
-    DGFS_CUDA(cudaMalloc(&plan->twiddle, sizeof(double2) * N));
+    const int N = plan->N;
+    DGFS_CUDA(dev_malloc(&plan->twiddle, sizeof(double2) * N));
     k_twiddle<<<1, 64>>>(plan->twiddle, N);
     DGFS_LAUNCHED(plan);
 
     int *d_over = nullptr;
-    DGFS_CUDA(cudaMalloc(&d_over, sizeof(int)));
+    DGFS_CUDA(dev_malloc(&d_over, sizeof(int)));
+    const dgfs_status st = build_pair_tables(plan, d_over);
+    dev_free(d_over);
+    return st;
+}
+
+// b, c, c_omega, phases and weights of every pair; d_over receives the
+// overflow flag of the angular-integral kernels
+dgfs_status build_pair_tables(dgfs_plan_s *plan, int *d_over)
+{
+    const int N = plan->N, M = plan->M, Nrho = plan->Nrho, RS = Nrho * M;
+    const long n = (long)N * N * N;
     DGFS_CUDA(cudaMemset(d_over, 0, sizeof(int)));
     const size_t qn = 2 * Nrho + 4 * M;
-    DGFS_CUDA(cudaMalloc(&plan->quad_dev, sizeof(double) * qn));
+    DGFS_CUDA(dev_malloc(&plan->quad_dev, sizeof(double) * qn));
     std::vector<double> quad(qn);
     for (auto &pt : plan->pairs) {
         for (int r = 0; r < Nrho; ++r) {
@@ -200,12 +212,12 @@ dgfs_status build_tables(dgfs_plan_s *plan)
         for (int i = 0; i < 3 * M; ++i) quad[2 * Nrho + i] = plan->sigma[i];
         for (int s = 0; s < M; ++s) quad[2 * Nrho + 3 * M + s] = plan->wsig[s];
         DGFS_CUDA(cudaMemcpy(plan->quad_dev, quad.data(), sizeof(double) * qn, cudaMemcpyHostToDevice));
-        DGFS_CUDA(cudaMalloc(&pt.b, sizeof(double2) * RS * n));
-        DGFS_CUDA(cudaMalloc(&pt.c, sizeof(double2) * n));
-        DGFS_CUDA(cudaMalloc(&pt.c_om, sizeof(double2) * n));
-        DGFS_CUDA(cudaMalloc(&pt.phase, sizeof(double2) * RS * 6 * N));
-        DGFS_CUDA(cudaMalloc(&pt.w, sizeof(double) * RS));
-        DGFS_CUDA(cudaMalloc(&pt.wlog, sizeof(double) * RS));
+        DGFS_CUDA(dev_malloc(&pt.b, sizeof(double2) * RS * n));
+        DGFS_CUDA(dev_malloc(&pt.c, sizeof(double2) * n));
+        DGFS_CUDA(dev_malloc(&pt.c_om, sizeof(double2) * n));
+        DGFS_CUDA(dev_malloc(&pt.phase, sizeof(double2) * RS * 6 * N));
+        DGFS_CUDA(dev_malloc(&pt.w, sizeof(double) * RS));
+        DGFS_CUDA(dev_malloc(&pt.wlog, sizeof(double) * RS));
         plan->table_bytes += sizeof(double2) * (RS * n + 2 * n + RS * 6 * N) + 2 * sizeof(double) * RS;
 
         k_phase<<<blocks_for((long)RS * 6 * N, 256), 256>>>(pt.phase, plan->quad_dev, N, M, Nrho, plan->L,
@@ -224,7 +236,6 @@ dgfs_status build_tables(dgfs_plan_s *plan)
     }
     int over = 0;
     DGFS_CUDA(cudaMemcpy(&over, d_over, sizeof(int), cudaMemcpyDeviceToHost));
-    cudaFree(d_over);
     if (over) {
         set_error("angular integral needs more Funk-Hecke terms than the table kernel holds");
         return DGFS_EUNSUPPORTED;

@@ -1585,15 +1585,15 @@ dgfs_status build_images(dgfs_plan_s *plan, TcState *ts)
     const long n = (long)N * N * N;
     const long IC = tcfmt::img_c<FMT>(N);
     constexpr int NT = Fmt<FMT>::NT;
-    DGFS_CUDA(cudaMalloc(&ts->Fimg, NT * IC));
+    DGFS_CUDA(dev_malloc(&ts->Fimg, NT * IC));
     DGFS_CUDA(cudaMemset(ts->Fimg, 0, NT * IC));
     k_fimg<FMT><<<nblk((long)N * N, 256), 256>>>(ts->Fimg, N);
     DGFS_LAUNCHED(plan);
     for (auto &pt : plan->pairs) {
         const size_t tbytes = (size_t)RS * 2 * 3 * NT * IC;
-        DGFS_CUDA(cudaMalloc(&pt.tmat, tbytes));
+        DGFS_CUDA(dev_malloc(&pt.tmat, tbytes));
         DGFS_CUDA(cudaMemset(pt.tmat, 0, tbytes));
-        DGFS_CUDA(cudaMalloc(&pt.b32, sizeof(float2) * RS * n));
+        DGFS_CUDA(dev_malloc(&pt.b32, sizeof(float2) * RS * n));
         plan->table_bytes += tbytes + sizeof(float2) * RS * n;
         k_timg<FMT><<<nblk((long)RS * 6 * N * N, 256), 256>>>(reinterpret_cast<uint8_t *>(pt.tmat), pt.phase, N, RS);
         DGFS_LAUNCHED(plan);
@@ -1629,7 +1629,11 @@ dgfs_status tc_prepare(dgfs_plan_s *plan)
         set_error("tensor-core plans support N in {8, 16, 24, 32, 48}");
         return DGFS_EUNSUPPORTED;
     }
-    TcState *ts = new TcState();
+    TcState *ts = host_new<TcState>();
+    if (!ts) {
+        set_error("tc_prepare: out of host memory");
+        return DGFS_ENOMEM;
+    }
     plan->tc = ts;
     ts->fmt = plan->prec == DGFS_BF16X3 ? 1 : 0;
     ts->nterms = plan->prec == DGFS_TF32 ? 1 : (plan->prec == DGFS_BF16X3 ? 6 : 3);
@@ -1643,7 +1647,7 @@ dgfs_status tc_prepare(dgfs_plan_s *plan)
     // about 8 waves of CTAs per stage (the autotuner's usual choice at N = 32)
     ts->groups_a = std::max(1, (8 * sms + RS) / (2 * RS));
     ts->groups_b = std::max(1, (8 * sms + RS / 2) / RS);
-    DGFS_CUDA(cudaMalloc(&ts->err, sizeof(int)));
+    DGFS_CUDA(dev_malloc(&ts->err, sizeof(int)));
     DGFS_CUDA(cudaMemset(ts->err, 0, sizeof(int)));
     DGFS_CUDA(cudaStreamCreateWithFlags(&ts->side, cudaStreamNonBlocking));
     DGFS_CUDA(cudaEventCreateWithFlags(&ts->ev_entry, cudaEventDisableTiming));
@@ -1657,7 +1661,7 @@ dgfs_status tc_prepare(dgfs_plan_s *plan)
             const double *sg = plan->sigma + 3 * (rs % plan->M);
             mask[rs] = (uint8_t)((sg[0] == 0.0 ? 1 : 0) | (sg[1] == 0.0 ? 2 : 0) | (sg[2] == 0.0 ? 4 : 0));
         }
-        DGFS_CUDA(cudaMalloc(&ts->idmask, RS));
+        DGFS_CUDA(dev_malloc(&ts->idmask, RS));
         DGFS_CUDA(cudaMemcpy(ts->idmask, mask.data(), RS, cudaMemcpyHostToDevice));
     }
     dgfs_status st = ts->fmt == 0 ? build_images<0>(plan, ts) : build_images<1>(plan, ts);
@@ -1670,10 +1674,10 @@ void tc_release(dgfs_plan_s *plan)
 {
     TcState *ts = reinterpret_cast<TcState *>(plan->tc);
     if (!ts) return;
-    cudaFree(ts->Fimg);
-    cudaFree(ts->err);
-    cudaFree(ts->idmask);
-    cudaFree(ts->tw_df);
+    dev_free(ts->Fimg);
+    dev_free(ts->err);
+    dev_free(ts->idmask);
+    dev_free(ts->tw_df);
     if (ts->side) cudaStreamDestroy(ts->side);
     if (ts->ev_entry) cudaEventDestroy(ts->ev_entry);
     if (ts->ev_a) cudaEventDestroy(ts->ev_a);
@@ -1722,8 +1726,11 @@ void tc_batch_free(void *handle)
 dgfs_status tc_batch_build(int count, dgfs_plan_s *const *plans, const int *P, void *const *f, void *const *Q,
                            void **out)
 {
-    TcBatch *b = new (std::nothrow) TcBatch;
-    if (!b) return DGFS_ENOMEM;
+    TcBatch *b = host_new<TcBatch>();
+    if (!b) {
+        set_error("dgfs_batch_create: out of host memory");
+        return DGFS_ENOMEM;
+    }
     for (int i = 0; i < count; ++i) {
         dgfs_plan_s *plan = plans[i];
         const TcState *ts = reinterpret_cast<const TcState *>(plan->tc);

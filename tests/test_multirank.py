@@ -145,3 +145,57 @@ def test_element_range_keeps_elements_whole():
             spans = [D.element_range(Ne, r, world) for r in range(world)]
             assert spans[0][0] == 0 and spans[-1][1] == Ne
             assert all(b == c for (_, b), (c, _) in zip(spans, spans[1:]))
+
+
+def _failing_worker(rank, world, port, out_path):
+    """Rank 1 raises between two decomposed DG steps (none of its work in
+    flight); rank 0 goes on to its next step and must get an error from the
+    trace exchange within the process group's short timeout instead of
+    waiting forever."""
+    import datetime
+    import time
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    from oracle import dg as ODG
+
+    Ne, K = SLAB["Ne"], SLAB["K"]
+    e0, e1 = D.element_range(Ne, rank, world)
+    he = 1.0 / Ne
+    ref = ODG.Slab(e1 - e0, K, e0 * he, e1 * he, SLAB["N"], SLAB["L"], SLAB["masses"], WALLS)
+    f = torch.from_numpy(_slab_f()[e0 * K:e1 * K].copy())
+    D.dg_step_decomposed(_OracleBlock(ref), f, 0.004, with_collisions=False, rank=rank, world=world)
+    if rank == 1:
+        raise RuntimeError("injected failure of rank 1 between steps")
+    t0 = time.monotonic()
+    try:
+        D.dg_step_decomposed(_OracleBlock(ref), f, 0.004, with_collisions=False, rank=rank, world=world)
+        res = {"error": None}
+    except Exception as e:  # the exchange with the dead neighbour fails
+        res = {"error": type(e).__name__ + ": " + str(e)[:200]}
+    res["seconds"] = time.monotonic() - t0
+    torch.save(res, out_path)
+
+
+def test_rank_failure_between_steps_surfaces_as_an_error(tmp_path):
+    import multiprocessing
+
+    out = str(tmp_path / "fail.pt")
+    port = _free_port()
+    ctx = multiprocessing.get_context("spawn")
+    procs = [ctx.Process(target=_failing_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(60)
+    alive = [p.is_alive() for p in procs]
+    for p in procs:
+        if p.is_alive():
+            p.kill()
+    assert not any(alive), "a rank hung after its neighbour failed"
+    assert procs[1].exitcode != 0  # the failing rank
+    assert procs[0].exitcode == 0
+    res = torch.load(out)
+    assert res["error"] is not None, "rank 0 completed a step with a dead neighbour"
+    assert res["seconds"] < 30.0, res

@@ -58,3 +58,32 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
         B.dgfs_collide_noalloc(plan._h, 1, f, Q)
     assert e.value.status == 1
     assert "scratch" in str(e.value)
+
+
+def test_noalloc_splits_points_over_passes():
+    # N = 16, M = 6, N_rho = 8, S = 2, P = 8: the 32 MiB scratch holds five
+    # evaluations per pass next to the forward transforms of all eight points,
+    # so the points run in passes of 5 and 3 (the size loop's ragged last pass)
+    pb = W.make_problem("c1_homog_n16", points=8)
+    plan = B.Plan(pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"], "fp64", 8)
+    f = torch.from_numpy(pb["f"]).to("cuda", torch.float64)
+    ref = plan.collide(f)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        Q = torch.full_like(ref, float("nan"))
+        B.dgfs_collide_noalloc(plan._h, 8, f, Q)
+        torch.cuda.synchronize()
+        assert _rel(Q.cpu().numpy(), ref.cpu().numpy()) <= TOL64
+
+
+def test_noalloc_rejects_points_beyond_its_scratch():
+    # at N = 16, M = 6, N_rho = 8, S = 2 one evaluation per pass fits up to
+    # P = 207 (16 B x 4096 x (2 P + 98) <= 32 MiB); P = 208 is refused
+    pb = W.make_problem("c1_homog_n16")
+    plan = B.Plan(pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"], "fp64", 1)
+    f = torch.zeros((208, 2, 16, 16, 16), dtype=torch.float64, device="cuda")
+    Q = torch.zeros((208, 2, 2, 16, 16, 16), dtype=torch.float64, device="cuda")
+    with pytest.raises(B.DgfsError) as e:
+        B.dgfs_collide_noalloc(plan._h, 208, f, Q)
+    assert e.value.status == 1
+    assert "scratch" in str(e.value)
