@@ -9,8 +9,13 @@ inputs resident in HBM, L2 flushed (256 MiB write) before every timed step.
 Prints ONE JSON line (rank 0).  Fields beyond the base contract:
   forms        evals/s and relative max-norm error vs the FP64 CPU oracle for
                every precision form measured (tensor-core FP32 vs FP64),
-  roofline     the dominant kernel: algorithmic work per launch / its average
-               CUDA-event duration inside the timed region,
+  roofline     the dominant kernel: algorithmic FLOPs per launch (5 N^3 log2 N per
+               length-N axis pass of a 3-D transform, plus the elementwise work
+               the method performs) / its average CUDA-event duration, against the
+               tensor-core rate measured on this GPU by the library's own probe;
+               beside it the executed dense-MMA FLOPs (the DFT contractions as
+               GEMMs, all split products) under "executed_mma", and the whole
+               step's algorithmic rate,
   cpu_baseline the FP64 oracle timed on this host's cores on a bounded sample,
   e2e          the same metric through the host-buffer C-ABI call,
   clocks       nvidia-smi samples taken during the timed region,
@@ -227,14 +232,24 @@ def run_ours(args, rank, world):
                       "launch_parameters": "dgfs_plan_autotune before timing" if not args.no_tune else "defaults",
                       "parallelism": "replicas: every rank evaluates its own 96 (point, pair) operators"}}
 
+    peaks, src = _peaks()
     if not args.no_peaks:
         out["alu_peaks"] = alu_peaks(torch)
+        # the tensor-core denominators, measured here by the library's probe
+        try:
+            out["tensor_peaks"] = {"tf32": B.dgfs_probe_mma_rate(dev, "tf32", 4096),
+                                   "bf16": B.dgfs_probe_mma_rate(dev, "bf16", 4096), "unit": "TFLOP/s",
+                                   "how": "one CTA per SM issues 4096 back-to-back tcgen05 MMAs (M = 128, "
+                                          "N = 256) into TMEM; best of three timed launches",
+                                   "measured_peaks_json": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops",
+                                                                                     "bf16_tflops_sustained")}}
+        except B.DgfsError as e:
+            out["tensor_peaks"] = {"error": str(e)}
 
     # roofline of the dominant kernel (by summed event time)
     prof = rec["profile"]
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     name, (cnt, tot_ms) = dom
-    peaks, src = _peaks()
     work = kernel_work(name, info, P, S, RS)
     avg_s = tot_ms / cnt / 1e3
     if name.startswith("fp64"):
@@ -248,7 +263,17 @@ def run_ours(args, rank, world):
                 "unit": "GFLOP/s", "peak_source": psrc}
     else:
         sigma = plan.pair_tables(0, 0, with_b=False)["sigma"]
-        roof = tc_roofline(name, info, P, S, RS, avg_s, peaks, src, cnt / rec["profile_steps"], sigma)
+        kind = "bf16" if main == "bf16x3" else "tf32"
+        probe = out.get("tensor_peaks", {}).get(kind)
+        if probe:
+            peak, psrc = probe, ("tcgen05 kind::%s M = 128, N = 256 back-to-back issue rate on all SMs, measured "
+                                 "in this run (dgfs_probe_mma_rate)" % ("tf32" if kind == "tf32" else "f16 (bf16)"))
+        else:
+            bf16 = peaks["bf16_tflops"]
+            peak = bf16 * ((1.1 / 2.25) if kind == "tf32" else 1.0)
+            psrc = "%s bf16 GEMM (%.1f TFLOP/s)%s" % (src, bf16, " x nominal tf32/bf16 1.1/2.25" if kind == "tf32"
+                                                      else "")
+        roof = tc_roofline(name, info, P, S, RS, avg_s, peak, psrc, cnt / rec["profile_steps"], sigma)
     roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("achieved") else None
     roof["kernel"] = name
     roof["launches"] = cnt
@@ -256,7 +281,27 @@ def run_ours(args, rank, world):
     roof["share_of_step"] = tot_ms / sum(v[1] for v in prof.values())
     roof["timing"] = ("CUDA events around each launch in a %d-step pass right after the timed region "
                       "(the library then issues the plan's launches in one stream)" % rec["profile_steps"])
-    roof["traffic"] = ncu_traffic(name, P)
+    roof["traffic"], roof["traffic_source"] = ncu_traffic(name, P)
+    # DRAM traffic of the three stage kernels per step against the step's
+    # algorithmic bytes (f in, Q out, the b tables once): the cost of the
+    # per-(r, s) intermediates that pass through HBM
+    if not name.startswith("fp64"):
+        tsum = 0.0
+        for k in NCU_TRAFFIC_8PT:
+            t, _ = ncu_traffic(k, P)
+            if t is None or k not in prof:
+                tsum = None
+                break
+            tsum += t * prof[k][0] / rec["profile_steps"]
+        if tsum:
+            ab = step_algorithmic_bytes(int(info["N"]), P, S, RS)
+            roof["step_traffic"] = {"stage_kernels_bytes": tsum, "algorithmic_bytes": ab, "ratio": tsum / ab}
+    # the whole step on the same peak: every kernel of the call, algorithmic FLOPs
+    if not name.startswith("fp64"):
+        sf = step_algorithmic_flops(int(info["N"]), P, S, RS)
+        roof["step"] = {"achieved": sf / (rec["ms_per_step"] / 1e3) / 1e12, "unit": "TFLOP/s",
+                        "frac": sf / (rec["ms_per_step"] / 1e3) / 1e12 / roof["peak"],
+                        "work_per_step": sf, "work_unit": "algorithmic FLOPs of all evaluations of the step"}
     out["roofline"] = roof
     out["kernels"] = {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in prof.items()}
     out["kernels_steps"] = rec["profile_steps"]
@@ -446,6 +491,8 @@ def uneven_batch(B, W, torch, np, prec, dev, flush, stream, plan, rec, count=256
     the work list's own device cost on the benchmark call (one instance)."""
     _, plans, fs, Qs = uneven_plans(B, W, torch, np, prec, dev, count)
     evals = sum(f.shape[0] * pl.S * pl.S for pl, f in zip(plans, fs))
+    # algorithmic FLOPs of one pass (each problem at its own N, S, M, N_rho)
+    aflops = sum(step_algorithmic_flops(pl.N, f.shape[0], pl.S, pl.M * pl.N_rho) for pl, f in zip(plans, fs))
     dt = 1e-3
 
     def timed(fn, reps=reps):
@@ -478,18 +525,20 @@ def uneven_batch(B, W, torch, np, prec, dev, flush, stream, plan, rec, count=256
                        "per pass" % count,
            "instances": count, "plans": len(plans), "evals_per_pass": evals, "precision": prec}
     t = timed(separate)
-    res["separate_calls"] = {"ms_per_pass": t, "evals_per_s": evals / (t / 1e3), "launches": launches(separate)}
+    res["algorithmic_flops_per_pass"] = aflops
+    res["separate_calls"] = {"ms_per_pass": t, "evals_per_s": evals / (t / 1e3),
+                             "alg_tflops": aflops / (t / 1e3) / 1e12, "launches": launches(separate)}
     g = B.dgfs_graph_capture([pl._h for pl in plans], [f.shape[0] for f in fs], fs, Qs, dt=dt)
     try:
         t = timed(lambda: B.dgfs_graph_launch(g, stream))
         res["graph_of_calls"] = {"ms_per_pass": t, "evals_per_s": evals / (t / 1e3),
-                                 "launches": B.dgfs_graph_kernel_count(g)}
+                                 "alg_tflops": aflops / (t / 1e3) / 1e12, "launches": B.dgfs_graph_kernel_count(g)}
     finally:
         B.dgfs_graph_destroy(g)
     bt = B.Batch(plans, fs, Qs, dt)
     try:
         t = timed(lambda: bt.launch(stream))
-        res["batch"] = {"ms_per_pass": t, "evals_per_s": evals / (t / 1e3),
+        res["batch"] = {"ms_per_pass": t, "evals_per_s": evals / (t / 1e3), "alg_tflops": aflops / (t / 1e3) / 1e12,
                         "launches": launches(lambda: bt.launch(stream))}
         cg = torch.cuda.CUDAGraph()
         cs = torch.cuda.Stream()
@@ -497,7 +546,8 @@ def uneven_batch(B, W, torch, np, prec, dev, flush, stream, plan, rec, count=256
         with torch.cuda.graph(cg, stream=cs):
             bt.launch(cs)
         t = timed(cg.replay)
-        res["batch_graph"] = {"ms_per_pass": t, "evals_per_s": evals / (t / 1e3)}
+        res["batch_graph"] = {"ms_per_pass": t, "evals_per_s": evals / (t / 1e3),
+                              "alg_tflops": aflops / (t / 1e3) / 1e12}
         del cg
     finally:
         bt.close()
@@ -553,20 +603,65 @@ NCU_TRAFFIC_8PT = {"tc_stage_a": 351.4e6, "tc_stage_b": 574.7e6, "tc_stage_c": 2
 
 
 def ncu_traffic(name, P):
+    """(bytes per launch, where the figure comes from), or (None, reason)."""
     if WORKLOAD != "c2_slab_n32" or name not in NCU_TRAFFIC_8PT:
-        return None
-    return NCU_TRAFFIC_8PT[name] * min(P, 24) / 8.0
+        return None, "no ncu capture of this kernel"
+    return (NCU_TRAFFIC_8PT[name] * min(P, 24) / 8.0,
+            "not measured in this run: ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch captured "
+            "on 8 points, scaled by %d/8 points per launch (the per-(r, s) intermediates scale with the points)"
+            % min(P, 24))
 
 
-def tc_roofline(name, info, P, S, RS, avg_s, peaks, src, launches_per_step, sigma=None):
-    flops_step = tc_executed_flops(name, info, P, S, RS, sigma)
-    bf16 = peaks["bf16_tflops"]
-    tf32 = bf16 * (1.1 / 2.25)
-    ach = flops_step / launches_per_step / avg_s / 1e12 if flops_step else None
-    return {"bound": "tensor", "achieved": ach, "peak": tf32, "unit": "TFLOP/s",
-            "peak_source": "%s bf16 (%.1f TFLOP/s) x nominal dense tf32/bf16 ratio 1.1/2.25" % (src, bf16),
-            "work_per_launch": flops_step / launches_per_step if flops_step else None,
-            "work_unit": "executed MMA FLOPs (all split products; identity translates not issued)"}
+def step_algorithmic_bytes(N, P, S, RS, es=4):
+    """Algorithmic HBM bytes of one step: f_p and f_q in and Q out per evaluation
+    (es bytes per value) and each pair's b table (complex) read once."""
+    n = N ** 3
+    return S * S * P * 3.0 * n * es + S * S * RS * n * 2.0 * es
+
+
+def alg_axis_flops(N):
+    """One length-N pass of a 3-D transform over an N^3 grid: N^2 transforms of
+    5 N log2 N flops (the radix-2 count the paper's FFTs would take)."""
+    return 5.0 * N ** 3 * math.log2(N)
+
+
+def tc_algorithmic_flops(name, N, P, S, RS):
+    """Algorithmic FLOPs of one step's launches of a tensor-core stage kernel:
+    per (point, pair, r, s), stage A does the z and y passes of both translates
+    (4 axis passes), stage B the two x passes, the complex product and the
+    forward x pass (3 passes + 6 N^3), stage C the forward y and z passes and the
+    multiply-accumulate with w b (2 passes + 8 N^3); the 9 passes are the 3 x 3-D
+    transforms of the (r, s) step of Algorithm 2."""
+    a = alg_axis_flops(N)
+    per = {"tc_stage_a": 4 * a, "tc_stage_b": 3 * a + 6.0 * N ** 3, "tc_stage_c": 2 * a + 8.0 * N ** 3}.get(name)
+    return None if per is None else S * S * P * RS * per
+
+
+def step_algorithmic_flops(N, P, S, RS):
+    """The whole operator per step: (3 M N_rho + 2) 3-D transforms per evaluation,
+    S forward transforms per point, ~28 flops per grid point per (r, s)."""
+    t = 3 * alg_axis_flops(N)
+    return S * S * P * ((3 * RS + 2) * t + 28.0 * RS * N ** 3) + S * P * t
+
+
+def tc_roofline(name, info, P, S, RS, avg_s, peak, peak_src, launches_per_step, sigma=None):
+    N = int(info["N"])
+    alg = tc_algorithmic_flops(name, N, P, S, RS)
+    exe = tc_executed_flops(name, info, P, S, RS, sigma)
+    r = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak, "peak_source": peak_src,
+         "achieved": alg / launches_per_step / avg_s / 1e12 if alg else None,
+         "work_per_launch": alg / launches_per_step if alg else None,
+         "work_unit": "algorithmic FLOPs: 5 N^3 log2 N per axis pass of a 3-D transform plus the method's "
+                      "elementwise work (per (point, pair, r, s): stage A 4 passes, stage B 3 passes + 6 N^3, "
+                      "stage C 2 passes + 8 N^3)"}
+    if exe:
+        ach = exe / launches_per_step / avg_s / 1e12
+        r["executed_mma"] = {"achieved": ach, "frac": ach / peak, "work_per_launch": exe / launches_per_step,
+                             "unit": "TFLOP/s",
+                             "work_unit": "executed dense MMA FLOPs: every length-N pass as a 128 x 2N x K GEMM "
+                                          "(K = N real or 2N complex input), all split products, identity "
+                                          "translates not issued"}
+    return r
 
 
 # ------------------------------------------------------------ reference arm
