@@ -52,6 +52,8 @@ def lib():
             "orc_adjoint": (None, [p, p, p, p, p, p, p]),
             "orc_moments": (None, [i, d, d, p, p]),
             "orc_collide_batch": (None, [p, i, i, p, p]),
+            "orc_collide_hermitian": (None, [p, p, p, p]),
+            "orc_collide_hermitian_batch": (None, [p, i, i, p, p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -219,6 +221,16 @@ class Pair:
         dd = dict(zip(keys, diag.tolist()))
         return (Q, dd, dQ) if domega else (Q, dd)
 
+    def collide_hermitian(self, fp, fq):
+        """The declared Hermitian variant: Algorithm 2 with the Nyquist planes
+        removed from the inputs and from the gain (see dgfs_oracle.c)."""
+        N = self.N
+        fp = _f64(fp).reshape(N, N, N)
+        fq = _f64(fq).reshape(N, N, N)
+        Q = np.empty((N, N, N))
+        lib().orc_collide_hermitian(self._h, _ptr(fp), _ptr(fq), _ptr(Q))
+        return Q
+
     def adjoint(self, fp, fq, gbar, domega=True):
         N = self.N
         fp = _f64(fp).reshape(N, N, N)
@@ -250,6 +262,20 @@ class Problem:
 
     def pair(self, p, q):
         return self.pairs[p * self.S + q]
+
+    def collide_all_hermitian(self, f, points=None):
+        """Like collide_all, for the declared Hermitian variant."""
+        f = _f64(f)
+        P = f.shape[0]
+        N, S = self.N, self.S
+        f = f.reshape(P, S, N ** 3)
+        if points is not None:
+            f = np.ascontiguousarray(f[list(points)])
+            P = f.shape[0]
+        Q = np.empty((P, S, S, N ** 3))
+        arr = (ctypes.c_void_p * (S * S))(*[pr._h for pr in self.pairs])
+        lib().orc_collide_hermitian_batch(arr, S, P, _ptr(f), _ptr(Q))
+        return Q.reshape(P, S, S, N, N, N)
 
     def collide_all(self, f, points=None):
         """f: [P][S][N,N,N] -> Q: [P][S][S][N,N,N] (all pair operators)."""

@@ -26,6 +26,8 @@
  *   - The adjoint of the bilinear map (f_p, f_q) -> Q (derived from Eq. 7)
  *     and the derivative with respect to the VHS/VSS exponent omega.
  *   - Moments of Q (mass, momentum, energy) on the cell-centred grid.
+ *   - A declared variant that is not in the paper: Algorithm 2 with the
+ *     Nyquist planes removed (orc_collide_hermitian), for the real-data form.
  *
  * Readings where the paper is silent or inconsistent (each also listed in the
  * design notes of the repository):
@@ -658,6 +660,95 @@ void orc_collide(const orc_pair *P, const double *fp, const double *fq, double *
     free(QGw);
     free(t1);
     free(t2);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Declared variant (not in the paper): Algorithm 2 on the Hermitian          */
+/* subspace.  With N even, the wavenumber -N/2 has no +N/2 partner on the     */
+/* grid (Algorithm 1's wavenumber map), so a translate of a real f is not    */
+/* exactly real.  Let P zero every Fourier mode with an index equal to N/2   */
+/* (the Nyquist planes).  Then                                               */
+/*   F~ = P fft(f),  f~ = ifft(F~) (real),                                   */
+/*   QG = sum_rs w_r w_s b_rs . fft(ifft(e^{+i cq a} F~_p) . ifft(e^{-i cp a} F~_q)),  */
+/*   Q  = beta ( ifft(P QG) - f~_p . ifft(c . F~_q) ).                        */
+/* Every translate is real, and so are both terms of Q, because b_rs and c    */
+/* satisfy X(-k) = conj X(k) on the Nyquist-free wavenumbers; the real part  */
+/* taken at the end only drops rounding.                                     */
+/* ------------------------------------------------------------------------ */
+static int on_nyquist_plane(long idx, int N)
+{
+    int ix = (int)(idx / ((long)N * N)), iy = (int)((idx / N) % N), iz = (int)(idx % N);
+    return (N % 2 == 0) && (ix == N / 2 || iy == N / 2 || iz == N / 2);
+}
+
+void orc_collide_hermitian(const orc_pair *P, const double *fp, const double *fq, double *Q)
+{
+    int N = P->N;
+    long n = (long)N * N * N;
+    double cq = P->mq / (P->mp + P->mq), cp = P->mp / (P->mp + P->mq);
+    cplx *FTf = (cplx *)malloc(sizeof(cplx) * n);
+    cplx *FTg = (cplx *)malloc(sizeof(cplx) * n);
+    cplx *ft = (cplx *)malloc(sizeof(cplx) * n);
+    cplx *QG = (cplx *)calloc((size_t)n, sizeof(cplx));
+    cplx *t1 = (cplx *)malloc(sizeof(cplx) * n);
+    cplx *t2 = (cplx *)malloc(sizeof(cplx) * n);
+
+    /* F~_p, F~_q and f~_p */
+    for (long i = 0; i < n; ++i) {
+        FTf[i] = fp[i];
+        FTg[i] = fq[i];
+    }
+    fft3(N, FTf, -1);
+    fft3(N, FTg, -1);
+    for (long i = 0; i < n; ++i)
+        if (on_nyquist_plane(i, N)) FTf[i] = FTg[i] = 0;
+    for (long i = 0; i < n; ++i) ft[i] = FTf[i];
+    ifft3(N, ft);
+
+    /* the (rho, sigma) loop of Algorithm 2 on the projected spectra */
+    for (int r = 0; r < P->Nrho; ++r)
+        for (int s = 0; s < P->M; ++s) {
+            for (long i = 0; i < n; ++i) {
+                double a = phase_arg(P, r, s, i);
+                t1[i] = cexp(I * cq * a) * FTf[i];
+                t2[i] = cexp(-I * cp * a) * FTg[i];
+            }
+            ifft3(N, t1);
+            ifft3(N, t2);
+            for (long i = 0; i < n; ++i) t1[i] *= t2[i];
+            fft3(N, t1, -1);
+            const cplx *brs = P->b + ((long)r * P->M + s) * n;
+            double w = P->wrho[r] * P->wsig[s];
+            for (long i = 0; i < n; ++i) QG[i] += w * brs[i] * t1[i];
+        }
+
+    /* Q = beta ( ifft(P QG) - f~_p . ifft(c . F~_q) ) */
+    for (long i = 0; i < n; ++i)
+        if (on_nyquist_plane(i, N)) QG[i] = 0;
+    ifft3(N, QG);
+    for (long i = 0; i < n; ++i) t2[i] = P->c[i] * FTg[i];
+    ifft3(N, t2);
+    for (long i = 0; i < n; ++i) Q[i] = P->beta * creal(QG[i] - creal(ft[i]) * t2[i]);
+    free(FTf);
+    free(FTg);
+    free(ft);
+    free(QG);
+    free(t1);
+    free(t2);
+}
+
+/* Batched driver of the Hermitian variant, like orc_collide_batch. */
+void orc_collide_hermitian_batch(orc_pair **pairs, int S, int Pn, const double *f, double *Q)
+{
+    int N = pairs[0]->N;
+    long n = (long)N * N * N;
+    long total = (long)Pn * S * S;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long e = 0; e < total; ++e) {
+        long pt = e / (S * S);
+        int p = (int)((e / S) % S), q = (int)(e % S);
+        orc_collide_hermitian(pairs[p * S + q], f + (pt * S + p) * n, f + (pt * S + q) * n, Q + e * n);
+    }
 }
 
 /* ------------------------------------------------------------------------ */
