@@ -290,6 +290,27 @@ dgfs_status dgfs_plan_autotune(dgfs_plan plan, int P, const void *f_dev, void *Q
  * variant does not fit N). */
 dgfs_status dgfs_plan_set_kernel_variant(dgfs_plan plan, int variant);
 
+/* Declared variant (not the paper's literal Algorithm 2): the Hermitian form.
+ * Algorithm 1's wavenumber map gives index N/2 the wavenumber -N/2, which has
+ * no +N/2 partner, so a translate of a real f is not exactly real.  With
+ * enable != 0, dgfs_collide evaluates
+ *   F~ = P fft(f),  f~ = ifft(F~),
+ *   QG = sum_rs w_r w_s b_rs . fft( ifft(e^{+i m_q/mu a_rs} F~_p) . ifft(e^{-i m_p/mu a_rs} F~_q) ),
+ *   Q  = beta ( ifft(P QG) - f~_p . ifft(c . F~_q) ),
+ * P removing every Fourier mode with an index equal to N/2 (the Nyquist
+ * planes, of the inputs and of the gain).  Every translate is then real, so
+ * the library carries two spatial points in one complex grid (point 2e as
+ * the real part, 2e+1 as the imaginary part): the (r, s) work per evaluation
+ * halves.  Results differ from the literal form by the Nyquist content (small
+ * for resolved distributions).  Enabling allocates the form's workspace
+ * (about max_points/2 packed spectra, plus the tensor-core forms' z-pass
+ * images); disabling frees it.  dgfs_collide and dgfs_collide_host (and graphs
+ * captured from them) follow the setting; dgfs_collide_backward,
+ * dgfs_collide_noalloc, dgfs_collide_dealiased and dgfs_batch_create refuse a
+ * plan in this form (EUNSUPPORTED).  Errors: EINVAL, EUNSUPPORTED (odd N, or
+ * N = 48 on a tensor-core plan), ENOMEM, ECUDA. */
+dgfs_status dgfs_plan_set_hermitian(dgfs_plan plan, int enable);
+
 /* Number of the library's kernels launched since the plan was created
  * (host-side counter of launches enqueued by dgfs_* calls on this plan). */
 dgfs_status dgfs_plan_launch_count(dgfs_plan plan, long long *count);

@@ -71,6 +71,7 @@ def lib():
             "dgfs_plan_profile_read": (i, [_P, i, _P, _P, _P, ctypes.POINTER(i)]),
             "dgfs_plan_set_collapse": (i, [_P, i]),
             "dgfs_plan_set_kernel_variant": (i, [_P, i]),
+            "dgfs_plan_set_hermitian": (i, [_P, i]),
             "dgfs_dealias_work_bytes": (i, [_P, i, i, ctypes.POINTER(ctypes.c_size_t)]),
             "dgfs_collide_dealiased": (i, [_P, i, i, _P, _P, _P, ctypes.c_size_t, _P]),
             "dgfs_dg_create": (i, [ctypes.POINTER(_P), _P, i, i, d, d, _P]),
@@ -222,6 +223,10 @@ def dgfs_plan_pair_tables(h, p, q, N, M, N_rho, with_b=True):
 
 def dgfs_plan_set_collapse(h, enable):
     _check(lib().dgfs_plan_set_collapse(h, int(bool(enable))), "dgfs_plan_set_collapse")
+
+
+def dgfs_plan_set_hermitian(h, enable):
+    _check(lib().dgfs_plan_set_hermitian(h, int(bool(enable))), "dgfs_plan_set_hermitian")
 
 
 def dgfs_plan_set_kernel_variant(h, variant):
@@ -406,6 +411,10 @@ class Plan:
 
     def set_collapse(self, enable):
         dgfs_plan_set_collapse(self._h, enable)
+
+    def set_hermitian(self, enable):
+        """Switch the declared Hermitian form (Nyquist planes removed) on or off."""
+        dgfs_plan_set_hermitian(self._h, enable)
 
     def set_kernel_variant(self, variant):
         dgfs_plan_set_kernel_variant(self._h, variant)

@@ -168,6 +168,10 @@ dgfs_status dgfs_batch_create(int count, const dgfs_plan *plans, const int *P, v
                 set_error("dgfs_batch_create: a plan appears twice (each instance needs its own workspace)");
                 return DGFS_EINVAL;
             }
+        if (plans[i]->hermitian) {
+            set_error("dgfs_batch_create: the work list runs the literal operator (a plan is in the Hermitian form)");
+            return DGFS_EUNSUPPORTED;
+        }
     }
     dgfs_status st = plan_entry_check(plans[0]);
     if (st != DGFS_OK) return st;

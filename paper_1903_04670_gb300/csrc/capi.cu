@@ -227,6 +227,7 @@ void free_plan(dgfs_plan_s *plan)
     dev_free(plan->ws);
     dev_free(plan->stage_f);
     dev_free(plan->stage_Q);
+    dev_free(plan->herm_ws);
     delete plan;
 }
 
@@ -458,6 +459,49 @@ dgfs_status dgfs_plan_set_collapse(dgfs_plan plan, int enable)
     return DGFS_OK;
 }
 
+dgfs_status dgfs_plan_set_hermitian(dgfs_plan plan, int enable)
+{
+    if (!plan) return DGFS_EINVAL;
+    if (!enable) {
+        if (plan->herm_ws) {
+            DGFS_CUDA(cudaSetDevice(plan->device));
+            DGFS_CUDA(cudaDeviceSynchronize());
+            dev_free(plan->herm_ws);
+        }
+        plan->herm_ws = nullptr;
+        plan->herm_bytes = 0;
+        plan->hermitian = 0;
+        plan->config_gen++;
+        return DGFS_OK;
+    }
+    if (plan->N % 2 != 0 || (plan->prec != DGFS_FP64 && !tc_herm_supported(plan))) {
+        set_error("dgfs_plan_set_hermitian: needs even N, and N <= 32 for the tensor-core forms");
+        return DGFS_EUNSUPPORTED;
+    }
+    dgfs_status st = entry_check(plan);
+    if (st != DGFS_OK) return st;
+    if (!plan->herm_ws) {
+        const size_t bytes = plan->prec == DGFS_FP64 ? fp64_herm_bytes(plan) : tc_herm_bytes(plan);
+        void *p = nullptr;
+        cudaError_t e = dev_malloc(&p, bytes);
+        if (e != cudaSuccess) return cuda_status(e, "dgfs_plan_set_hermitian: workspace");
+        plan->herm_ws = p;
+        plan->herm_bytes = bytes;
+        if (plan->prec != DGFS_FP64) {
+            st = tc_herm_build(plan);
+            if (st != DGFS_OK) {
+                dev_free(plan->herm_ws);
+                plan->herm_ws = nullptr;
+                plan->herm_bytes = 0;
+                return st;
+            }
+        }
+    }
+    plan->hermitian = 1;
+    plan->config_gen++;
+    return DGFS_OK;
+}
+
 dgfs_status dgfs_collide_host(dgfs_plan plan, int P, const void *f_host, void *Q_host, void *stream)
 {
     if (!plan || !f_host || !Q_host || P < 1 || P > plan->max_points) {
@@ -506,6 +550,10 @@ dgfs_status dgfs_collide_backward(dgfs_plan plan, int P, const void *f_dev, cons
     if (st != DGFS_OK) return st;
     if (plan->prec != DGFS_FP64) {
         set_error("dgfs_collide_backward: tensor-core plans do not implement the adjoint yet");
+        return DGFS_EUNSUPPORTED;
+    }
+    if (plan->hermitian) {
+        set_error("dgfs_collide_backward: the adjoint is of the literal operator; switch the Hermitian form off");
         return DGFS_EUNSUPPORTED;
     }
     return fp64_backward(plan, P, f_dev, dQ_dev, df_dev, domega, domega_on_host,

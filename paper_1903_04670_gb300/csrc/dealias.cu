@@ -268,6 +268,10 @@ dgfs_status dgfs_collide_dealiased(dgfs_plan plan, int P, int N, const void *f_d
                   "buffer (256-byte aligned, at least dgfs_dealias_work_bytes)");
         return DGFS_EINVAL;
     }
+    if (plan->hermitian) {
+        set_error("dgfs_collide_dealiased: runs the literal operator; switch the plan's Hermitian form off");
+        return DGFS_EUNSUPPORTED;
+    }
     dgfs_status st = plan_entry_check(plan);
     if (st != DGFS_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

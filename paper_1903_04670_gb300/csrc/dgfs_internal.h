@@ -67,6 +67,11 @@ struct dgfs_plan_s {
     unsigned config_gen = 0;
     // per-kernel CUDA-event profiler (capi.cu), null unless enabled
     void *prof = nullptr;
+    // 1: the declared Hermitian form (Nyquist planes removed, two points per
+    // grid slot); herm_ws is its extra workspace (dgfs_plan_set_hermitian)
+    int hermitian = 0;
+    void *herm_ws = nullptr;
+    size_t herm_bytes = 0;
 };
 
 namespace dgfs {
@@ -148,6 +153,10 @@ dgfs_status df_forward(dgfs_plan_s *plan, int P, const float *f, float4 *F, cons
 dgfs_status df_finish(dgfs_plan_s *plan, int P, float4 *G, long pair_stride, const float4 *F, const float *f,
                       float *Q, const float4 *tw, cudaStream_t st);
 dgfs_status df_tables(dgfs_plan_s *plan, float4 **tw_out);
+dgfs_status df_herm_prepare(dgfs_plan_s *plan, int P, float4 *F, float4 *tmp, float *ft, const float4 *tw,
+                            cudaStream_t st);
+dgfs_status df_herm_finish(dgfs_plan_s *plan, int P, float4 *G, long pair_stride, float4 *Z2, long z2_stride,
+                           const float4 *F, const float *ft, float *Q, const float4 *tw, cudaStream_t st);
 // moments (fft64.cu)
 dgfs_status moments(dgfs_plan_s *plan, int P, const void *Q, double *out, cudaStream_t st);
 // tc32.cu
@@ -157,6 +166,10 @@ dgfs_status tc_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStr
 size_t tc_workspace_bytes(const dgfs_plan_s *plan);
 dgfs_status tc_check(dgfs_plan_s *plan);
 bool tc_supports_collapse(const dgfs_plan_s *plan);
+size_t tc_herm_bytes(const dgfs_plan_s *plan);
+bool tc_herm_supported(const dgfs_plan_s *plan);
+dgfs_status tc_herm_build(dgfs_plan_s *plan);
+size_t fp64_herm_bytes(const dgfs_plan_s *plan);
 dgfs_status tc_set_variant(dgfs_plan_s *plan, int variant);
 dgfs_status tc_batch_build(int count, dgfs_plan_s *const *plans, const int *P, void *const *f, void *const *Q,
                            void **out);

@@ -65,6 +65,7 @@ struct PassArgs {
     double beta, inv_n, inv_n2;
     void *Q;              // [P][S][S][n]
     const double2 *tw;
+    int herm = 0;         // Hermitian form: PROD / PROD_SUM multiply real and imaginary parts separately
 };
 
 template <int N, int AXIS>
@@ -145,8 +146,13 @@ __global__ void __launch_bounds__(128) k_pass(PassArgs a)
 #pragma unroll
         for (int j = 0; j < N; ++j) u[j] = cmul(gb[pencil_off<N, AXIS>(pi, j)], phq[j]);
         fft<N, +1>(u, tw);
+        if (a.herm) {  // two packed real translates per slot: (Re A Re B, Im A Im B)
 #pragma unroll
-        for (int j = 0; j < N; ++j) v[j] = cmul(v[j], u[j]);
+            for (int j = 0; j < N; ++j) v[j] = make_double2(v[j].x * u[j].x, v[j].y * u[j].y);
+        } else {
+#pragma unroll
+            for (int j = 0; j < N; ++j) v[j] = cmul(v[j], u[j]);
+        }
         fft<N, -1>(v, tw);
 #pragma unroll
         for (int k = 0; k < N; ++k) ga[pencil_off<N, AXIS>(pi, k)] = v[k];
@@ -169,8 +175,14 @@ __global__ void __launch_bounds__(128) k_pass(PassArgs a)
 #pragma unroll
             for (int j = 0; j < N; ++j) u[j] = cmul(gb[pencil_off<N, AXIS>(pi, j)], phq[j]);
             fft<N, +1>(u, tw);
+            if (a.herm) {
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc[j] = cadd(acc[j], cmul(v[j], u[j]));
+                for (int j = 0; j < N; ++j)
+                    acc[j] = make_double2(acc[j].x + v[j].x * u[j].x, acc[j].y + v[j].y * u[j].y);
+            } else {
+#pragma unroll
+                for (int j = 0; j < N; ++j) acc[j] = cadd(acc[j], cmul(v[j], u[j]));
+            }
         }
         fft<N, -1>(acc, tw);
         double2 *go = a.GA + ((long)e * a.RS + (long)r * a.M) * n;
@@ -260,6 +272,59 @@ __global__ void k_herm(double2 *G2, const double2 *QG, const double2 *F, const d
     const double h1x = 0.5 * (a0.x + a1.x), h1y = 0.5 * (a0.y - a1.y);
     const double h2x = 0.5 * (l0.x + l1.x), h2y = 0.5 * (l0.y - l1.y);
     G2[e * n + k] = make_double2(h1x - h2y, h1y + h2x);
+}
+
+// Hermitian form (declared variant): slot e carries points 2e (real part)
+// and 2e + 1 (imaginary part).  Fpk[e][s] = P (F[2e][s] + i F[2e + 1][s]), P
+// removing every mode on a Nyquist plane (index N / 2 along any axis).
+__device__ __forceinline__ bool nyquist_index(long k, int N)
+{
+    const int kx = (int)(k / ((long)N * N)), ky = (int)((k / N) % N), kz = (int)(k % N);
+    return kx == N / 2 || ky == N / 2 || kz == N / 2;
+}
+
+__global__ void k_pack64(double2 *Fpk, const double2 *F, int N, long n, int S, int P, int Ps)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;  // over [Ps][S][n]
+    if (i >= (long)Ps * S * n) return;
+    const long k = i % n, es = i / n;
+    const int s = (int)(es % S), e = (int)(es / S);
+    double2 v = make_double2(0.0, 0.0);
+    if (!nyquist_index(k, N)) {
+        const double2 a = F[((long)(2 * e) * S + s) * n + k];
+        const double2 b = 2 * e + 1 < P ? F[((long)(2 * e + 1) * S + s) * n + k] : make_double2(0.0, 0.0);
+        v = make_double2(a.x - b.y, a.y + b.x);
+    }
+    Fpk[i] = v;
+}
+
+// Finish, first step, per slot e of the chunk: G2 = P QG (gain), QG = c Fpk_q
+// (loss spectra of both points), Z3 = Fpk_p (f~_p of both points)
+__global__ void k_herm_prep64(double2 *G2, double2 *QG, double2 *Z3, const double2 *Fpk, const double2 *c, int N,
+                              long n, int S, int p, int q, int pt0, int E)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long)E * n) return;
+    const long e = i / n, k = i % n;
+    const double2 g = QG[i];
+    G2[i] = nyquist_index(k, N) ? make_double2(0.0, 0.0) : g;
+    QG[i] = cmul(c[k], Fpk[((pt0 + e) * S + q) * n + k]);
+    Z3[i] = Fpk[((pt0 + e) * S + p) * n + k];
+}
+
+// Finish, last step: with G = ifft3_u(P QG), L = ifft3_u(c Fpk_q) and
+// W = ifft3_u(Fpk_p) = n (f~_p(2e) + i f~_p(2e + 1)):
+// Q(2e) = beta/n (Re G - Re W / n Re L), Q(2e + 1) likewise with the imaginary parts
+__global__ void k_herm_combine64(double *Q, const double2 *G2, const double2 *QG, const double2 *Z3, long n, int S,
+                                 int p, int q, int pt0, int E, int P, double sc, double inv_n)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long)E * n) return;
+    const long e = i / n, k = i % n;
+    const double2 g = G2[i], l = QG[i], w = Z3[i];
+    const long i0 = 2 * (pt0 + e), i1 = i0 + 1;
+    Q[((i0 * S + p) * S + q) * n + k] = sc * (g.x - w.x * inv_n * l.x);
+    if (i1 < P) Q[((i1 * S + p) * S + q) * n + k] = sc * (g.y - w.y * inv_n * l.y);
 }
 
 constexpr int kThreads = 128;
@@ -371,6 +436,101 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, void 
     return DGFS_OK;
 }
 
+// Hermitian form of the FP64 path (FP64 plans): the forward transforms of
+// every point, the packed Nyquist-free spectra of the slots (herm_ws), then
+// the passes of collide_n over slots with the packed product, and a finish
+// that removes the gain's Nyquist planes and separates the two points.
+template <int N>
+dgfs_status collide_herm_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaStream_t st)
+{
+    const int S = plan->S, RS = plan->Nrho * plan->M, E = plan->chunk, Ps = (P + 1) / 2;
+    const long n = (long)N * N * N;
+    double2 *F = reinterpret_cast<double2 *>(plan->ws);
+    double2 *GA = F + (long)plan->max_points * S * n;
+    double2 *GB = GA + (long)E * RS * n;
+    double2 *QG = GB + (long)E * RS * n;
+    double2 *G2 = QG + (long)E * n;
+    double2 *Fpk = reinterpret_cast<double2 *>(plan->herm_ws);
+
+    PassArgs a{};
+    a.n = n;
+    a.S = S;
+    a.RS = RS;
+    a.f = reinterpret_cast<const double *>(f);
+    a.f32 = 0;
+    a.F = F;
+    a.buf = F;
+    a.tw = plan->twiddle;
+    a.inv_n = 1.0 / (double)n;
+    a.inv_n2 = a.inv_n * a.inv_n;
+    DGFS_TRY((launch<N, 0, FWD_REAL>(plan, dim3(1, S, P), a, st)));
+    DGFS_TRY((launch<N, 1, FWD_INPLACE>(plan, dim3(1, S, P), a, st)));
+    DGFS_TRY((launch<N, 2, FWD_INPLACE>(plan, dim3(1, S, P), a, st)));
+    {
+        const long total = (long)Ps * S * n;
+        ProfScope ps(plan, "fp64_herm_pack", st);
+        k_pack64<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(Fpk, F, N, n, S, P, Ps);
+    }
+    DGFS_LAUNCHED(plan);
+
+    a.F = Fpk;  // slots in place of points
+    a.GA = GA;
+    a.GB = GB;
+    a.QG = QG;
+    a.herm = 1;
+    for (int p = 0; p < S; ++p)
+        for (int q = 0; q < S; ++q) {
+            const PairTables &pt = plan->pairs[p * S + q];
+            a.p = p;
+            a.q = q;
+            a.phase = pt.phase;
+            a.b = pt.b;
+            a.w = pt.w;
+            for (int pt0 = 0; pt0 < Ps; pt0 += E) {
+                const int Ec = std::min(E, Ps - pt0);
+                a.pt0 = pt0;
+                DGFS_TRY((launch<N, 0, INV_AB_FIRST>(plan, dim3(1, RS, Ec), a, st)));
+                DGFS_TRY((launch<N, 1, INV_AB>(plan, dim3(1, RS, Ec), a, st)));
+                a.buf = GA;
+                if (plan->collapse) {
+                    a.M = plan->M;
+                    a.grid_step = plan->M;
+                    DGFS_TRY((launch<N, 2, PROD_SUM>(plan, dim3(1, plan->Nrho, Ec), a, st)));
+                    DGFS_TRY((launch<N, 1, FWD_INPLACE>(plan, dim3(1, plan->Nrho, Ec), a, st)));
+                } else {
+                    a.M = 1;
+                    a.grid_step = 1;
+                    DGFS_TRY((launch<N, 2, PROD>(plan, dim3(1, RS, Ec), a, st)));
+                    DGFS_TRY((launch<N, 1, FWD_INPLACE>(plan, dim3(1, RS, Ec), a, st)));
+                }
+                DGFS_TRY((launch<N, 0, MAC>(plan, dim3(1, 1, Ec), a, st)));
+                a.grid_step = 1;
+                {
+                    const long total = (long)Ec * n;
+                    ProfScope ps(plan, "fp64_herm_prep", st);
+                    k_herm_prep64<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(G2, QG, GA, Fpk, pt.c, N, n, S, p,
+                                                                                     q, pt0, Ec);
+                }
+                DGFS_LAUNCHED(plan);
+                for (double2 *base : {G2, QG, GA}) {
+                    a.G2 = base;
+                    DGFS_TRY((launch<N, 0, FIN2>(plan, dim3(1, 1, Ec), a, st)));
+                    DGFS_TRY((launch<N, 1, FIN2>(plan, dim3(1, 1, Ec), a, st)));
+                    DGFS_TRY((launch<N, 2, FIN2>(plan, dim3(1, 1, Ec), a, st)));
+                }
+                {
+                    const long total = (long)Ec * n;
+                    ProfScope ps(plan, "fp64_herm_combine", st);
+                    k_herm_combine64<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+                        reinterpret_cast<double *>(Qout), G2, QG, GA, n, S, p, q, pt0, Ec, P, pt.beta * a.inv_n,
+                        a.inv_n);
+                }
+                DGFS_LAUNCHED(plan);
+            }
+        }
+    return DGFS_OK;
+}
+
 // Forward transforms F = fft3(f) of every (point, species) in FP64; f is
 // double for FP64 plans and float otherwise.
 template <int N>
@@ -460,7 +620,26 @@ dgfs_status fp64_collide_ws(dgfs_plan_s *plan, int P, const void *f, void *Q, vo
 
 dgfs_status fp64_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st)
 {
+    if (plan->hermitian) {
+        switch (plan->N) {
+        case 4: return collide_herm_n<4>(plan, P, f, Q, st);
+        case 6: return collide_herm_n<6>(plan, P, f, Q, st);
+        case 8: return collide_herm_n<8>(plan, P, f, Q, st);
+        case 12: return collide_herm_n<12>(plan, P, f, Q, st);
+        case 16: return collide_herm_n<16>(plan, P, f, Q, st);
+        case 24: return collide_herm_n<24>(plan, P, f, Q, st);
+        case 32: return collide_herm_n<32>(plan, P, f, Q, st);
+        case 48: return collide_herm_n<48>(plan, P, f, Q, st);
+        default: set_error("N not supported by the FP64 path"); return DGFS_EUNSUPPORTED;
+        }
+    }
     return fp64_collide_ws(plan, P, f, Q, plan->ws, plan->max_points, plan->chunk, st);
+}
+
+size_t fp64_herm_bytes(const dgfs_plan_s *plan)
+{
+    const long n = (long)plan->N * plan->N * plan->N;
+    return sizeof(double2) * (size_t)((plan->max_points + 1) / 2) * plan->S * n;
 }
 
 dgfs_status fp64_forward(dgfs_plan_s *plan, int P, const void *f, double2 *F, cudaStream_t st)

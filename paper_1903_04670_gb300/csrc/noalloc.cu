@@ -98,8 +98,8 @@ extern "C" dgfs_status dgfs_collide_noalloc(dgfs_plan plan, int P, const void *f
         set_error("dgfs_collide_noalloc: bad plan, pointer or P");
         return DGFS_EINVAL;
     }
-    if (plan->prec != DGFS_FP64) {
-        set_error("dgfs_collide_noalloc: only DGFS_FP64 plans are supported");
+    if (plan->prec != DGFS_FP64 || plan->hermitian) {
+        set_error("dgfs_collide_noalloc: only DGFS_FP64 plans in the literal form are supported");
         return DGFS_EUNSUPPORTED;
     }
     // largest number of evaluations per pass whose scratch fits the array

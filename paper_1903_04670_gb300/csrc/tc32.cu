@@ -85,6 +85,13 @@ struct TcArgs {
     const double *w;       // [RS]
     const uint8_t *idmask; // [RS] identity-axis bits (x: 1, y: 2, z: 4), null = none
     int *err;
+    // Hermitian form (declared variant): grid slot e carries points 2(pt0 + e)
+    // (real part) and 2(pt0 + e) + 1 (imaginary part, absent beyond npts) of
+    // the Nyquist-free f~ in a.f; stage A's z-pass takes that complex input
+    // with the complex-input images zimg [RS][2 sides][terms][IMGC], and stage
+    // B multiplies real parts and imaginary parts separately
+    int herm, npts;
+    const uint8_t *zimg;
 };
 
 __host__ __device__ constexpr int pow2_cols(int c)
@@ -278,7 +285,7 @@ template <int N, int FMT> struct Smem {
 // its NP pipelines loops over items (point e, group of G x-planes): z-pass
 // (real input), an in-plane transpose through shared memory, y-pass, result A'
 // or B' to global.
-template <int N, int FMT>
+template <int N, int FMT, bool HC = false>
 __device__ __forceinline__ void k_stage_a_body(const TcArgs &a, const uint3 bid, const uint3 gdim)
 {
     using SM = Smem<N, FMT>;
@@ -293,9 +300,13 @@ __device__ __forceinline__ void k_stage_a_body(const TcArgs &a, const uint3 bid,
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = align1024(smem_raw);
     const int pp = threadIdx.x / kRows, t = threadIdx.x % kRows, bar = 1 + pp;
-    uint8_t *Bz = sm;                            // NT terms, IR apart
-    uint8_t *By = RESIDENT ? Bz + NT * IR : Bz;  // NT terms, IC apart (one reloaded slot if not resident)
-    uint8_t *A0 = sm + (RESIDENT ? NT * (IR + IC) : NT * IC) + pp * NT * AB;
+    // the z image: real input (K = N) in the literal form, complex input
+    // (K = 2N, IZ = IC bytes per term) in the Hermitian form
+    constexpr bool herm = HC;
+    constexpr int IZ = herm ? IC : IR;
+    uint8_t *Bz = sm;                            // NT terms, IZ apart
+    uint8_t *By = RESIDENT ? Bz + NT * IZ : Bz;  // NT terms, IC apart (one reloaded slot if not resident)
+    uint8_t *A0 = sm + (RESIDENT ? NT * (IR + IC) + (herm ? NT * (IC - IR) : 0) : NT * IC) + pp * NT * AB;
     __shared__ uint64_t mb[NP + 1];  // [0, NP): MMA per pipeline, NP: copies
     __shared__ uint32_t tslot;
     const int rs = bid.y, side = bid.z;
@@ -311,29 +322,42 @@ __device__ __forceinline__ void k_stage_a_body(const TcArgs &a, const uint3 bid,
     uint32_t ph_mma = 0, ph_cp = 0;
     auto load_imgs = [&](int which) {  // 0: z, 1: y, 2: both
         if (threadIdx.x == 0) {
-            const uint32_t bytes = which == 0 ? NT * IR : which == 1 ? NT * IC : NT * (IR + IC);
+            const uint32_t bytes = which == 0 ? NT * IZ : which == 1 ? NT * IC : NT * (IZ + IC);
             mbar_expect_tx(&mb[NP], bytes);
-            if (which != 1) copy_terms(Bz, IR, timg_at<FMT>(a.timg, N, rs, side, 2), IC, IR, NT, &mb[NP]);
+            if (which != 1) {
+                if (herm)
+                    copy_terms(Bz, IZ, a.zimg + ((long)rs * 2 + side) * NT * (long)IC, IC, IZ, NT, &mb[NP]);
+                else
+                    copy_terms(Bz, IR, timg_at<FMT>(a.timg, N, rs, side, 2), IC, IR, NT, &mb[NP]);
+            }
             if (which != 0) copy_terms(By, IC, timg_at<FMT>(a.timg, N, rs, side, 1), IC, IC, NT, &mb[NP]);
         }
     };
     const int sp = side == 0 ? a.p : a.q;
     const int g = t / N, yl = t % N;
     float4 pf[FPT];
+    float4 pf2[HC ? FPT : 1];  // Hermitian form: the slot's second point
     auto prefetch = [&](int it) {
         const int e = it / NG, x0 = (it % NG) * G, nval = min(G, N - x0);
-        const float4 *fs =
-            reinterpret_cast<const float4 *>(a.f + ((long)(a.pt0 + e) * a.S + sp) * n + (long)x0 * NN);
+        const int pt = herm ? 2 * (a.pt0 + e) : a.pt0 + e;
+        const float4 *fs = reinterpret_cast<const float4 *>(a.f + ((long)pt * a.S + sp) * n + (long)x0 * NN);
+        const bool second = HC && herm && pt + 1 < a.npts;
+        const float4 *fs2 = fs + (long)a.S * n / 4;
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (ident_z) {  // row t = (g, y): f(x0 + g, y, z) for all z
 #pragma unroll
-            for (int j = 0; j < FPT; ++j)
-                pf[j] = (j < N / 4 && t < nval * N) ? fs[t * (N / 4) + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int j = 0; j < FPT; ++j) {
+                const bool ok = j < N / 4 && t < nval * N;
+                pf[j] = ok ? fs[t * (N / 4) + j] : zero4;
+                if constexpr (HC) pf2[j] = (ok && second) ? fs2[t * (N / 4) + j] : zero4;
+            }
             return;
         }
 #pragma unroll
         for (int j = 0; j < FPT; ++j) {
             const int i = t + kRows * j;
-            pf[j] = (4 * i < nval * NN) ? fs[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            pf[j] = (4 * i < nval * NN) ? fs[i] : zero4;
+            if constexpr (HC) pf2[j] = (4 * i < nval * NN && second) ? fs2[i] : zero4;
         }
     };
     const int stride = gdim.x * NP;
@@ -354,8 +378,10 @@ __device__ __forceinline__ void k_stage_a_body(const TcArgs &a, const uint3 bid,
                 if (t < nval * N) {
 #pragma unroll
                     for (int j = 0; j < N / 4; ++j) {
-                        dst[2 * j] = make_float4(pf[j].x, 0.f, pf[j].y, 0.f);
-                        dst[2 * j + 1] = make_float4(pf[j].z, 0.f, pf[j].w, 0.f);
+                        float4 im = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if constexpr (HC) im = pf2[j];
+                        dst[2 * j] = make_float4(pf[j].x, im.x, pf[j].y, im.y);
+                        dst[2 * j + 1] = make_float4(pf[j].z, im.z, pf[j].w, im.w);
                     }
                 }
                 if (it + stride < items) prefetch(it + stride);
@@ -365,20 +391,35 @@ __device__ __forceinline__ void k_stage_a_body(const TcArgs &a, const uint3 bid,
             if (t < nval * N) {
 #pragma unroll
                 for (int j = 0; j < N / 4; ++j) {
-                    tcfmt::st_c<FMT>(A0, AB, g * N + 4 * j, yl, pf[j].x, 0.f);
-                    tcfmt::st_c<FMT>(A0, AB, g * N + 4 * j + 1, yl, pf[j].y, 0.f);
-                    tcfmt::st_c<FMT>(A0, AB, g * N + 4 * j + 2, yl, pf[j].z, 0.f);
-                    tcfmt::st_c<FMT>(A0, AB, g * N + 4 * j + 3, yl, pf[j].w, 0.f);
+                    float4 im = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if constexpr (HC) im = pf2[j];
+                    tcfmt::st_c<FMT>(A0, AB, g * N + 4 * j, yl, pf[j].x, im.x);
+                    tcfmt::st_c<FMT>(A0, AB, g * N + 4 * j + 1, yl, pf[j].y, im.y);
+                    tcfmt::st_c<FMT>(A0, AB, g * N + 4 * j + 2, yl, pf[j].z, im.z);
+                    tcfmt::st_c<FMT>(A0, AB, g * N + 4 * j + 3, yl, pf[j].w, im.w);
                 }
             }
             if (it + stride < items) prefetch(it + stride);
+        } else {
+        if constexpr (HC) {  // complex input: (point 2e, point 2e + 1) at K = 2 z, 2 z + 1
+#pragma unroll
+            for (int j = 0; j < FPT; ++j) {
+                const int i = t + kRows * j;
+                if (4 * i < nval * NN) {
+                    const int row = (4 * i) / N, z = (4 * i) % N;
+                    tcfmt::st_c2<FMT>(A0, AB, row, z, make_float2(pf[j].x, pf2[j].x), make_float2(pf[j].y, pf2[j].y));
+                    tcfmt::st_c2<FMT>(A0, AB, row, z + 2, make_float2(pf[j].z, pf2[j].z),
+                                      make_float2(pf[j].w, pf2[j].w));
+                }
+            }
         } else {
 #pragma unroll
         for (int j = 0; j < FPT; ++j) {
             const int i = t + kRows * j;
             if (4 * i < nval * NN) tcfmt::st_f4<FMT>(A0, AB, (4 * i) / N, (4 * i) % N, pf[j]);
         }
-        if constexpr (KR > N) {  // zero the pad of this thread's row in every term
+        }
+        if constexpr (KR > N && !HC) {  // zero the pad of this thread's row in every term
             if (t < nval * N)
 #pragma unroll
                 for (int term = 0; term < NT; ++term)
@@ -393,7 +434,10 @@ __device__ __forceinline__ void k_stage_a_body(const TcArgs &a, const uint3 bid,
             ok = wait_copy_pipe(&mb[NP], ph_cp, bar);
             if (!ok) break;
         }
-        ok = run_mma(&mb[pp], ph_mma, bar, [&] { tcfmt::gemm<FMT>(tb, A0, AB, Bz, IR, NO, KR, a.nterms); });
+        ok = run_mma(&mb[pp], ph_mma, bar, [&] {
+            if constexpr (HC) tcfmt::gemm<FMT>(tb, A0, AB, Bz, IC, NO, KC, a.nterms);
+            else tcfmt::gemm<FMT>(tb, A0, AB, Bz, IR, NO, KR, a.nterms);
+        });
         if (!ok) break;
         if (ident_y) {
             // sigma_y = 0: T_y = I, row t = (g, y) already holds A'(x0+g, y, z') for all z'
@@ -440,6 +484,13 @@ template <int N, int FMT>
 __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a(TcArgs a)
 {
     k_stage_a_body<N, FMT>(a, blockIdx, dim3(gridDim.x, gridDim.y, gridDim.z));
+}
+
+// Stage A of the Hermitian form (complex z-pass input, two points per slot)
+template <int N, int FMT>
+__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_stage_a_herm(TcArgs a)
+{
+    k_stage_a_body<N, FMT, true>(a, blockIdx, dim3(gridDim.x, gridDim.y, gridDim.z));
 }
 
 // ------------------------------------------- stage A, two threads per row
@@ -814,7 +865,7 @@ __global__ void __launch_bounds__(4 * kRows, 1) k_stage_a_ws(TcArgs a)
 // fit next to the data operands (else it reloads one image slot per
 // contraction); each of its NP pipelines loops over items (point e, tile of
 // 128 (y, z) pencils): H = F_x ((T^p_x A') . (T^q_x B')).
-template <int N, int FMT>
+template <int N, int FMT, bool HP = false>
 __device__ __forceinline__ void k_stage_b_body(const TcArgs &a, const uint3 bid, const uint3 gdim)
 {
     using SM = Smem<N, FMT>;
@@ -877,9 +928,12 @@ __device__ __forceinline__ void k_stage_b_body(const TcArgs &a, const uint3 bid,
             unpack_pair<N>(pb, pb_raw);
 #pragma unroll
             for (int x = 0; x < N; x += 2) {
-                const float2 u = make_float2(pa[x].x * pb[x].x - pa[x].y * pb[x].y, pa[x].x * pb[x].y + pa[x].y * pb[x].x);
-                const float2 v = make_float2(pa[x + 1].x * pb[x + 1].x - pa[x + 1].y * pb[x + 1].y,
-                                             pa[x + 1].x * pb[x + 1].y + pa[x + 1].y * pb[x + 1].x);
+                const float2 u = HP ? make_float2(pa[x].x * pb[x].x, pa[x].y * pb[x].y)
+                                        : make_float2(pa[x].x * pb[x].x - pa[x].y * pb[x].y,
+                                                      pa[x].x * pb[x].y + pa[x].y * pb[x].x);
+                const float2 v = HP ? make_float2(pa[x + 1].x * pb[x + 1].x, pa[x + 1].y * pb[x + 1].y)
+                                        : make_float2(pa[x + 1].x * pb[x + 1].x - pa[x + 1].y * pb[x + 1].y,
+                                                      pa[x + 1].x * pb[x + 1].y + pa[x + 1].y * pb[x + 1].x);
                 tcfmt::st_c2<FMT>(A0, AB, t, x, u, v);
             }
             const int nx = it + stride;
@@ -928,10 +982,16 @@ __device__ __forceinline__ void k_stage_b_body(const TcArgs &a, const uint3 bid,
             tmem_ld16x2(tl + c0, tl + NO + c0, va, vb);
 #pragma unroll
             for (int j = 0; j < 8; j += 2) {
-                const float2 p0v = make_float2(va[2 * j] * vb[2 * j] - va[2 * j + 1] * vb[2 * j + 1],
-                                               va[2 * j] * vb[2 * j + 1] + va[2 * j + 1] * vb[2 * j]);
-                const float2 p1v = make_float2(va[2 * j + 2] * vb[2 * j + 2] - va[2 * j + 3] * vb[2 * j + 3],
-                                               va[2 * j + 2] * vb[2 * j + 3] + va[2 * j + 3] * vb[2 * j + 2]);
+                // literal: the complex product; Hermitian form: the two real
+                // translates of each packed point multiply separately
+                const float2 p0v =
+                    HP ? make_float2(va[2 * j] * vb[2 * j], va[2 * j + 1] * vb[2 * j + 1])
+                           : make_float2(va[2 * j] * vb[2 * j] - va[2 * j + 1] * vb[2 * j + 1],
+                                         va[2 * j] * vb[2 * j + 1] + va[2 * j + 1] * vb[2 * j]);
+                const float2 p1v =
+                    HP ? make_float2(va[2 * j + 2] * vb[2 * j + 2], va[2 * j + 3] * vb[2 * j + 3])
+                           : make_float2(va[2 * j + 2] * vb[2 * j + 2] - va[2 * j + 3] * vb[2 * j + 3],
+                                         va[2 * j + 2] * vb[2 * j + 3] + va[2 * j + 3] * vb[2 * j + 2]);
                 tcfmt::st_c2<FMT>(A0, AB, t, c0 / 2 + j, p0v, p1v);
             }
         }
@@ -959,6 +1019,13 @@ template <int N, int FMT>
 __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b(TcArgs a)
 {
     k_stage_b_body<N, FMT>(a, blockIdx, dim3(gridDim.x, gridDim.y, gridDim.z));
+}
+
+// Stage B of the Hermitian form (products of the packed real translates)
+template <int N, int FMT>
+__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b_herm(TcArgs a)
+{
+    k_stage_b_body<N, FMT, true>(a, blockIdx, dim3(gridDim.x, gridDim.y, gridDim.z));
 }
 
 // ------------------------------------------------------------------ stage C
@@ -1239,6 +1306,36 @@ __global__ void k_timg(uint8_t *out, const double2 *phase, int N, int RS)
     }
 }
 
+// Hermitian form: T_z of every (r, s) and side as a complex-input image (the
+// real 2x2 block [Re -Im; Im Re] at K = 2j', 2j'+1), out [RS][2 sides][terms][IMGC]
+template <int FMT>
+__global__ void k_timg_zc(uint8_t *out, const double2 *phase, int N, int RS)
+{
+    const long total = (long)RS * 2 * N * N;
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int jp = (int)(i % N), j = (int)((i / N) % N), side = (int)((i / ((long)N * N)) % 2);
+    const int rs = (int)(i / (2L * N * N));
+    const double2 *ph = phase + ((long)rs * 6 + side * 3 + 2) * N;
+    double tr = 0, ti = 0;
+    for (int l = 0; l < N; ++l) {
+        const int m = ((l * (j - jp)) % N + N) % N;
+        double s, c;
+        sincospi(2.0 * m / N, &s, &c);
+        tr += c * ph[l].x - s * ph[l].y;
+        ti += c * ph[l].y + s * ph[l].x;
+    }
+    tr /= N;
+    ti /= N;
+    const int NO = 2 * N;
+    const long IC = tcfmt::img_c<FMT>(N);
+    uint8_t *img = out + ((long)rs * 2 + side) * Fmt<FMT>::NT * IC;
+    tcfmt::put_img<FMT>(img, IC, 2 * j, 2 * jp, NO, tr);
+    tcfmt::put_img<FMT>(img, IC, 2 * j, 2 * jp + 1, NO, -ti);
+    tcfmt::put_img<FMT>(img, IC, 2 * j + 1, 2 * jp, NO, ti);
+    tcfmt::put_img<FMT>(img, IC, 2 * j + 1, 2 * jp + 1, NO, tr);
+}
+
 // forward DFT F[k][j] = exp(-2 pi i jk/N) as pre-swizzled complex-input images
 template <int FMT>
 __global__ void k_fimg(uint8_t *out, int N)
@@ -1287,6 +1384,35 @@ TcWs ws_of(const dgfs_plan_s *plan)
     w.H = w.Bq + (long)ts->chunk_max * RS * n;
     w.QGp = w.H + (long)ts->chunk_max * RS * n;
     return w;
+}
+
+// Workspace of the Hermitian form (dgfs_plan_set_hermitian), per plan:
+//   ft [maxP][S][n] float (f~) | Z2 [S*S][Ps_max][n] float4 | zimg [S*S][RS][2][terms][IMGC]
+struct HermWs {
+    float *ft;
+    float4 *z2;
+    long z2_stride;
+    uint8_t *zimg;
+    long zimg_pair;  // bytes per pair
+};
+
+template <int FMT> long zimg_pair_bytes(const dgfs_plan_s *plan)
+{
+    return (long)plan->Nrho * plan->M * 2 * Fmt<FMT>::NT * tcfmt::img_c<FMT>(plan->N);
+}
+
+HermWs herm_ws_of(const dgfs_plan_s *plan)
+{
+    const TcState *ts = reinterpret_cast<const TcState *>(plan->tc);
+    const long n = (long)plan->N * plan->N * plan->N;
+    const long Psmax = (plan->max_points + 1) / 2;
+    HermWs h;
+    h.ft = reinterpret_cast<float *>(plan->herm_ws);
+    h.z2 = reinterpret_cast<float4 *>(h.ft + (long)plan->max_points * plan->S * n);
+    h.z2_stride = Psmax * n;
+    h.zimg = reinterpret_cast<uint8_t *>(h.z2 + (long)plan->S * plan->S * h.z2_stride);
+    h.zimg_pair = ts->fmt == 0 ? zimg_pair_bytes<0>(plan) : zimg_pair_bytes<1>(plan);
+    return h;
 }
 
 // accumulation blocks of (r, s); with the sigma collapse every block holds whole radial nodes
@@ -1413,6 +1539,78 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
                      reinterpret_cast<float *>(Qout), ts->tw_df, st);
 }
 
+// Hermitian form (declared variant, dgfs_plan_set_hermitian): Algorithm 2
+// with the Nyquist planes removed.  Every translate is then real, so a grid
+// slot carries two points, point 2e as the real part and 2e + 1 as the
+// imaginary part, and each (r, s) step serves both: the stage kernels run
+// over ceil(P/2) slots.  Stage A packs the two Nyquist-free inputs into its
+// complex z-pass, stage B multiplies the two real translates of each point
+// separately, stage C and the partial sums are unchanged; the finish removes
+// the gain's Nyquist planes and separates the two points.
+template <int N, int FMT>
+dgfs_status collide_herm_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaStream_t st)
+{
+    using SM = Smem<N, FMT>;
+    TcState *ts = reinterpret_cast<TcState *>(plan->tc);
+    const int S = plan->S;
+    const long n = (long)N * N * N;
+    const int E = ts->chunk, RSB = rs_blocks(plan), Ps = (P + 1) / 2;
+    const TcWs w = ws_of(plan);
+    const HermWs h = herm_ws_of(plan);
+    constexpr int NT = Fmt<FMT>::NT;
+    constexpr size_t smem_a = SM::A + (size_t)NT * (tcfmt::img_c<FMT>(N) - tcfmt::img_r<FMT>(N));
+    cudaStream_t sa = plan->prof ? st : ts->side;
+    const bool fork = sa != st;
+    bool first = true;
+    // F = fft3(f), projected; f~ = ifft3(P F) (the QG region is free until the first partial sum)
+    DGFS_TRY(df_forward(plan, P, reinterpret_cast<const float *>(f), w.F, ts->tw_df, st));
+    DGFS_TRY(df_herm_prepare(plan, P, w.F, w.QG, h.ft, ts->tw_df, st));
+    // the side stream's first stage A reads f~: fork after it is written
+    if (fork) DGFS_CUDA(cudaEventRecord(ts->ev_entry, st));
+    for (int p = 0; p < S; ++p)
+        for (int q = 0; q < S; ++q) {
+            for (int pt0 = 0; pt0 < Ps; pt0 += E) {
+                const int Ec = std::min(E, Ps - pt0);
+                TcArgs a = job_args(plan, h.ft, p, q, pt0, Ec);
+                a.herm = 1;
+                a.npts = P;
+                a.zimg = h.zimg + (long)(p * S + q) * h.zimg_pair;
+                dim3 gA, gB, gC;
+                job_grids<N, FMT>(plan, Ec, gA, gB, gC);
+                if (fork) DGFS_CUDA(cudaStreamWaitEvent(sa, first ? ts->ev_entry : ts->ev_b, 0));
+                first = false;
+                {
+                    ProfScope ps(plan, "tc_stage_a", sa);
+                    k_stage_a_herm<N, FMT><<<gA, kRows * NPipes<N, FMT>::A, smem_a, sa>>>(a);
+                }
+                DGFS_LAUNCHED(plan);
+                if (fork) {
+                    DGFS_CUDA(cudaEventRecord(ts->ev_a, sa));
+                    DGFS_CUDA(cudaStreamWaitEvent(st, ts->ev_a, 0));
+                }
+                {
+                    ProfScope ps(plan, "tc_stage_b", st);
+                    k_stage_b_herm<N, FMT><<<gB, kRows * NPipes<N, FMT>::B, SM::B, st>>>(a);
+                }
+                DGFS_LAUNCHED(plan);
+                if (fork) DGFS_CUDA(cudaEventRecord(ts->ev_b, st));
+                {
+                    ProfScope ps(plan, "tc_stage_c", st);
+                    k_stage_c<N, FMT><<<gC, kRows * NPipes<N, FMT>::C, SM::C, st>>>(a);
+                }
+                DGFS_LAUNCHED(plan);
+                {
+                    ProfScope ps(plan, "tc_sum_partials", st);
+                    k_sum_partials<<<nblk((long)Ec * n, 256), 256, 0, st>>>(w.QG + (p * S + q) * w.qg_stride,
+                                                                           w.QGp, RSB, n, pt0, Ec);
+                }
+                DGFS_LAUNCHED(plan);
+            }
+        }
+    return df_herm_finish(plan, P, w.QG, w.qg_stride, h.z2, h.z2_stride, w.F, h.ft, reinterpret_cast<float *>(Qout),
+                          ts->tw_df, st);
+}
+
 template <int N, int FMT>
 dgfs_status set_smem_attrs()
 {
@@ -1425,6 +1623,12 @@ dgfs_status set_smem_attrs()
         DGFS_CUDA(cudaFuncSetAttribute(k_stage_a2<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::A));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_b<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_c<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::C));
+    if constexpr (N <= 32) {
+        DGFS_CUDA(cudaFuncSetAttribute(k_stage_a_herm<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(SM::A + (size_t)Fmt<FMT>::NT *
+                                                         (tcfmt::img_c<FMT>(N) - tcfmt::img_r<FMT>(N)))));
+        DGFS_CUDA(cudaFuncSetAttribute(k_stage_b_herm<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B));
+    }
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_a_batch<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::A));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_b_batch<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_c_batch<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::C));
@@ -1555,6 +1759,15 @@ dgfs_status round_dispatch(int N, BatchRound &r, bool build, cudaStream_t st, Fo
 template <int FMT>
 dgfs_status dispatch_collide(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaStream_t st)
 {
+    if (plan->hermitian) {
+        switch (plan->N) {
+        case 8: return collide_herm_n<8, FMT>(plan, P, f, Q, st);
+        case 16: return collide_herm_n<16, FMT>(plan, P, f, Q, st);
+        case 24: return collide_herm_n<24, FMT>(plan, P, f, Q, st);
+        case 32: return collide_herm_n<32, FMT>(plan, P, f, Q, st);
+        default: set_error("the Hermitian form of the tensor-core path supports N <= 32"); return DGFS_EUNSUPPORTED;
+        }
+    }
     switch (plan->N) {
     case 8: return collide_n<8, FMT>(plan, P, f, Q, st);
     case 16: return collide_n<16, FMT>(plan, P, f, Q, st);
@@ -1801,6 +2014,37 @@ dgfs_status tc_batch_launch(void *handle, cudaStream_t st)
         DGFS_TRY(df_finish(bp.plan, bp.P, w.QG, w.qg_stride, w.F, reinterpret_cast<const float *>(bp.f),
                            reinterpret_cast<float *>(bp.Q), ts->tw_df, st));
     }
+    return DGFS_OK;
+}
+
+// Hermitian form: bytes of the plan's extra workspace (see HermWs), and the
+// complex-input z images written into it
+size_t tc_herm_bytes(const dgfs_plan_s *plan)
+{
+    const TcState *ts = reinterpret_cast<const TcState *>(plan->tc);
+    const long n = (long)plan->N * plan->N * plan->N, S = plan->S;
+    const long Psmax = (plan->max_points + 1) / 2;
+    const long zi = ts->fmt == 0 ? zimg_pair_bytes<0>(plan) : zimg_pair_bytes<1>(plan);
+    return sizeof(float) * plan->max_points * S * n + sizeof(float4) * S * S * Psmax * n + (size_t)(S * S) * zi;
+}
+
+bool tc_herm_supported(const dgfs_plan_s *plan) { return plan->N <= 32; }
+
+dgfs_status tc_herm_build(dgfs_plan_s *plan)
+{
+    const TcState *ts = reinterpret_cast<const TcState *>(plan->tc);
+    const HermWs h = herm_ws_of(plan);
+    const int N = plan->N, RS = plan->Nrho * plan->M, S = plan->S;
+    DGFS_CUDA(cudaMemset(h.zimg, 0, (size_t)S * S * h.zimg_pair));
+    for (int pr = 0; pr < S * S; ++pr) {
+        uint8_t *dst = h.zimg + (long)pr * h.zimg_pair;
+        if (ts->fmt == 0)
+            k_timg_zc<0><<<nblk((long)RS * 2 * N * N, 256), 256>>>(dst, plan->pairs[pr].phase, N, RS);
+        else
+            k_timg_zc<1><<<nblk((long)RS * 2 * N * N, 256), 256>>>(dst, plan->pairs[pr].phase, N, RS);
+        DGFS_LAUNCHED(plan);
+    }
+    DGFS_CUDA(cudaDeviceSynchronize());
     return DGFS_OK;
 }
 
