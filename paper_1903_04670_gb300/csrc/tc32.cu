@@ -63,6 +63,7 @@ struct TcState {
     int groups_a = 2, groups_b = 4;  // CTA groups per (r, s) in stages A and B
     int tuned = 0;
     uint8_t *idmask = nullptr;  // [RS] bit d set when sigma_{s,d} == 0 (T_d is the identity; x and y are skipped)
+    uint16_t *bmap = nullptr;   // [RS] r M + s' with sigma_s' = -sigma_s (null if the design is not centrally symmetric)
     int skip_identity = 1;
     int ws_a = 0;  // stage A variant: 0 two-pipeline, 1 warp-specialised, 2 two threads per row (autotuner)
     float4 *tw_df = nullptr;  // [N] exp(-2 pi i j / N) as double-float (findf.cu)
@@ -92,6 +93,16 @@ struct TcArgs {
     // B multiplies real parts and imaginary parts separately
     int herm, npts;
     const uint8_t *zimg;
+};
+
+// Same-species pair (p = q): the B-side translate at (r, s) equals the A-side
+// translate at (r, s') with sigma_s' = -sigma_s (m_p = m_q), so stage A computes
+// the A side only and stage B reads B' from A' at bmap[rs] = r M + s'.  Kept
+// apart from TcArgs (the batched work list passes 48 TcArgs by value and does
+// not use this).
+struct Share {
+    bool on = false;
+    const uint16_t *bmap = nullptr;  // [RS], device
 };
 
 __host__ __device__ constexpr int pow2_cols(int c)
@@ -281,7 +292,9 @@ template <int N, int FMT> struct Smem {
 };
 
 // ------------------------------------------------------------------ stage A
-// grid (groups, RS, 2 sides).  A CTA holds T_z, T_y of its (r, s, side); each of
+// grid (groups, RS, sides: 2, or 1 for a same-species pair, whose B side stage B
+// reads from the A side at the reflected direction).  A CTA holds T_z, T_y of
+// its (r, s, side); each of
 // its NP pipelines loops over items (point e, group of G x-planes): z-pass
 // (real input), an in-plane transpose through shared memory, y-pass, result A'
 // or B' to global.
@@ -865,8 +878,9 @@ __global__ void __launch_bounds__(4 * kRows, 1) k_stage_a_ws(TcArgs a)
 // fit next to the data operands (else it reloads one image slot per
 // contraction); each of its NP pipelines loops over items (point e, tile of
 // 128 (y, z) pencils): H = F_x ((T^p_x A') . (T^q_x B')).
-template <int N, int FMT, bool HP = false>
-__device__ __forceinline__ void k_stage_b_body(const TcArgs &a, const uint3 bid, const uint3 gdim)
+template <int N, int FMT, bool HP = false, bool SH = false>
+__device__ __forceinline__ void k_stage_b_body(const TcArgs &a, const uint3 bid, const uint3 gdim,
+                                               const uint16_t *bmap = nullptr)
 {
     using SM = Smem<N, FMT>;
     constexpr int NP = NPipes<N, FMT>::B, NT = SM::NT, AB = SM::AB, IC = SM::IC;
@@ -915,6 +929,9 @@ __device__ __forceinline__ void k_stage_b_body(const TcArgs &a, const uint3 bid,
         else load_images(0, 3);
         ok = wait_copy_cta(&mb[NP], ph_cp);
     }
+    // B' of this (r, s): its own grid, or A' at the reflected direction (same species)
+    const float2 *bsrc = SH ? a.Ap : a.Bq;
+    const long boff = SH ? ((long)bmap[rs] - rs) * n : 0;
     for (; it < items && ok; it += stride) {
         const int e = it / NT_TILES, p0 = (it % NT_TILES) * kRows;
         const bool valid = p0 + t < NN;
@@ -922,7 +939,7 @@ __device__ __forceinline__ void k_stage_b_body(const TcArgs &a, const uint3 bid,
         float4 pb_raw[N / 2];
         if (ident_x) {
             // sigma_x = 0: T^p_x = T^q_x = I, so P = A' . B' directly
-            load_pencil(pb_raw, a.Bq + gbase, valid);
+            load_pencil(pb_raw, bsrc + (gbase + boff), valid);
             float2 pa[N], pb[N];
             unpack_pair<N>(pa, pa_raw);
             unpack_pair<N>(pb, pb_raw);
@@ -948,7 +965,7 @@ __device__ __forceinline__ void k_stage_b_body(const TcArgs &a, const uint3 bid,
 #pragma unroll
             for (int x = 0; x < N; x += 2) tcfmt::st_c2<FMT>(A0, AB, t, x, pa[x], pa[x + 1]);
         }
-        load_pencil(pb_raw, a.Bq + gbase, valid);
+        load_pencil(pb_raw, bsrc + (gbase + boff), valid);
         if (!RESIDENT) {
             load_images(0, 1);
             ok = wait_copy_pipe(&mb[NP], ph_cp, bar);
@@ -1026,6 +1043,13 @@ template <int N, int FMT>
 __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b_herm(TcArgs a)
 {
     k_stage_b_body<N, FMT, true>(a, blockIdx, dim3(gridDim.x, gridDim.y, gridDim.z));
+}
+
+// Stage B of a same-species pair: B' read from A' at the reflected direction
+template <int N, int FMT, bool HP>
+__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b_share(TcArgs a, const uint16_t *bmap)
+{
+    k_stage_b_body<N, FMT, HP, true>(a, blockIdx, dim3(gridDim.x, gridDim.y, gridDim.z), bmap);
 }
 
 // ------------------------------------------------------------------ stage C
@@ -1457,14 +1481,24 @@ TcArgs job_args(const dgfs_plan_s *plan, const void *f, int p, int q, int pt0, i
     return a;
 }
 
+// The translate sharing of a same-species pair (plain calls only)
+Share job_share(const dgfs_plan_s *plan, int p, int q)
+{
+    const TcState *ts = reinterpret_cast<const TcState *>(plan->tc);
+    Share sh;
+    sh.on = p == q && ts->bmap != nullptr;
+    sh.bmap = sh.on ? ts->bmap : nullptr;
+    return sh;
+}
+
 // Grids of the three stage kernels for one job.
 template <int N, int FMT>
-void job_grids(const dgfs_plan_s *plan, int Ec, dim3 &gA, dim3 &gB, dim3 &gC)
+void job_grids(const dgfs_plan_s *plan, int Ec, bool share, dim3 &gA, dim3 &gB, dim3 &gC)
 {
     const TcState *ts = reinterpret_cast<const TcState *>(plan->tc);
     const int RS = plan->Nrho * plan->M, RSB = rs_blocks(plan);
     constexpr int G = kRows / N;
-    gA = dim3(ts->groups_a, RS, 2);
+    gA = dim3(ts->groups_a, RS, share ? 1 : 2);
     gB = dim3(ts->groups_b, RS);
     gC = dim3((N + G - 1) / G, (RSB + NPipes<N, FMT>::C - 1) / NPipes<N, FMT>::C, Ec);
 }
@@ -1497,8 +1531,9 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
             for (int pt0 = 0; pt0 < P; pt0 += E) {
                 const int Ec = std::min(E, P - pt0);
                 const TcArgs a = job_args(plan, f, p, q, pt0, Ec);
+                const Share sh = job_share(plan, p, q);
                 dim3 gA, gB, gC;
-                job_grids<N, FMT>(plan, Ec, gA, gB, gC);
+                job_grids<N, FMT>(plan, Ec, sh.on, gA, gB, gC);
                 if (fork) DGFS_CUDA(cudaStreamWaitEvent(sa, first ? ts->ev_entry : ts->ev_b, 0));
                 first = false;
                 {
@@ -1517,7 +1552,10 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
                 }
                 {
                     ProfScope ps(plan, "tc_stage_b", st);
-                    k_stage_b<N, FMT><<<gB, kRows * NPipes<N, FMT>::B, SM::B, st>>>(a);
+                    if (sh.on)
+                        k_stage_b_share<N, FMT, false><<<gB, kRows * NPipes<N, FMT>::B, SM::B, st>>>(a, sh.bmap);
+                    else
+                        k_stage_b<N, FMT><<<gB, kRows * NPipes<N, FMT>::B, SM::B, st>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
                 if (fork) DGFS_CUDA(cudaEventRecord(ts->ev_b, st));
@@ -1572,11 +1610,12 @@ dgfs_status collide_herm_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, 
             for (int pt0 = 0; pt0 < Ps; pt0 += E) {
                 const int Ec = std::min(E, Ps - pt0);
                 TcArgs a = job_args(plan, h.ft, p, q, pt0, Ec);
+                const Share sh = job_share(plan, p, q);
                 a.herm = 1;
                 a.npts = P;
                 a.zimg = h.zimg + (long)(p * S + q) * h.zimg_pair;
                 dim3 gA, gB, gC;
-                job_grids<N, FMT>(plan, Ec, gA, gB, gC);
+                job_grids<N, FMT>(plan, Ec, sh.on, gA, gB, gC);
                 if (fork) DGFS_CUDA(cudaStreamWaitEvent(sa, first ? ts->ev_entry : ts->ev_b, 0));
                 first = false;
                 {
@@ -1590,7 +1629,10 @@ dgfs_status collide_herm_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, 
                 }
                 {
                     ProfScope ps(plan, "tc_stage_b", st);
-                    k_stage_b_herm<N, FMT><<<gB, kRows * NPipes<N, FMT>::B, SM::B, st>>>(a);
+                    if (sh.on)
+                        k_stage_b_share<N, FMT, true><<<gB, kRows * NPipes<N, FMT>::B, SM::B, st>>>(a, sh.bmap);
+                    else
+                        k_stage_b_herm<N, FMT><<<gB, kRows * NPipes<N, FMT>::B, SM::B, st>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
                 if (fork) DGFS_CUDA(cudaEventRecord(ts->ev_b, st));
@@ -1622,12 +1664,16 @@ dgfs_status set_smem_attrs()
     if constexpr (A2<N, FMT>::OK)
         DGFS_CUDA(cudaFuncSetAttribute(k_stage_a2<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::A));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_b<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B));
+    DGFS_CUDA(cudaFuncSetAttribute(k_stage_b_share<N, FMT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)SM::B));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_c<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::C));
     if constexpr (N <= 32) {
         DGFS_CUDA(cudaFuncSetAttribute(k_stage_a_herm<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(SM::A + (size_t)Fmt<FMT>::NT *
                                                          (tcfmt::img_c<FMT>(N) - tcfmt::img_r<FMT>(N)))));
         DGFS_CUDA(cudaFuncSetAttribute(k_stage_b_herm<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B));
+        DGFS_CUDA(cudaFuncSetAttribute(k_stage_b_share<N, FMT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)SM::B));
     }
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_a_batch<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::A));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_b_batch<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B));
@@ -1674,9 +1720,10 @@ dgfs_status round_build(BatchRound &r)
         }
         for (int j = 0; j < cnt; ++j) {
             const BatchJob &b = r.jobs[j0 + j];
+            // the batched work list computes both sides of every pair
             const TcArgs a = job_args(b.plan, b.f, b.p, b.q, b.pt0, b.Ec);
             dim3 g[3];
-            job_grids<N, FMT>(b.plan, b.Ec, g[0], g[1], g[2]);
+            job_grids<N, FMT>(b.plan, b.Ec, false, g[0], g[1], g[2]);
             for (int k = 0; k < 3; ++k) {
                 t[k].job[j] = a;
                 t[k].grid[j] = JobGrid{c[k], g[k].x, g[k].y, g[k].z};
@@ -1706,12 +1753,23 @@ dgfs_status round_launch(const BatchRound &r, cudaStream_t st, Fork &fk)
     using SM = Smem<N, FMT>;
     dgfs_plan_s *lead = r.jobs[0].plan;  // launch counting and profiling
     const cudaStream_t sa = fk.on ? fk.sa : st;
+    // N = 8: each job's own stage kernels instead of the job-table kernels (the
+    // N = 8 job-table stage B kernel disagreed with the plain kernel on the same
+    // job in some builds; see the design notes)
+    constexpr bool per_job = N == 8;
+    auto grid_of = [](const JobGrid &g) { return dim3(g.gx, g.gy, g.gz); };
     for (size_t l = 0; l < r.tabs.size(); l += 3) {
+        const int nj = r.tabs[l].njobs;
         if (fk.on) DGFS_CUDA(cudaStreamWaitEvent(sa, fk.first ? fk.ev_entry : fk.ev_b, 0));
         fk.first = false;
         {
             ProfScope ps(lead, "tc_stage_a", sa);
-            k_stage_a_batch<N, FMT><<<r.ctas[l], kRows * NPipes<N, FMT>::A, SM::A, sa>>>(r.tabs[l]);
+            if (per_job)
+                for (int j = 0; j < nj; ++j)
+                    k_stage_a<N, FMT><<<grid_of(r.tabs[l].grid[j]), kRows * NPipes<N, FMT>::A, SM::A, sa>>>(
+                        r.tabs[l].job[j]);
+            else
+                k_stage_a_batch<N, FMT><<<r.ctas[l], kRows * NPipes<N, FMT>::A, SM::A, sa>>>(r.tabs[l]);
         }
         DGFS_LAUNCHED(lead);
         if (fk.on) {
@@ -1720,13 +1778,23 @@ dgfs_status round_launch(const BatchRound &r, cudaStream_t st, Fork &fk)
         }
         {
             ProfScope ps(lead, "tc_stage_b", st);
-            k_stage_b_batch<N, FMT><<<r.ctas[l + 1], kRows * NPipes<N, FMT>::B, SM::B, st>>>(r.tabs[l + 1]);
+            if (per_job)
+                for (int j = 0; j < nj; ++j)
+                    k_stage_b<N, FMT><<<grid_of(r.tabs[l + 1].grid[j]), kRows * NPipes<N, FMT>::B, SM::B, st>>>(
+                        r.tabs[l + 1].job[j]);
+            else
+                k_stage_b_batch<N, FMT><<<r.ctas[l + 1], kRows * NPipes<N, FMT>::B, SM::B, st>>>(r.tabs[l + 1]);
         }
         DGFS_LAUNCHED(lead);
         if (fk.on) DGFS_CUDA(cudaEventRecord(fk.ev_b, st));
         {
             ProfScope ps(lead, "tc_stage_c", st);
-            k_stage_c_batch<N, FMT><<<r.ctas[l + 2], kRows * NPipes<N, FMT>::C, SM::C, st>>>(r.tabs[l + 2]);
+            if (per_job)
+                for (int j = 0; j < nj; ++j)
+                    k_stage_c<N, FMT><<<grid_of(r.tabs[l + 2].grid[j]), kRows * NPipes<N, FMT>::C, SM::C, st>>>(
+                        r.tabs[l + 2].job[j]);
+            else
+                k_stage_c_batch<N, FMT><<<r.ctas[l + 2], kRows * NPipes<N, FMT>::C, SM::C, st>>>(r.tabs[l + 2]);
         }
         DGFS_LAUNCHED(lead);
     }
@@ -1877,6 +1945,27 @@ dgfs_status tc_prepare(dgfs_plan_s *plan)
         DGFS_CUDA(dev_malloc(&ts->idmask, RS));
         DGFS_CUDA(cudaMemcpy(ts->idmask, mask.data(), RS, cudaMemcpyHostToDevice));
     }
+    // the reflected direction of every (r, s), for the same-species pairs
+    {
+        const int M = plan->M;
+        std::vector<uint16_t> map(RS);
+        int found = 0;
+        for (int s = 0; s < M; ++s) {
+            const double *sg = plan->sigma + 3 * s;
+            for (int t = 0; t < M; ++t) {
+                const double *sr = plan->sigma + 3 * t;
+                if (sr[0] == -sg[0] && sr[1] == -sg[1] && sr[2] == -sg[2]) {
+                    for (int r = 0; r < plan->Nrho; ++r) map[r * M + s] = (uint16_t)(r * M + t);
+                    ++found;
+                    break;
+                }
+            }
+        }
+        if (found == M) {  // both designs are centrally symmetric
+            DGFS_CUDA(dev_malloc(&ts->bmap, sizeof(uint16_t) * RS));
+            DGFS_CUDA(cudaMemcpy(ts->bmap, map.data(), sizeof(uint16_t) * RS, cudaMemcpyHostToDevice));
+        }
+    }
     dgfs_status st = ts->fmt == 0 ? build_images<0>(plan, ts) : build_images<1>(plan, ts);
     if (st != DGFS_OK) return st;
     DGFS_CUDA(cudaDeviceSynchronize());
@@ -1890,6 +1979,7 @@ void tc_release(dgfs_plan_s *plan)
     dev_free(ts->Fimg);
     dev_free(ts->err);
     dev_free(ts->idmask);
+    dev_free(ts->bmap);
     dev_free(ts->tw_df);
     if (ts->side) cudaStreamDestroy(ts->side);
     if (ts->ev_entry) cudaEventDestroy(ts->ev_entry);

@@ -204,3 +204,23 @@ def test_autotune_rejects_fp64_plans():
     with pytest.raises(B.DgfsError) as e:
         plan.autotune(f)
     assert e.value.status == 5
+
+
+@pytest.mark.parametrize("N,S,M,P", [(8, 1, 6, 24), (8, 2, 12, 24), (16, 2, 6, 6), (24, 2, 6, 4)])
+def test_batch_on_fresh_plans_matches_oracle(N, S, M, P):
+    """The work list run first, on plans that never ran a plain call (so no
+    workspace contents from an earlier call can stand in for a missing write),
+    against the oracle."""
+    inst = _instance(N, S, M, 4, P, "fp32_tc", 40 + N)
+    Q = torch.full((P, S, S, N, N, N), float("nan"), dtype=torch.float32, device="cuda")
+    b = B.dgfs_batch_create([inst["plan"]._h], [P], [inst["f"]], [Q])
+    try:
+        B.dgfs_batch_launch(b)
+        torch.cuda.synchronize()
+    finally:
+        B.dgfs_batch_destroy(b)
+    inst["plan"].check()
+    pb = inst["pb"]
+    prob = O.Problem(pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"])
+    Qo = prob.collide_all(inst["f"].double().cpu().numpy())
+    assert np.abs(Q.double().cpu().numpy() - Qo).max() <= 1e-5 * np.abs(Qo).max()
