@@ -26,7 +26,9 @@ Prints ONE JSON line (rank 0).  Fields beyond the base contract:
   graph        the same call replayed from one CUDA graph,
   dg_step      one SSP-RK3 step of the 1-D DG heat-transfer slab,
   uneven_batch 256 uneven relaxation problems: separate calls, a graph of them,
-               and the batched work list (eager and captured).
+               and the batched work list (eager and captured),
+  adjoint      the FP64 backward on the 64-point adjoint workload against its forward,
+  tensor_peaks the tensor pipe's tf32 and bf16 issue rates measured by the library's probe.
 
 --impl reference times the FP64 CPU oracle (the only reference that exists:
 the paper publishes no code) on a bounded sample of the same workload.
@@ -287,14 +289,15 @@ def run_ours(args, rank, world):
     roof["share_of_step"] = tot_ms / sum(v[1] for v in prof.values())
     roof["timing"] = ("CUDA events around each launch in a %d-step pass right after the timed region "
                       "(the library then issues the plan's launches in one stream)" % rec["profile_steps"])
-    roof["traffic"], roof["traffic_source"] = ncu_traffic(name, P)
+    ppl = min(P, int(info["chunk"])) if not name.startswith("fp64") else None
+    roof["traffic"], roof["traffic_source"] = ncu_traffic(name, P, ppl)
     # DRAM traffic of the three stage kernels per step against the step's
     # algorithmic bytes (f in, Q out, the b tables once): the cost of the
     # per-(r, s) intermediates that pass through HBM
     if not name.startswith("fp64"):
         tsum = 0.0
-        for k in NCU_TRAFFIC_8PT:
-            t, _ = ncu_traffic(k, P)
+        for k in NCU_TRAFFIC_24PT:
+            t, _ = ncu_traffic(k, P, ppl)
             if t is None or k not in prof:
                 tsum = None
                 break
@@ -377,6 +380,43 @@ def run_ours(args, rank, world):
                           "collision_evals_per_step": nev, "evals_per_s": nev / (dms / 1e3),
                           "transport_kernel_ms_per_step": tr, "collision_kernel_ms_per_step": co}
         del slab, splan
+
+    # the adjoint on the adjoint workload (64 points x 2 species x 32^3): one
+    # dgfs_collide_backward of the FP64 plan (the only form with an adjoint)
+    # against one forward call of the same plan, and the 3xTF32 forward that
+    # the autograd wrapper pairs with it
+    if not args.no_adjoint:
+        ap = W.make_problem("c4_adjoint_n32")
+        Pa = ap["f"].shape[0]
+        p64 = B.Plan(ap["N"], ap["L"], ap["M"], ap["Nrho"], ap["masses"], ap["pairs"], "fp64", Pa, dev)
+        fa = torch.from_numpy(ap["f"]).to("cuda", torch.float64)
+        ga = torch.from_numpy(np.random.default_rng(4).normal(size=(Pa, S, S) + fa.shape[2:])).to("cuda")
+        Qa = p64.collide(fa)
+        p64.backward(fa, ga)
+        torch.cuda.synchronize()
+
+        def tev(fn, reps=2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        t_f = tev(lambda: p64.collide(fa, Qa))
+        t_b = tev(lambda: p64.backward(fa, ga))
+        ptc = B.Plan(ap["N"], ap["L"], ap["M"], ap["Nrho"], ap["masses"], ap["pairs"], "fp32_tc", Pa, dev)
+        fa32 = fa.float()
+        Qt = ptc.collide(fa32)
+        torch.cuda.synchronize()
+        t_t = tev(lambda: ptc.collide(fa32, Qt), reps=5)
+        ne = Pa * S * S
+        out["adjoint"] = {"workload": "c4_adjoint_n32: 64 points, 2 species (m = 1, 2), N = 32, M = 12, N_rho = 8",
+                          "fp64_forward_ms": t_f, "fp64_backward_ms": t_b, "backward_over_forward": t_b / t_f,
+                          "fp64_backward_evals_per_s": ne / (t_b / 1e3), "fp32_tc_forward_ms": t_t,
+                          "note": "the backward runs on an FP64 plan (tensor-core plans have no adjoint)"}
+        del p64, ptc
 
     # end to end through the host-buffer C-ABI call (pinned host memory)
     if not args.no_e2e:
@@ -610,19 +650,21 @@ def tc_executed_flops(name, info, P, S, RS, sigma=None):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the stage kernels of the
-# 3xTF32 form at N = 32, M = 12, N_rho = 8 from one ncu capture on 8 points (one species
-# pair per launch); A', B' and H are per point, so the bytes scale with the points per launch.
-NCU_TRAFFIC_8PT = {"tc_stage_a": 351.4e6, "tc_stage_b": 574.7e6, "tc_stage_c": 229.9e6}
+# 3xTF32 form on the slab workload, averaged over the four species-pair launches of one
+# call, from a one-pass ncu capture at 24 points per launch (profiles/launches_c2_slab_n32_fp32_tc.md;
+# stage A and B launches of the same-species pairs move about half of the others).
+# A', B' and H are per point, so a launch over fewer points moves proportionally less.
+NCU_TRAFFIC_24PT = {"tc_stage_a": 0.858e9, "tc_stage_b": 1.488e9, "tc_stage_c": 0.700e9}
 
 
-def ncu_traffic(name, P):
+def ncu_traffic(name, P, points_per_launch=None):
     """(bytes per launch, where the figure comes from), or (None, reason)."""
-    if WORKLOAD != "c2_slab_n32" or name not in NCU_TRAFFIC_8PT:
+    if WORKLOAD != "c2_slab_n32" or name not in NCU_TRAFFIC_24PT:
         return None, "no ncu capture of this kernel"
-    return (NCU_TRAFFIC_8PT[name] * min(P, 24) / 8.0,
-            "not measured in this run: ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch captured "
-            "on 8 points, scaled by %d/8 points per launch (the per-(r, s) intermediates scale with the points)"
-            % min(P, 24))
+    E = min(P, 24) if points_per_launch is None else points_per_launch
+    return (NCU_TRAFFIC_24PT[name] * E / 24.0,
+            "not measured in this run: one-pass ncu dram__bytes_read.sum + dram__bytes_write.sum at 24 points "
+            "per launch, averaged over the species pairs%s" % ("" if E == 24 else ", scaled by %d/24 points" % E))
 
 
 def step_algorithmic_bytes(N, P, S, RS, es=4):
@@ -728,6 +770,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-hermitian", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--points", type=int, default=None,
                     help="evaluate only the first POINTS spatial points (small cases for profiling)")
