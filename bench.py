@@ -26,7 +26,9 @@ Prints ONE JSON line (rank 0).  Fields beyond the base contract:
   graph        the same call replayed from one CUDA graph,
   dg_step      one SSP-RK3 step of the 1-D DG heat-transfer slab,
   uneven_batch 256 uneven relaxation problems: separate calls, a graph of them,
-               and the batched work list (eager and captured),
+               the batched rounds (eager and captured) and the batch as one
+               work-list launch per N group,
+  schedules    the benchmark call with per-stage launches and as one work-list launch,
   adjoint      the FP64 backward on the 64-point adjoint workload against its forward,
   tensor_peaks the tensor pipe's tf32 and bf16 issue rates measured by the library's probe.
 
@@ -318,6 +320,29 @@ def run_ours(args, rank, world):
     out["step_ms_p10_p50_p90"] = rec["step_ms_p10_p50_p90"]
     out["clocks"] = rec["clocks"]
 
+    # the two stage schedules of the tensor-core call (the autotuner keeps the
+    # faster): per-stage launches on two streams, and one work-list launch
+    if main != "fp64" and int(info["N"]) in (24, 32, 48) and not args.no_graph:
+        chosen = plan.schedule()
+        sch = {"chosen": chosen}
+        for mode in (0, 1):
+            plan.set_schedule(mode)
+            for _ in range(2):
+                plan.collide(rec["f"], rec["Q"])
+            torch.cuda.synchronize()
+            sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+            for a, b in sev:
+                flush.zero_()
+                a.record(stream)
+                plan.collide(rec["f"], rec["Q"])
+                b.record(stream)
+            torch.cuda.synchronize()
+            t = sorted(a.elapsed_time(b) for a, b in sev)[5]
+            sch["launches" if mode == 0 else "work_list"] = {"ms_per_step": t, "evals_per_s": evals / (t / 1e3)}
+        plan.set_schedule(chosen)
+        plan.check()
+        out["schedules"] = sch
+
     # the same call replayed from one CUDA graph: the host-side scheduling cost
     if not args.no_graph:
         g = B.dgfs_graph_capture([plan._h], [P], [rec["f"]], [rec["Q"]])
@@ -590,6 +615,12 @@ def uneven_batch(B, W, torch, np, prec, dev, flush, stream, plan, rec, count=256
         B.dgfs_graph_destroy(g)
     bt = B.Batch(plans, fs, Qs, dt)
     try:
+        bt.set_schedule(1)
+        t = timed(lambda: bt.launch(stream))
+        res["batch_work_list"] = {"ms_per_pass": t, "evals_per_s": evals / (t / 1e3),
+                                  "alg_tflops": aflops / (t / 1e3) / 1e12,
+                                  "launches": launches(lambda: bt.launch(stream))}
+        bt.set_schedule(0)
         t = timed(lambda: bt.launch(stream))
         res["batch"] = {"ms_per_pass": t, "evals_per_s": evals / (t / 1e3), "alg_tflops": aflops / (t / 1e3) / 1e12,
                         "launches": launches(lambda: bt.launch(stream))}
@@ -640,12 +671,17 @@ def tc_executed_flops(name, info, P, S, RS, sigma=None):
         live = [sum(1 for v in sg if v[d] != 0.0) / len(sg) for d in range(3)]
         if N > 32:  # stage A skips the z-pass only where a row's z-pencil fits its prefetch registers
             live[2] = 1.0
+    # translate sides stage A computes per step: same-species pairs compute the
+    # A side only (their B side is the A side at the reflected direction)
+    sides = 2 * S * S - S
     if name == "tc_stage_a":
-        return S * S * P * planes * RS * 2 * (live[2] * gem(KR) + live[1] * gem(KC))
+        return sides * P * planes * RS * (live[2] * gem(KR) + live[1] * gem(KC))
     if name == "tc_stage_b":
         return S * S * P * (-(-N * N // 128)) * RS * (2 * live[0] + 1) * gem(KC)
     if name == "tc_stage_c":
         return S * S * P * planes * RS * 2 * gem(KC)
+    if name == "tc_worklist":  # one launch runs all three stages
+        return sum(tc_executed_flops(k, info, P, S, RS, sigma) for k in ("tc_stage_a", "tc_stage_b", "tc_stage_c"))
     return None
 
 
@@ -688,7 +724,8 @@ def tc_algorithmic_flops(name, N, P, S, RS):
     multiply-accumulate with w b (2 passes + 8 N^3); the 9 passes are the 3 x 3-D
     transforms of the (r, s) step of Algorithm 2."""
     a = alg_axis_flops(N)
-    per = {"tc_stage_a": 4 * a, "tc_stage_b": 3 * a + 6.0 * N ** 3, "tc_stage_c": 2 * a + 8.0 * N ** 3}.get(name)
+    per = {"tc_stage_a": 4 * a, "tc_stage_b": 3 * a + 6.0 * N ** 3, "tc_stage_c": 2 * a + 8.0 * N ** 3,
+           "tc_worklist": 9 * a + 14.0 * N ** 3}.get(name)
     return None if per is None else S * S * P * RS * per
 
 

@@ -246,10 +246,13 @@ dgfs_status dgfs_graph_destroy(dgfs_graph graph);
  * tensor-core plans) into Q_dev[i] ([P[i]][S][S][N^3]) exactly as
  * dgfs_collide would; with dt != 0 each launch then applies
  * dgfs_relax_step(plans[i], P[i], f_dev[i], Q_dev[i], dt).  The tensor-core
- * instances that share N and the operand format run their stages together:
- * round k launches each stage once over the k-th (species pair, chunk of
- * points) job of every such instance, each CTA finding its job in a device
- * table; FP64 instances run their own collision call.  The pointers are fixed
+ * instances that share N and the operand format run their stages together.
+ * Their jobs (species pair, chunk of points) form rounds: round k holds the
+ * k-th job of every such instance.  By default each stage is launched once
+ * per round over all its jobs, each CTA finding its job in a device table;
+ * with dgfs_batch_set_schedule(batch, 1) a group of N = 24, 32 or 48 runs all
+ * its rounds in one work-list launch instead (see dgfs_plan_set_schedule).
+ * FP64 instances run their own collision call.  The pointers are fixed
  * at creation (their contents may change between launches); plans must be
  * distinct, on one device, not used elsewhere while the batch runs, and
  * destroyed only after the batch.  A plan
@@ -265,6 +268,15 @@ dgfs_status dgfs_batch_create(int count, const dgfs_plan *plans, const int *P, v
 /* Enqueue one pass of the batch on `stream` (asynchronous; capturable into a
  * CUDA graph).  Errors: EINVAL (NULL or stale batch), ECUDA. */
 dgfs_status dgfs_batch_launch(dgfs_batch batch, void *stream);
+
+/* How the batch's tensor-core groups run (Sec. 2.2 batches the M N_rho
+ * transforms of a point; Sec. 3.3 makes every (point, pair) evaluation
+ * independent, so any order of the jobs is the same computation):
+ *   0  per-stage launches, one round of jobs at a time (two streams; default);
+ *   1  one work-list launch per group of N = 24, 32, 48.
+ * Both give the same bits.  Takes effect at the next dgfs_batch_launch.
+ * Errors: EINVAL (NULL batch or mode not 0 or 1). */
+dgfs_status dgfs_batch_set_schedule(dgfs_batch batch, int mode);
 
 /* Release a batch (synchronises its device).  NULL is accepted. */
 dgfs_status dgfs_batch_destroy(dgfs_batch batch);
@@ -289,6 +301,41 @@ dgfs_status dgfs_plan_autotune(dgfs_plan plan, int P, const void *f_dev, void *Q
  * fit and keeps the fastest.  Errors: EINVAL, EUNSUPPORTED (FP64 plan, or the
  * variant does not fit N). */
 dgfs_status dgfs_plan_set_kernel_variant(dgfs_plan plan, int variant);
+
+/* Tensor-core plans: how dgfs_collide runs the stages of Algorithm 2's
+ * (r, s) loop for its jobs (a job: one species pair and chunk of points):
+ *   0  one launch per stage and job; the next job's first stage overlaps the
+ *      current job's last on a second stream (default);
+ *   1  one work-list launch per call (N = 24, 32, 48): CTAs claim tasks (one
+ *      CTA's share of a stage for a job, or a slice of the partial sums) from
+ *      a device-side queue in which every task comes after the tasks it reads
+ *      from, wait (bounded) on per-job counters for them, run the stage body
+ *      and publish their completion; a CTA keeps claiming while the tasks are
+ *      of its stage and hands a task of another stage on to a fresh CTA.
+ *      Uses the default first-stage kernel variant.
+ * Both give the same bits (the same stage bodies on the same data).
+ * dgfs_plan_autotune also times mode 1 and keeps it where it is faster.
+ * Changing the schedule makes batches built on the plan stale.  The plan's
+ * mode is read back with dgfs_plan_get_schedule.  Errors: EINVAL (mode not 0
+ * or 1), EUNSUPPORTED (FP64 plan, or mode 1 with another N). */
+dgfs_status dgfs_plan_set_schedule(dgfs_plan plan, int mode);
+dgfs_status dgfs_plan_get_schedule(dgfs_plan plan, int *mode);
+
+/* Instrumentation of the work-list schedule (no counterpart in the paper):
+ * while trace_dev (device memory of `bytes` bytes, caller-owned) is set,
+ * every work-list launch records per task four 64-bit words at
+ * trace_dev[4 * task]: the global timer (ns) when a CTA took the task, when
+ * its dependencies were met and when it ended, and (SM id << 8 | stage, 0-3 =
+ * A, B, C, partial sums).  Tasks past bytes / 32 are not recorded; each launch
+ * overwrites the buffer from task 0.  NULL switches the trace off.  Process-wide,
+ * not thread-safe.  Always returns OK. */
+dgfs_status dgfs_debug_worklist_trace(void *trace_dev, size_t bytes);
+
+/* Instrumentation of the work-list schedule: the (r, s) per wave of its queue
+ * (rounded up to whole radial nodes; default 12), for the work lists built
+ * afterwards (every call in plan mode, at creation for batches).
+ * Process-wide.  Errors: EINVAL (rs_per_wave < 1). */
+dgfs_status dgfs_debug_worklist_chunk(int rs_per_wave);
 
 /* Declared variant (not the paper's literal Algorithm 2): the Hermitian form.
  * Algorithm 1's wavenumber map gives index N/2 the wavenumber -N/2, which has

@@ -71,6 +71,11 @@ def lib():
             "dgfs_plan_profile_read": (i, [_P, i, _P, _P, _P, ctypes.POINTER(i)]),
             "dgfs_plan_set_collapse": (i, [_P, i]),
             "dgfs_plan_set_kernel_variant": (i, [_P, i]),
+            "dgfs_plan_set_schedule": (i, [_P, i]),
+            "dgfs_plan_get_schedule": (i, [_P, ctypes.POINTER(i)]),
+            "dgfs_batch_set_schedule": (i, [_P, i]),
+            "dgfs_debug_worklist_trace": (i, [_P, ctypes.c_size_t]),
+            "dgfs_debug_worklist_chunk": (i, [i]),
             "dgfs_plan_set_hermitian": (i, [_P, i]),
             "dgfs_dealias_work_bytes": (i, [_P, i, i, ctypes.POINTER(ctypes.c_size_t)]),
             "dgfs_collide_dealiased": (i, [_P, i, i, _P, _P, _P, ctypes.c_size_t, _P]),
@@ -231,6 +236,32 @@ def dgfs_plan_set_hermitian(h, enable):
 
 def dgfs_plan_set_kernel_variant(h, variant):
     _check(lib().dgfs_plan_set_kernel_variant(h, int(variant)), "dgfs_plan_set_kernel_variant")
+
+
+def dgfs_plan_set_schedule(h, mode):
+    _check(lib().dgfs_plan_set_schedule(h, int(mode)), "dgfs_plan_set_schedule")
+
+
+def dgfs_plan_get_schedule(h):
+    v = ctypes.c_int(0)
+    _check(lib().dgfs_plan_get_schedule(h, ctypes.byref(v)), "dgfs_plan_get_schedule")
+    return int(v.value)
+
+
+def dgfs_debug_worklist_trace(buf):
+    """buf: a CUDA int64 tensor of 4 words per task to record, or None (off)."""
+    if buf is None:
+        _check(lib().dgfs_debug_worklist_trace(None, 0), "dgfs_debug_worklist_trace")
+    else:
+        _check(lib().dgfs_debug_worklist_trace(_ptr(buf), buf.numel() * 8), "dgfs_debug_worklist_trace")
+
+
+def dgfs_debug_worklist_chunk(rs_per_wave):
+    _check(lib().dgfs_debug_worklist_chunk(int(rs_per_wave)), "dgfs_debug_worklist_chunk")
+
+
+def dgfs_batch_set_schedule(h, mode):
+    _check(lib().dgfs_batch_set_schedule(h, int(mode)), "dgfs_batch_set_schedule")
 
 
 def dgfs_dealias_work_bytes(h, P, N):
@@ -419,6 +450,13 @@ class Plan:
     def set_kernel_variant(self, variant):
         dgfs_plan_set_kernel_variant(self._h, variant)
 
+    def set_schedule(self, mode):
+        """0: one launch per stage and job; 1: one persistent work-list launch."""
+        dgfs_plan_set_schedule(self._h, mode)
+
+    def schedule(self):
+        return dgfs_plan_get_schedule(self._h)
+
     def collide_dealiased(self, f, N, Q=None, work=None):
         """Linear-convolution operator on the N grid (this plan is built at 3N/2)."""
         if not (f.is_cuda and f.dtype == self.dtype and f.is_contiguous() and f.shape[2:] == (N, N, N)):
@@ -468,6 +506,10 @@ class Batch:
 
     def launch(self, stream=None):
         dgfs_batch_launch(self._h, stream)
+
+    def set_schedule(self, mode):
+        """0: per-stage launches per round; 1: persistent work lists (default)."""
+        dgfs_batch_set_schedule(self._h, mode)
 
     def close(self):
         if getattr(self, "_h", None):

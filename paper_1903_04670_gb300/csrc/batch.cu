@@ -229,6 +229,12 @@ dgfs_status dgfs_batch_launch(dgfs_batch b, void *stream)
     return DGFS_OK;
 }
 
+dgfs_status dgfs_batch_set_schedule(dgfs_batch b, int mode)
+{
+    if (!b) return DGFS_EINVAL;
+    return tc_batch_set_schedule(b->tc, mode);
+}
+
 dgfs_status dgfs_batch_destroy(dgfs_batch b)
 {
     if (!b) return DGFS_OK;

@@ -446,6 +446,32 @@ dgfs_status dgfs_plan_set_kernel_variant(dgfs_plan plan, int variant)
     return tc_set_variant(plan, variant);
 }
 
+dgfs_status dgfs_plan_set_schedule(dgfs_plan plan, int mode)
+{
+    if (!plan) return DGFS_EINVAL;
+    return tc_set_schedule(plan, mode);
+}
+
+dgfs_status dgfs_debug_worklist_trace(void *trace_dev, size_t bytes)
+{
+    tc_debug_worklist_trace(trace_dev, bytes);
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_debug_worklist_chunk(int rs_per_wave)
+{
+    if (rs_per_wave < 1) return DGFS_EINVAL;
+    tc_debug_worklist_chunk(rs_per_wave);
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_plan_get_schedule(dgfs_plan plan, int *mode)
+{
+    if (!plan || !mode) return DGFS_EINVAL;
+    *mode = tc_schedule(plan);
+    return DGFS_OK;
+}
+
 dgfs_status dgfs_plan_set_collapse(dgfs_plan plan, int enable)
 {
     if (!plan) return DGFS_EINVAL;

@@ -171,6 +171,11 @@ bool tc_herm_supported(const dgfs_plan_s *plan);
 dgfs_status tc_herm_build(dgfs_plan_s *plan);
 size_t fp64_herm_bytes(const dgfs_plan_s *plan);
 dgfs_status tc_set_variant(dgfs_plan_s *plan, int variant);
+dgfs_status tc_set_schedule(dgfs_plan_s *plan, int mode);
+int tc_schedule(const dgfs_plan_s *plan);
+dgfs_status tc_batch_set_schedule(void *batch, int mode);
+void tc_debug_worklist_trace(void *buf, size_t bytes);
+void tc_debug_worklist_chunk(int rs);
 dgfs_status tc_batch_build(int count, dgfs_plan_s *const *plans, const int *P, void *const *f, void *const *Q,
                            void **out);
 dgfs_status tc_batch_launch(void *batch, cudaStream_t st);

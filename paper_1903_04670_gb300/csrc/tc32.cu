@@ -71,6 +71,12 @@ struct TcState {
     // current one drains (it only has to wait for stage B to have read A', B')
     cudaStream_t side = nullptr;
     cudaEvent_t ev_entry = nullptr, ev_a = nullptr, ev_b = nullptr;
+    // 1: every stage of a call runs in one work-list launch
+    // (k_worklist) instead of one launch per stage and job
+    int sched = 0;
+    int sms = 148;
+    uint32_t *wl_ctr = nullptr;  // dependency counters of the work list
+    size_t wl_words = 0;
 };
 
 struct TcArgs {
@@ -251,10 +257,23 @@ __device__ __forceinline__ void copy_terms(uint8_t *dst, int dstride, const uint
     for (int t = 0; t < terms; ++t) bulk_g2s(dst + t * dstride, src + t * sstride, bytes, mbar);
 }
 
-// Allocate ncols TMEM columns for the CTA and initialise `nb` mbarriers.
-__device__ __forceinline__ void cta_setup(uint32_t *slot, uint32_t ncols, uint64_t *mb, int nb)
+// A stage body run as one task of the work list (k_worklist): the CTA, which
+// may run several tasks, allocated all of TMEM once, at its start, and its
+// mbarriers are initialised per task and invalidated after it.
+struct Persist {
+    uint32_t tmem;  // TMEM base address of the CTA's allocation
+};
+
+// Allocate ncols TMEM columns for the CTA (or take the work-list CTA's
+// allocation) and initialise `nb` mbarriers.
+__device__ __forceinline__ void cta_setup(uint32_t *slot, uint32_t ncols, uint64_t *mb, int nb,
+                                          const Persist *ps = nullptr)
 {
-    if (threadIdx.x < 32) tmem_alloc(slot, ncols);
+    if (ps) {
+        if (threadIdx.x == 0) *slot = ps->tmem;
+    } else if (threadIdx.x < 32) {
+        tmem_alloc(slot, ncols);
+    }
     if (threadIdx.x == 0)
         for (int i = 0; i < nb; ++i) mbar_init(mb + i, 1);
     fence_before();
@@ -262,12 +281,18 @@ __device__ __forceinline__ void cta_setup(uint32_t *slot, uint32_t ncols, uint64
     fence_after();
 }
 
-__device__ __forceinline__ void cta_teardown(uint32_t tb, uint32_t ncols, bool ok, int *err)
+__device__ __forceinline__ void cta_teardown(uint32_t tb, uint32_t ncols, bool ok, int *err, uint64_t *mb = nullptr,
+                                             int nb = 0, const Persist *ps = nullptr)
 {
     if (!ok) atomicExch(err, kErrTimeout);
     fence_before();
     __syncthreads();
-    if (threadIdx.x < 32) tmem_dealloc(tb, ncols);
+    if (ps) {
+        if (threadIdx.x == 0)
+            for (int i = 0; i < nb; ++i) mbar_inval(mb + i);
+    } else if (threadIdx.x < 32) {
+        tmem_dealloc(tb, ncols);
+    }
 }
 
 // Pipelines per CTA: each pipeline is 128 threads with its own data operand,
@@ -299,7 +324,8 @@ template <int N, int FMT> struct Smem {
 // (real input), an in-plane transpose through shared memory, y-pass, result A'
 // or B' to global.
 template <int N, int FMT, bool HC = false>
-__device__ __forceinline__ void k_stage_a_body(const TcArgs &a, const uint3 bid, const uint3 gdim)
+__device__ __forceinline__ bool k_stage_a_body(const TcArgs &a, const uint3 bid, const uint3 gdim,
+                                               const Persist *ps = nullptr)
 {
     using SM = Smem<N, FMT>;
     constexpr int NP = NPipes<N, FMT>::A, NT = SM::NT, AB = SM::AB, IR = SM::IR, IC = SM::IC;
@@ -330,7 +356,7 @@ __device__ __forceinline__ void k_stage_a_body(const TcArgs &a, const uint3 bid,
     // thread then loads its own row's z-pencil (needs N / 4 <= FPT float4)
     constexpr bool ZSKIP = N % 4 == 0 && N / 4 <= FPT;
     const bool ident_z = ZSKIP && a.idmask && (a.idmask[rs] & 4);
-    cta_setup(&tslot, NCOL, mb, NP + 1);
+    cta_setup(&tslot, NCOL, mb, NP + 1, ps);
     const uint32_t tb = tslot + pp * 2 * NO, tl = lane_base(tb);
     uint32_t ph_mma = 0, ph_cp = 0;
     auto load_imgs = [&](int which) {  // 0: z, 1: y, 2: both
@@ -490,7 +516,8 @@ __device__ __forceinline__ void k_stage_a_body(const TcArgs &a, const uint3 bid,
             store_pair<8>(dstp + (long)(c0 / 2) * N, h, N, t < nval * N);
         });
     }
-    cta_teardown(tslot, NCOL, ok, a.err);
+    cta_teardown(tslot, NCOL, ok, a.err, mb, NP + 1, ps);
+    return ok;
 }
 
 template <int N, int FMT>
@@ -879,8 +906,8 @@ __global__ void __launch_bounds__(4 * kRows, 1) k_stage_a_ws(TcArgs a)
 // contraction); each of its NP pipelines loops over items (point e, tile of
 // 128 (y, z) pencils): H = F_x ((T^p_x A') . (T^q_x B')).
 template <int N, int FMT, bool HP = false, bool SH = false>
-__device__ __forceinline__ void k_stage_b_body(const TcArgs &a, const uint3 bid, const uint3 gdim,
-                                               const uint16_t *bmap = nullptr)
+__device__ __forceinline__ bool k_stage_b_body(const TcArgs &a, const uint3 bid, const uint3 gdim,
+                                               const uint16_t *bmap = nullptr, const Persist *ps = nullptr)
 {
     using SM = Smem<N, FMT>;
     constexpr int NP = NPipes<N, FMT>::B, NT = SM::NT, AB = SM::AB, IC = SM::IC;
@@ -898,7 +925,7 @@ __device__ __forceinline__ void k_stage_b_body(const TcArgs &a, const uint3 bid,
     const long n = a.n;
     const int items = a.Ec * NT_TILES;
     const bool ident_x = a.idmask && (a.idmask[rs] & 1);
-    cta_setup(&tslot, NCOL, mb, NP + 1);
+    cta_setup(&tslot, NCOL, mb, NP + 1, ps);
     const uint32_t tb = tslot + pp * 3 * NO, tl = lane_base(tb);
     uint32_t ph_mma = 0, ph_cp = 0;
     auto src_img = [&](int which) -> const uint8_t * {
@@ -1029,7 +1056,8 @@ __device__ __forceinline__ void k_stage_b_body(const TcArgs &a, const uint3 bid,
             store_pair<8>(dstp + (long)(c0 / 2) * NN, h, NN, valid);
         });
     }
-    cta_teardown(tslot, NCOL, ok, a.err);
+    cta_teardown(tslot, NCOL, ok, a.err, mb, NP + 1, ps);
+    return ok;
 }
 
 template <int N, int FMT>
@@ -1058,7 +1086,8 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b_share(T
 // cores and QG_part += w_rs b_rs . t3 in registers; the next (r, s)'s H tile
 // is prefetched into registers meanwhile.
 template <int N, int FMT>
-__device__ __forceinline__ void k_stage_c_body(const TcArgs &a, const uint3 bid, const uint3 gdim)
+__device__ __forceinline__ bool k_stage_c_body(const TcArgs &a, const uint3 bid, const uint3 gdim,
+                                               const Persist *ps = nullptr)
 {
     using SM = Smem<N, FMT>;
     constexpr int NP = NPipes<N, FMT>::C, NT = SM::NT, AB = SM::AB, IC = SM::IC;
@@ -1076,7 +1105,7 @@ __device__ __forceinline__ void k_stage_c_body(const TcArgs &a, const uint3 bid,
     const int x0 = bid.x * G, rb = bid.y * NP + pp, e = bid.z;
     const int nval = min(G, N - x0);
     const long n = a.n;
-    cta_setup(&tslot, NCOL, mb, NP + 1);
+    cta_setup(&tslot, NCOL, mb, NP + 1, ps);
     const uint32_t tb = tslot + pp * 2 * NO, tl = lane_base(tb);
     uint32_t ph_mma = 0, ph_cp = 0;
     if (threadIdx.x == 0) {
@@ -1207,7 +1236,8 @@ __device__ __forceinline__ void k_stage_c_body(const TcArgs &a, const uint3 bid,
         float2 *dstp = a.QGp + ((long)e * a.rsb + rb) * n + (long)(x0 + g) * NN + (yl & ~1);
         store_pair<N>(dstp, acc, N, t < nval * N);
     }
-    cta_teardown(tslot, NCOL, ok, a.err);
+    cta_teardown(tslot, NCOL, ok, a.err, mb, NP + 1, ps);
+    return ok;
 }
 
 template <int N, int FMT>
@@ -1278,10 +1308,8 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::C, 1) k_stage_c_batch(c
 }
 
 // QG[pt0 + e][k] = sum_rb QGp[e][rb][k]  (FP32 partials summed in double-float)
-__global__ void k_sum_partials(float4 *QG, const float2 *QGp, int rsb, long n, int pt0, int E)
+__device__ __forceinline__ void sum_partial(float4 *QG, const float2 *QGp, int rsb, long n, int pt0, long i)
 {
-    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long)E * n) return;
     const long e = i / n, k = i % n;
     dfl sx(0.f, 0.f), sy(0.f, 0.f);
     for (int rb = 0; rb < rsb; ++rb) {
@@ -1290,6 +1318,387 @@ __global__ void k_sum_partials(float4 *QG, const float2 *QGp, int rsb, long n, i
         sy = add_f(sy, v.y);
     }
     st_dcx(QG + (pt0 + e) * n + k, dcx{sx, sy});
+}
+
+__global__ void k_sum_partials(float4 *QG, const float2 *QGp, int rsb, long n, int pt0, int E)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long)E * n) return;
+    sum_partial(QG, QGp, rsb, n, pt0, i);
+}
+
+// -------------------------------------------------------- work list
+// One launch of k_worklist runs every stage of a list of jobs (a job: one
+// species pair and chunk of points of one plan).  A task is one CTA of a plain
+// launch's stage A, B or C grid, run by the same body with the same block
+// index, or one slice of the partial sums.  CTAs claim tasks from a queue in
+// global memory (see k_worklist), wait until the tasks they depend on are
+// complete, run them and publish their completion in per-job counters.  With
+// prev the job of the same plan queued before job j (whose workspace slots j
+// overwrites):
+//   A(j, rs)  after B(prev, rs), and B(prev, rs') if prev reads B' from A' at rs' = bmap[rs]
+//   B(j, rs)  after A(j, rs) (and A(j, bmap[rs]) when j reads B' from A') and C(prev, g(rs))
+//   C(j, g)   after B(j, rs) for every rs of g, and S(prev)
+//   S(j)      after C(j, every g)
+// where g(rs) is the stage C grid index y whose (r, s)-blocks hold rs.  Tasks
+// are queued so that every task's dependencies come before it.  Every wait is
+// bounded (global timer); on expiry the CTA raises the job's error flag and
+// the launch's abort flag, and every CTA stops taking tasks.
+constexpr int kWlJobs = 96;    // jobs per launch
+constexpr int kWlSegs = 1024;  // task segments per launch
+constexpr long kWlSumChunk = 8192;  // grid points per partial-sum task
+constexpr uint64_t kWlWaitNs = 4000000000ull;  // bound of one dependency wait
+enum { WL_A = 0, WL_B = 1, WL_C = 2, WL_S = 3 };
+
+struct WlJob {
+    TcArgs a;
+    float4 *qg;            // QG of the job's pair, as in k_sum_partials
+    const uint16_t *bmap;  // same-species pair: B' read from A' at bmap[rs] (null: both sides computed)
+    int prev;              // job of the same plan queued before this one in this launch, or -1
+    uint32_t cnt;          // first counter of the job: A[RS] B[RS] Bg[gyc] C[gyc] Ctot S
+    uint16_t ga, sides, gb, ngc, gyc, ec;  // grids (ga, RS, sides), (gb, RS), (ngc, gyc, ec)
+    uint32_t ns;           // partial-sum tasks
+};
+
+// Passed by value (constant bank).  seg[i]: x = first task of the segment,
+// y = job | stage << 12 | first linear block index << 14; a segment's tasks are
+// consecutive linear block indices of one stage grid of one job.
+struct WlTable {
+    WlJob job[kWlJobs];
+    uint2 seg[kWlSegs];
+    // ctr: [0] queue head, [1] abort flag, [2] tasks handed on, [3] handed-on
+    // tasks taken, [4] claims resolved (run or handed on), from [8] the jobs'
+    // counters, from [8 + ring] the ring of handed-on tasks (task + 1; zero at launch)
+    uint32_t *ctr;
+    uint32_t ring;
+    int nseg;
+    uint32_t ntasks;
+    // optional task trace (dgfs_debug_worklist_trace): per task, the global
+    // timer when it was taken, when its dependencies were met and when it
+    // ended, and (SM << 8 | stage); tasks beyond trace_cap are not recorded
+    unsigned long long *trace;
+    uint32_t trace_cap;
+};
+static_assert(sizeof(WlTable) <= 32764, "a kernel's parameters are limited to 32764 bytes");
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// thread 0: wait until *c >= target; false on abort or when the bound expires
+__device__ __noinline__ bool wl_wait(const uint32_t *c, uint32_t target, const uint32_t *abort_flag)
+{
+    if (ld_acquire_u32(c) >= target) return true;
+    const uint64_t t_end = global_ns() + kWlWaitNs;
+    for (;;) {
+        __nanosleep(128);
+        if (ld_acquire_u32(c) >= target) return true;
+        if (ld_acquire_u32(abort_flag) || global_ns() > t_end) return false;
+    }
+}
+
+// counters of a job
+struct WlCtr {
+    uint32_t *A, *B, *Bg, *C, *Ctot, *S;
+};
+__device__ __forceinline__ WlCtr wl_ctr(const WlTable &t, const WlJob &J)
+{
+    WlCtr c;
+    c.A = t.ctr + 8 + J.cnt;
+    c.B = c.A + J.a.RS;
+    c.Bg = c.B + J.a.RS;
+    c.C = c.Bg + J.gyc;
+    c.Ctot = c.C + J.gyc;
+    c.S = c.Ctot + 1;
+    return c;
+}
+
+// stage C grid index y whose (r, s)-blocks hold rs, and the rs range of index g
+template <int NPC> __device__ __forceinline__ int wl_g(const TcArgs &a, int rs) { return rs / a.rs_per_block / NPC; }
+template <int NPC> __device__ __forceinline__ int2 wl_grange(const TcArgs &a, int g)
+{
+    const int lo = g * NPC * a.rs_per_block;
+    const int hi = min(a.RS, min(a.rsb, (g + 1) * NPC) * a.rs_per_block);
+    return make_int2(lo, max(lo, hi));
+}
+
+// thread 0: wait for the dependencies of task (job j, stage, linear block v)
+template <int NPC> __device__ bool wl_deps(const WlTable &t, int j, int stage, uint32_t v)
+{
+    const WlJob &J = t.job[j];
+    const WlCtr c = wl_ctr(t, J);
+    const uint32_t *ab = t.ctr + 1;
+    const bool hp = J.prev >= 0;
+    const WlJob &P = t.job[hp ? J.prev : j];
+    const WlCtr pc = wl_ctr(t, P);
+    if (stage == WL_A) {
+        const int rs = (int)(v / J.ga / J.sides);
+        if (hp && !wl_wait(pc.B + rs, P.gb, ab)) return false;
+        if (hp && P.bmap && !wl_wait(pc.B + __ldg(P.bmap + rs), P.gb, ab)) return false;
+    } else if (stage == WL_B) {
+        const int rs = (int)(v / J.gb);
+        const uint32_t na = (uint32_t)J.ga * J.sides;
+        if (!wl_wait(c.A + rs, na, ab)) return false;
+        if (J.bmap && !wl_wait(c.A + __ldg(J.bmap + rs), na, ab)) return false;
+        if (hp && !wl_wait(pc.C + wl_g<NPC>(P.a, rs), (uint32_t)P.ngc * P.ec, ab)) return false;
+    } else if (stage == WL_C) {
+        const int g = (int)(v / J.ngc / J.ec);
+        const int2 r = wl_grange<NPC>(J.a, g);
+        if (!wl_wait(c.Bg + g, (uint32_t)J.gb * (r.y - r.x), ab)) return false;
+        if (hp && !wl_wait(pc.S, P.ns, ab)) return false;
+    } else {
+        if (!wl_wait(c.Ctot, (uint32_t)J.ngc * J.gyc * J.ec, ab)) return false;
+    }
+    return true;
+}
+
+// thread 0, after the task's writes: publish its completion
+template <int NPC> __device__ __forceinline__ void wl_done(const WlTable &t, int j, int stage, uint32_t v)
+{
+    const WlJob &J = t.job[j];
+    const WlCtr c = wl_ctr(t, J);
+    if (stage == WL_A) {
+        atomicAdd(c.A + v / J.ga / J.sides, 1u);
+    } else if (stage == WL_B) {
+        const int rs = (int)(v / J.gb);
+        atomicAdd(c.B + rs, 1u);
+        atomicAdd(c.Bg + wl_g<NPC>(J.a, rs), 1u);
+    } else if (stage == WL_C) {
+        atomicAdd(c.C + v / J.ngc / J.ec, 1u);
+        atomicAdd(c.Ctot, 1u);
+    } else {
+        atomicAdd(c.S, 1u);
+    }
+}
+
+// (job, stage, linear block index) of task h
+__device__ __forceinline__ void wl_decode(const WlTable &t, uint32_t h, int &job, int &stage, uint32_t &v)
+{
+    int lo = 0, hi = t.nseg - 1;  // the last segment starting at or before h
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (t.seg[mid].x <= h) lo = mid;
+        else hi = mid - 1;
+    }
+    const uint2 sg = t.seg[lo];
+    job = (int)(sg.y & 0xFFFu);
+    stage = (int)((sg.y >> 12) & 3u);
+    v = (sg.y >> 14) + (h - sg.x);
+}
+
+// thread 0, a CTA running tasks of one kind (stage `want`; for stage B also
+// whether the job reads B' from A', want_share): claim the next task.  True if
+// it is of that kind; a task of another kind is handed on through the ring
+// (a fresh CTA takes it) and false returned, as when the queue is exhausted
+// or the launch aborted.
+__device__ bool wl_claim_same(const WlTable &t, int want, int want_share, int &job, int &stage, uint32_t &v,
+                              uint32_t &task)
+{
+    if (ld_acquire_u32(t.ctr + 1)) return false;
+    const uint32_t h = atomicAdd(t.ctr, 1u);
+    if (h >= t.ntasks) return false;
+    wl_decode(t, h, job, stage, v);
+    const bool same =
+        stage == want && (want_share < 0 || (t.job[job].bmap != nullptr) == (want_share != 0));
+    if (!same) {
+        const uint32_t i = atomicAdd(t.ctr + 2, 1u);
+        atomicExch(t.ctr + 8 + t.ring + i, h + 1);
+        __threadfence();
+    }
+    atomicAdd(t.ctr + 4, 1u);
+    task = h;
+    return same;
+}
+
+// thread 0, a fresh CTA: its first task, a handed-on one if any is waiting,
+// else the next one in the queue.  False when no work is left (every task
+// claimed and run or handed on, and every handed-on task taken), on abort, or
+// when the bounded wait for work expires (the launch is then aborted).
+__device__ bool wl_claim_first(const WlTable &t, int &job, int &stage, uint32_t &v, uint32_t &task)
+{
+    const uint64_t t_end = global_ns() + kWlWaitNs;
+    const uint32_t *ring = t.ctr + 8 + t.ring;
+    for (;;) {
+        if (ld_acquire_u32(t.ctr + 1)) return false;
+        const uint32_t r = ld_acquire_u32(t.ctr + 3), w = ld_acquire_u32(t.ctr + 2);
+        if (r < w) {
+            if (atomicCAS(t.ctr + 3, r, r + 1) == r) {
+                // slot r was reserved by the CTA that hands the task on; it writes it next
+                uint32_t x;
+                while ((x = ld_acquire_u32(ring + r)) == 0) {
+                    if (global_ns() > t_end) {
+                        atomicExch(t.job[0].a.err, kErrTimeout);
+                        atomicExch(t.ctr + 1, 1u);
+                        return false;
+                    }
+                    __nanosleep(32);
+                }
+                task = x - 1;
+                wl_decode(t, task, job, stage, v);
+                return true;
+            }
+            continue;
+        }
+        if (ld_acquire_u32(t.ctr) < t.ntasks) {
+            const uint32_t h = atomicAdd(t.ctr, 1u);
+            if (h < t.ntasks) {
+                atomicAdd(t.ctr + 4, 1u);
+                task = h;
+                wl_decode(t, h, job, stage, v);
+                return true;
+            }
+        }
+        // the queue is exhausted: done once every claim is resolved and every handed-on task taken
+        if (ld_acquire_u32(t.ctr + 4) >= t.ntasks && ld_acquire_u32(t.ctr + 3) >= ld_acquire_u32(t.ctr + 2))
+            return false;
+        if (global_ns() > t_end) {
+            atomicExch(t.job[0].a.err, kErrTimeout);
+            atomicExch(t.ctr + 1, 1u);
+            return false;
+        }
+        __nanosleep(256);
+    }
+}
+
+// The work-list kernel.  A fresh CTA takes a handed-on task or the next one in
+// the queue, then keeps claiming tasks while they are of the same kind (stage,
+// and for stage B the body), and leaves when it claims one of another kind,
+// handing it on through the ring.  The grid has one CTA per task, more than
+// can ever be needed (each CTA's first task is one no other CTA took first),
+// so a fresh CTA always takes the place of one that left.  Every claim is a
+// fetch-and-add on the queue head, so claims do not serialise.  Each kind's
+// loop is a branch of its own, not one loop over all the bodies: the bodies use
+// nearly all 255 registers, and one loop around all of them makes the register
+// allocator spill inside them.
+//
+// No deadlock: a task's dependencies are earlier in the queue, so they were
+// claimed before it; a claimed task runs on its claiming CTA or waits in the
+// ring, and every hand-on is followed by the handing CTA leaving, which lets a
+// fresh CTA, which takes handed-on tasks first, start.
+template <int N, int FMT>
+__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::A, 1) k_worklist(const __grid_constant__ WlTable t)
+{
+    constexpr int NP = NPipes<N, FMT>::A;
+    static_assert(NP == NPipes<N, FMT>::B && NP == NPipes<N, FMT>::C, "one pipeline count for every stage");
+    __shared__ uint32_t s_tm;
+    __shared__ int s_job, s_stage;
+    __shared__ uint32_t s_v;
+    // thread 0 takes a task (of stage `want`, or any when want < 0) and waits
+    // for its dependencies; every thread returns its stage, or -1
+    __shared__ uint32_t s_task;
+    // want < 0: a fresh CTA's first task; else the next task of this kind
+    auto next = [&](int want, int want_share) -> int {
+        // the previous task's generic shared-memory writes before the next
+        // task's bulk copies into the same bytes
+        fence_proxy_async();
+        if (threadIdx.x == 0) {
+            int job = -1, stage = -1;
+            uint32_t v = 0, task = 0;
+            const bool got = want < 0 ? wl_claim_first(t, job, stage, v, task)
+                                      : wl_claim_same(t, want, want_share, job, stage, v, task);
+            if (!got) stage = -1;
+            if (got) {
+                const uint64_t t0 = t.trace ? global_ns() : 0;
+                const bool ready = wl_deps<NP>(t, job, stage, v);
+                if (t.trace && task < t.trace_cap) {
+                    uint32_t smid;
+                    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+                    t.trace[4 * task] = t0;
+                    t.trace[4 * task + 1] = global_ns();
+                    t.trace[4 * task + 3] = (unsigned long long)(smid << 8 | (uint32_t)stage);
+                }
+                s_task = task;
+                if (ready) {
+                    __threadfence();
+                } else {
+                    atomicExch(t.job[job].a.err, kErrTimeout);
+                    atomicExch(t.ctr + 1, 1u);
+                    stage = -1;
+                }
+            }
+            s_job = job;
+            s_stage = stage;
+            s_v = v;
+        }
+        __syncthreads();
+        return s_stage;
+    };
+    // thread 0: publish a finished task (or abort the launch)
+    auto done = [&](bool ok, int stage) {
+        if (threadIdx.x == 0) {
+            if (t.trace && s_task < t.trace_cap) t.trace[4 * s_task + 2] = global_ns();
+            if (ok) {
+                __threadfence();
+                wl_done<NP>(t, s_job, stage, s_v);
+            } else {
+                atomicExch(t.ctr + 1, 1u);
+            }
+        }
+    };
+    const int first = next(-1, -1);
+    if (first < 0) return;
+    const bool share = t.job[s_job].bmap != nullptr;
+    if (threadIdx.x < 32) tmem_alloc(&s_tm, 512);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const Persist ps{s_tm};
+    if (first == WL_A) {
+        for (int st = first; st == WL_A; st = next(WL_A, -1)) {
+            const WlJob &J = t.job[s_job];
+            const uint32_t v = s_v, r = v / J.ga;
+            done(k_stage_a_body<N, FMT>(J.a, make_uint3(v % J.ga, r / J.sides, r % J.sides),
+                                        make_uint3(J.ga, J.a.RS, J.sides), &ps),
+                 WL_A);
+        }
+    } else if (first == WL_B && share) {
+        for (int st = first; st == WL_B; st = next(WL_B, 1)) {
+            const WlJob &J = t.job[s_job];
+            const uint32_t v = s_v;
+            done(k_stage_b_body<N, FMT, false, true>(J.a, make_uint3(v % J.gb, v / J.gb, 0),
+                                                     make_uint3(J.gb, J.a.RS, 1), J.bmap, &ps),
+                 WL_B);
+        }
+    } else if (first == WL_B) {
+        for (int st = first; st == WL_B; st = next(WL_B, 0)) {
+            const WlJob &J = t.job[s_job];
+            const uint32_t v = s_v;
+            done(k_stage_b_body<N, FMT>(J.a, make_uint3(v % J.gb, v / J.gb, 0), make_uint3(J.gb, J.a.RS, 1),
+                                        nullptr, &ps),
+                 WL_B);
+        }
+    } else if (first == WL_C) {
+        for (int st = first; st == WL_C; st = next(WL_C, -1)) {
+            const WlJob &J = t.job[s_job];
+            const uint32_t v = s_v, r = v / J.ngc;
+            done(k_stage_c_body<N, FMT>(J.a, make_uint3(v % J.ngc, r / J.ec, r % J.ec),
+                                        make_uint3(J.ngc, J.gyc, J.ec), &ps),
+                 WL_C);
+        }
+    } else {
+        for (int st = first; st == WL_S; st = next(WL_S, -1)) {
+            const WlJob &J = t.job[s_job];
+            const long total = (long)J.ec * J.a.n, lo = (long)s_v * kWlSumChunk;
+            const long hi = min(total, lo + kWlSumChunk);
+            for (long i = lo + threadIdx.x; i < hi; i += blockDim.x)
+                sum_partial(J.qg, J.a.QGp, J.a.rsb, J.a.n, J.a.pt0, i);
+            __syncthreads();
+            done(true, WL_S);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) tmem_dealloc(s_tm, 512);
 }
 
 // ------------------------------------------------------ table preparation
@@ -1503,11 +1912,269 @@ void job_grids(const dgfs_plan_s *plan, int Ec, bool share, dim3 &gA, dim3 &gB, 
     gC = dim3((N + G - 1) / G, (RSB + NPipes<N, FMT>::C - 1) / NPipes<N, FMT>::C, Ec);
 }
 
+// -------------------------------------------------- work list (host)
+// N with one pipeline count for stages A, B and C (the work-list kernel runs
+// all three bodies in one CTA shape)
+bool wl_supported(int N) { return N == 24 || N == 32 || N == 48; }
+
+// One job of a schedule.
+struct WlSpec {
+    TcArgs a;
+    float4 *qg;
+    const uint16_t *bmap;
+    const void *key;  // the plan: jobs with one key reuse one workspace
+    dim3 gA, gB, gC;
+    int M;
+};
+
+template <int N, int FMT>
+WlSpec wl_spec(const dgfs_plan_s *plan, const void *f, int p, int q, int pt0, int Ec)
+{
+    const TcWs w = ws_of(plan);
+    WlSpec s;
+    s.a = job_args(plan, f, p, q, pt0, Ec);
+    const Share sh = job_share(plan, p, q);
+    s.bmap = sh.on ? sh.bmap : nullptr;
+    s.qg = w.QG + (p * plan->S + q) * w.qg_stride;
+    s.key = plan;
+    s.M = plan->M;
+    job_grids<N, FMT>(plan, Ec, sh.on, s.gA, s.gB, s.gC);
+    return s;
+}
+
+// Counter words of the work list's launches for jobs of RS (r, s) and gyc stage C grid rows.
+// task trace of the work-list launches (dgfs_debug_worklist_trace); off when null
+unsigned long long *g_wl_trace = nullptr;
+uint32_t g_wl_trace_cap = 0;
+// (r, s) per wave of the work-list queue (dgfs_debug_worklist_chunk)
+int g_wl_chunk = 48;
+
+// Counter words of a work-list launch: the control words, the jobs'
+// counters and one ring slot per task.
+size_t wl_words_for(int RS, int gyc, size_t tasks) { return 8 + (size_t)kWlJobs * (2 * RS + 2 * gyc + 2) + tasks; }
+
+// An upper bound of the tasks of one job of a plan over every launch
+// configuration the autotuner tries (CTA groups for up to 16 waves, chunks of
+// up to chunk_max points, up to rsb_max (r, s)-blocks).
+size_t wl_job_tasks_max(const dgfs_plan_s *plan, int sms, int chunk_max, int rsb_max)
+{
+    const long RS = (long)plan->Nrho * plan->M, N = plan->N, n = N * N * N;
+    const long ga = std::max(1L, (16L * sms + RS) / (2 * RS)), gb = std::max(1L, (16L * sms + RS / 2) / RS);
+    const long G = kRows / N, ngc = (N + G - 1) / G;
+    return (size_t)(2 * RS * ga + RS * gb + ngc * rsb_max * chunk_max + (chunk_max * n + kWlSumChunk - 1) / kWlSumChunk);
+}
+
+// Queue the jobs of `rounds` (a round holds at most one job per plan) into
+// work-list launches.  Within a round the tasks go in waves over chunks of
+// about twelve (r, s) (whole radial nodes): wave c holds stage A of chunk c,
+// stage B of chunk c - 2 and stage C of every grid row whose (r, s) had their
+// stage B queued in an earlier wave; the partial sums of a round follow at
+// wave 2 of the next round.  Every task's dependencies are queued before it.
+// Returns false if a launch's tables cannot hold one job.
+bool wl_build(const std::vector<std::vector<WlSpec>> &rounds, int npc, uint32_t *ctr, std::vector<WlTable> &L,
+              std::vector<uint32_t> &words, int chunk = g_wl_chunk)
+{
+    constexpr int LAG = 2;
+    L.clear();
+    words.clear();
+    bool open = false, fits = true;
+    uint32_t nw = 0;
+    int nj = 0;
+    std::vector<std::pair<const void *, int>> last;  // plan -> its latest job in the open launch
+    std::vector<int> pend;                           // jobs whose partial sums are not queued yet
+    auto T = [&]() -> WlTable & { return L.back(); };
+    auto seg = [&](int j, int stage, uint32_t v0, uint32_t cnt) {
+        if (!cnt) return;
+        WlTable &t = T();
+        if (t.nseg >= kWlSegs || v0 >= (1u << 18) || j > 0xFFF) {
+            fits = false;
+            return;
+        }
+        t.seg[t.nseg++] = make_uint2(t.ntasks, (uint32_t)j | ((uint32_t)stage << 12) | (v0 << 14));
+        t.ntasks += cnt;
+    };
+    auto close = [&] {
+        if (!open) return;
+        for (int j : pend) seg(j, WL_S, 0, T().job[j].ns);
+        pend.clear();
+        T().ring = nw;
+        words.push_back(8 + nw + T().ntasks);
+        open = false;
+    };
+    auto start = [&] {
+        L.emplace_back();
+        memset(&L.back(), 0, sizeof(WlTable));
+        L.back().ctr = ctr;
+        nw = 0;
+        nj = 0;
+        last.clear();
+        open = true;
+    };
+    auto chunk_rs = [chunk](const WlSpec &s) { return s.M * std::max(1, (chunk + s.M - 1) / s.M); };
+    auto nchunks = [&](const WlSpec &s) { return (s.a.RS + chunk_rs(s) - 1) / chunk_rs(s); };
+    auto est = [&](const WlSpec &s) { return 2 * nchunks(s) + (int)s.gC.y + 1; };
+    // rs range of stage C grid row g, as wl_grange on the device
+    auto grange_hi = [&](const TcArgs &a, int g) {
+        return std::min(a.RS, std::min(a.rsb, (g + 1) * npc) * a.rs_per_block);
+    };
+    for (const auto &round : rounds) {
+        size_t r0 = 0;
+        while (r0 < round.size()) {
+            if (!open) start();
+            int segs = T().nseg + (int)pend.size();
+            size_t r1 = r0;
+            while (r1 < round.size() && nj + (int)(r1 - r0) < kWlJobs && segs + est(round[r1]) <= kWlSegs)
+                segs += est(round[r1++]);
+            if (r1 == r0) {
+                if (nj == 0) return false;
+                close();
+                continue;
+            }
+            std::vector<int> idx;
+            for (size_t i = r0; i < r1; ++i) {
+                const WlSpec &s = round[i];
+                WlJob &J = T().job[nj];
+                J.a = s.a;
+                J.qg = s.qg;
+                J.bmap = s.bmap;
+                J.prev = -1;
+                for (auto &kv : last)
+                    if (kv.first == s.key) J.prev = kv.second;
+                J.cnt = nw;
+                nw += 2u * s.a.RS + 2u * s.gC.y + 2u;
+                J.ga = (uint16_t)s.gA.x;
+                J.sides = (uint16_t)s.gA.z;
+                J.gb = (uint16_t)s.gB.x;
+                J.ngc = (uint16_t)s.gC.x;
+                J.gyc = (uint16_t)s.gC.y;
+                J.ec = (uint16_t)s.gC.z;
+                J.ns = (uint32_t)(((long)J.ec * s.a.n + kWlSumChunk - 1) / kWlSumChunk);
+                idx.push_back(nj++);
+            }
+            int maxch = 0;
+            std::vector<int> gnext(idx.size(), 0);
+            for (size_t i = r0; i < r1; ++i) maxch = std::max(maxch, nchunks(round[i]));
+            for (int c = 0; c <= maxch + LAG; ++c) {
+                for (size_t k = 0; k < idx.size(); ++k) {
+                    const WlSpec &s = round[r0 + k];
+                    const WlJob &J = T().job[idx[k]];
+                    const int RC = chunk_rs(s), lo = c * RC, hi = std::min(s.a.RS, lo + RC);
+                    if (c < nchunks(s)) seg(idx[k], WL_A, (uint32_t)lo * J.sides * J.ga, (uint32_t)(hi - lo) * J.sides * J.ga);
+                }
+                if (c == LAG) {
+                    for (int j : pend) seg(j, WL_S, 0, T().job[j].ns);
+                    pend.clear();
+                }
+                // stage B of the jobs that compute both sides, then of those
+                // that read B' from A' (one stage B body per run of tasks)
+                for (int kind = 0; kind < 2; ++kind)
+                    for (size_t k = 0; k < idx.size(); ++k) {
+                        const WlSpec &s = round[r0 + k];
+                        const WlJob &J = T().job[idx[k]];
+                        const int RC = chunk_rs(s), cb = c - LAG;
+                        if ((s.bmap != nullptr) == (kind == 1) && cb >= 0 && cb < nchunks(s)) {
+                            const int lo = cb * RC, hi = std::min(s.a.RS, lo + RC);
+                            seg(idx[k], WL_B, (uint32_t)lo * J.gb, (uint32_t)(hi - lo) * J.gb);
+                        }
+                    }
+                for (size_t k = 0; k < idx.size(); ++k) {
+                    const WlSpec &s = round[r0 + k];
+                    const WlJob &J = T().job[idx[k]];
+                    const int RC = chunk_rs(s);
+                    // stage C rows whose stage B was queued in earlier waves
+                    const long lim = (long)(c - LAG) * RC;
+                    while (c > LAG && gnext[k] < (int)J.gyc && grange_hi(s.a, gnext[k]) <= lim) {
+                        seg(idx[k], WL_C, (uint32_t)gnext[k] * J.ec * J.ngc, (uint32_t)J.ec * J.ngc);
+                        ++gnext[k];
+                    }
+                }
+            }
+            for (size_t k = 0; k < idx.size(); ++k) {
+                bool found = false;
+                for (auto &kv : last)
+                    if (kv.first == round[r0 + k].key) {
+                        kv.second = idx[k];
+                        found = true;
+                    }
+                if (!found) last.emplace_back(round[r0 + k].key, idx[k]);
+                pend.push_back(idx[k]);
+            }
+            r0 = r1;
+        }
+    }
+    close();
+    return fits;
+}
+
+
+template <int N, int FMT> constexpr size_t wl_smem()
+{
+    using SM = Smem<N, FMT>;
+    return std::max(SM::A, std::max(SM::B, SM::C));
+}
+
+template <int N, int FMT>
+dgfs_status wl_launch(dgfs_plan_s *plan, const std::vector<WlTable> &L, const std::vector<uint32_t> &words, int sms,
+                      cudaStream_t st)
+{
+    for (size_t l = 0; l < L.size(); ++l) {
+        if (!L[l].ntasks) continue;
+        DGFS_CUDA(cudaMemsetAsync(L[l].ctr, 0, sizeof(uint32_t) * words[l], st));
+        const unsigned grid = L[l].ntasks;  // one CTA per task at most (see k_worklist)
+        {
+            ProfScope ps(plan, "tc_worklist", st);
+            if (g_wl_trace) {
+                WlTable tt = L[l];
+                tt.trace = g_wl_trace;
+                tt.trace_cap = g_wl_trace_cap;
+                k_worklist<N, FMT><<<grid, kRows * NPipes<N, FMT>::A, wl_smem<N, FMT>(), st>>>(tt);
+            } else {
+                k_worklist<N, FMT><<<grid, kRows * NPipes<N, FMT>::A, wl_smem<N, FMT>(), st>>>(L[l]);
+            }
+        }
+        DGFS_LAUNCHED(plan);
+    }
+    return DGFS_OK;
+}
+
+// A plain call as one work-list launch (TcState::sched = 1).  The jobs
+// (species pair, chunk of points) share the plan's workspace, so each is a
+// round of its own; the dependencies let the next job's stage A start as soon
+// as the current job's stage B has read the grids it overwrites.
+template <int N, int FMT>
+dgfs_status collide_wl(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaStream_t st)
+{
+    TcState *ts = reinterpret_cast<TcState *>(plan->tc);
+    const TcWs w = ws_of(plan);
+    std::vector<std::vector<WlSpec>> rounds;
+    for (int p = 0; p < plan->S; ++p)
+        for (int q = 0; q < plan->S; ++q)
+            for (int pt0 = 0; pt0 < P; pt0 += ts->chunk)
+                rounds.push_back({wl_spec<N, FMT>(plan, f, p, q, pt0, std::min(ts->chunk, P - pt0))});
+    std::vector<WlTable> L;
+    std::vector<uint32_t> words;
+    if (!wl_build(rounds, NPipes<N, FMT>::C, ts->wl_ctr, L, words)) {
+        set_error("dgfs_collide: the work list cannot hold this plan's jobs");
+        return DGFS_EUNSUPPORTED;
+    }
+    for (uint32_t wd : words)
+        if (wd > ts->wl_words) {
+            set_error("dgfs_collide: work-list counters exceed their buffer");
+            return DGFS_EUNSUPPORTED;
+        }
+    DGFS_TRY(df_forward(plan, P, reinterpret_cast<const float *>(f), w.F, ts->tw_df, st));
+    DGFS_TRY((wl_launch<N, FMT>(plan, L, words, ts->sms, st)));
+    return df_finish(plan, P, w.QG, w.qg_stride, w.F, reinterpret_cast<const float *>(f),
+                     reinterpret_cast<float *>(Qout), ts->tw_df, st);
+}
+
 template <int N, int FMT>
 dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaStream_t st)
 {
     using SM = Smem<N, FMT>;
     TcState *ts = reinterpret_cast<TcState *>(plan->tc);
+    if constexpr (N == 24 || N == 32 || N == 48)
+        if (ts->sched == 1) return collide_wl<N, FMT>(plan, P, f, Qout, st);
     const int S = plan->S;
     const long n = (long)N * N * N;
     const int E = ts->chunk, RSB = rs_blocks(plan);
@@ -1678,6 +2345,9 @@ dgfs_status set_smem_attrs()
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_a_batch<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::A));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_b_batch<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_c_batch<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::C));
+    if constexpr (N == 24 || N == 32 || N == 48)
+        DGFS_CUDA(cudaFuncSetAttribute(k_worklist<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)wl_smem<N, FMT>()));
     return DGFS_OK;
 }
 
@@ -1928,7 +2598,16 @@ dgfs_status tc_prepare(dgfs_plan_s *plan)
     // about 8 waves of CTAs per stage (the autotuner's usual choice at N = 32)
     ts->groups_a = std::max(1, (8 * sms + RS) / (2 * RS));
     ts->groups_b = std::max(1, (8 * sms + RS / 2) / RS);
+    ts->sms = sms;
     DGFS_CUDA(dev_malloc(&ts->err, sizeof(int)));
+    if (wl_supported(N)) {  // counters of the work list (stage C grid rows <= rsb_max)
+        // jobs of one call: S^2 pairs times the chunks of points (chunks of at
+        // least min(chunk_max, 8) points, the autotuner's smaller candidate)
+        const int cmin = std::min(ts->chunk_max, 8);
+        const size_t jobs = std::min<size_t>(kWlJobs, (size_t)plan->S * plan->S * ((plan->max_points + cmin - 1) / cmin));
+        ts->wl_words = wl_words_for(RS, ts->rsb_max, jobs * wl_job_tasks_max(plan, sms, ts->chunk_max, ts->rsb_max));
+        DGFS_CUDA(dev_malloc(&ts->wl_ctr, sizeof(uint32_t) * ts->wl_words));
+    }
     DGFS_CUDA(cudaMemset(ts->err, 0, sizeof(int)));
     DGFS_CUDA(cudaStreamCreateWithFlags(&ts->side, cudaStreamNonBlocking));
     DGFS_CUDA(cudaEventCreateWithFlags(&ts->ev_entry, cudaEventDisableTiming));
@@ -1978,6 +2657,7 @@ void tc_release(dgfs_plan_s *plan)
     if (!ts) return;
     dev_free(ts->Fimg);
     dev_free(ts->err);
+    dev_free(ts->wl_ctr);
     dev_free(ts->idmask);
     dev_free(ts->bmap);
     dev_free(ts->tw_df);
@@ -2011,12 +2691,21 @@ struct TcBatch {
     std::vector<BatchPlan> plans;  // forward transforms before the rounds, finishing passes after them
     cudaStream_t side = nullptr;   // stage A launches (see Fork)
     cudaEvent_t ev_entry = nullptr, ev_a = nullptr, ev_b = nullptr;
+    // work list per group (empty where N has none): the group's
+    // rounds queued into k_worklist launches, which share one counter buffer
+    // (sched = 1; the default 0 runs the rounds as per-stage launches)
+    int sched = 0;
+    std::vector<std::vector<WlTable>> wl;
+    std::vector<std::vector<uint32_t>> wl_words;
+    uint32_t *wl_ctr = nullptr;
+    int sms = 148;
 };
 
 void tc_batch_free(void *handle)
 {
     TcBatch *b = reinterpret_cast<TcBatch *>(handle);
     if (!b) return;
+    dev_free(b->wl_ctr);
     if (b->side) cudaStreamDestroy(b->side);
     if (b->ev_entry) cudaEventDestroy(b->ev_entry);
     if (b->ev_a) cudaEventDestroy(b->ev_a);
@@ -2070,6 +2759,47 @@ dgfs_status tc_batch_build(int count, dgfs_plan_s *const *plans, const int *P, v
                 return st;
             }
         }
+    // the same rounds as work lists (groups of N = 24, 32, 48)
+    size_t words = 0;
+    b->wl.resize(b->groups.size());
+    b->wl_words.resize(b->groups.size());
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        const BatchGroup &g = b->groups[gi];
+        if (!wl_supported(g.N)) continue;
+        std::vector<std::vector<WlSpec>> rounds;
+        for (const BatchRound &r : g.rounds) {
+            rounds.emplace_back();
+            for (const BatchJob &j : r.jobs) {
+                WlSpec sp;
+                switch (g.N * 2 + g.fmt) {
+                case 48: sp = wl_spec<24, 0>(j.plan, j.f, j.p, j.q, j.pt0, j.Ec); break;
+                case 49: sp = wl_spec<24, 1>(j.plan, j.f, j.p, j.q, j.pt0, j.Ec); break;
+                case 64: sp = wl_spec<32, 0>(j.plan, j.f, j.p, j.q, j.pt0, j.Ec); break;
+                case 65: sp = wl_spec<32, 1>(j.plan, j.f, j.p, j.q, j.pt0, j.Ec); break;
+                case 96: sp = wl_spec<48, 0>(j.plan, j.f, j.p, j.q, j.pt0, j.Ec); break;
+                default: sp = wl_spec<48, 1>(j.plan, j.f, j.p, j.q, j.pt0, j.Ec); break;
+                }
+                rounds.back().push_back(sp);
+            }
+        }
+        const int npc = g.N == 48 ? NPipes<48, 0>::C : NPipes<32, 0>::C;
+        if (!wl_build(rounds, npc, nullptr, b->wl[gi], b->wl_words[gi])) {
+            b->wl[gi].clear();  // this group runs its rounds as launches
+            b->wl_words[gi].clear();
+            continue;
+        }
+        for (uint32_t wd : b->wl_words[gi]) words = std::max(words, (size_t)wd);
+    }
+    if (words) {
+        cudaError_t ea = dev_malloc(&b->wl_ctr, sizeof(uint32_t) * words);
+        if (ea != cudaSuccess) {
+            tc_batch_free(b);
+            return cuda_status(ea, "dgfs_batch_create: work-list counters");
+        }
+        for (auto &L : b->wl)
+            for (WlTable &t : L) t.ctr = b->wl_ctr;
+    }
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, plans[0]->device);
     cudaError_t e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_entry, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_a, cudaEventDisableTiming);
@@ -2094,16 +2824,45 @@ dgfs_status tc_batch_launch(void *handle, cudaStream_t st)
         const TcState *ts = reinterpret_cast<const TcState *>(bp.plan->tc);
         DGFS_TRY(df_forward(bp.plan, bp.P, reinterpret_cast<const float *>(bp.f), ws_of(bp.plan).F, ts->tw_df, st));
     }
-    for (auto &g : b->groups)
-        for (auto &r : g.rounds)
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        const BatchGroup &g = b->groups[gi];
+        if (b->sched == 1 && !b->wl[gi].empty()) {
+            dgfs_plan_s *lead = g.rounds[0].jobs[0].plan;
+            const auto &L = b->wl[gi];
+            const auto &W = b->wl_words[gi];
+            switch (g.N * 2 + g.fmt) {
+            case 48: DGFS_TRY((wl_launch<24, 0>(lead, L, W, b->sms, st))); break;
+            case 49: DGFS_TRY((wl_launch<24, 1>(lead, L, W, b->sms, st))); break;
+            case 64: DGFS_TRY((wl_launch<32, 0>(lead, L, W, b->sms, st))); break;
+            case 65: DGFS_TRY((wl_launch<32, 1>(lead, L, W, b->sms, st))); break;
+            case 96: DGFS_TRY((wl_launch<48, 0>(lead, L, W, b->sms, st))); break;
+            default: DGFS_TRY((wl_launch<48, 1>(lead, L, W, b->sms, st))); break;
+            }
+            continue;
+        }
+        for (auto &r : b->groups[gi].rounds)
             DGFS_TRY(g.fmt == 0 ? round_dispatch<0>(g.N, r, false, st, &fk)
                                 : round_dispatch<1>(g.N, r, false, st, &fk));
+    }
     for (const BatchPlan &bp : b->plans) {
         const TcWs w = ws_of(bp.plan);
         const TcState *ts = reinterpret_cast<const TcState *>(bp.plan->tc);
         DGFS_TRY(df_finish(bp.plan, bp.P, w.QG, w.qg_stride, w.F, reinterpret_cast<const float *>(bp.f),
                            reinterpret_cast<float *>(bp.Q), ts->tw_df, st));
     }
+    return DGFS_OK;
+}
+
+// 0: every group runs its rounds as per-stage launches (the default); 1:
+// groups of N = 24, 32 and 48 run as work lists
+dgfs_status tc_batch_set_schedule(void *handle, int mode)
+{
+    TcBatch *b = reinterpret_cast<TcBatch *>(handle);
+    if (mode != 0 && mode != 1) {
+        set_error("dgfs_batch_set_schedule: mode must be 0 or 1");
+        return DGFS_EINVAL;
+    }
+    if (b) b->sched = mode;
     return DGFS_OK;
 }
 
@@ -2211,6 +2970,27 @@ dgfs_status tc_autotune(dgfs_plan_s *plan, int P, const void *f, void *Q, cudaSt
             bestcfg = *ts;
         }
     }
+    // the work-list schedule with the best launch parameters (variant 0)
+    if (status == DGFS_OK && wl_supported(plan->N)) {
+        *ts = bestcfg;
+        ts->ws_a = 0;
+        ts->sched = 1;
+        status = tc_collide(plan, P, f, Q, st);
+        double t = 1e300;
+        for (int rep = 0; rep < 2 && status == DGFS_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            status = tc_collide(plan, P, f, Q, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) status = cuda_status(cudaGetLastError(), "autotune");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t = std::min(t, (double)ms);
+        }
+        if (status == DGFS_OK && t < best) {
+            best = t;
+            bestcfg = *ts;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (status != DGFS_OK) {
@@ -2270,6 +3050,42 @@ dgfs_status tc_set_variant(dgfs_plan_s *plan, int variant)
     ts->ws_a = variant;
     plan->config_gen++;
     return DGFS_OK;
+}
+
+void tc_debug_worklist_chunk(int rs) { g_wl_chunk = std::max(1, rs); }
+
+void tc_debug_worklist_trace(void *buf, size_t bytes)
+{
+    g_wl_trace = reinterpret_cast<unsigned long long *>(buf);
+    g_wl_trace_cap = buf ? (uint32_t)std::min<size_t>(bytes / 32, 0xFFFFFFFFu) : 0;
+}
+
+// Select how a call runs its stages: 0 one launch per stage and job (two
+// streams), 1 one work-list launch (N = 24, 32, 48).
+dgfs_status tc_set_schedule(dgfs_plan_s *plan, int mode)
+{
+    TcState *ts = reinterpret_cast<TcState *>(plan->tc);
+    if (!ts) {
+        set_error("dgfs_plan_set_schedule: only tensor-core plans have a stage schedule");
+        return DGFS_EUNSUPPORTED;
+    }
+    if (mode != 0 && mode != 1) {
+        set_error("dgfs_plan_set_schedule: mode must be 0 or 1");
+        return DGFS_EINVAL;
+    }
+    if (mode == 1 && !wl_supported(plan->N)) {
+        set_error("dgfs_plan_set_schedule: the work list needs N in {24, 32, 48}");
+        return DGFS_EUNSUPPORTED;
+    }
+    ts->sched = mode;
+    plan->config_gen++;
+    return DGFS_OK;
+}
+
+int tc_schedule(const dgfs_plan_s *plan)
+{
+    const TcState *ts = reinterpret_cast<const TcState *>(plan->tc);
+    return ts ? ts->sched : 0;
 }
 
 dgfs_status tc_check(dgfs_plan_s *plan)

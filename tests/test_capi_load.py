@@ -58,6 +58,10 @@ def test_argument_errors_without_gpu():
     null = ctypes.c_void_p()
     assert B.lib().dgfs_collide(null, 1, None, None, None) == 1
     assert B.lib().dgfs_plan_destroy(null) == 0
+    # schedules: NULL handles
+    assert B.lib().dgfs_plan_set_schedule(null, 1) == 1
+    assert B.lib().dgfs_plan_get_schedule(null, None) == 1
+    assert B.lib().dgfs_batch_set_schedule(null, 0) == 1
     # batches: NULL handles and empty instance lists are argument errors
     out = ctypes.c_void_p()
     assert B.lib().dgfs_batch_create(0, None, None, None, None, 0.0, ctypes.byref(out)) == 1
