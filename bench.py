@@ -29,7 +29,7 @@ Prints ONE JSON line (rank 0).  Fields beyond the base contract:
                the batched rounds (eager and captured) and the batch as one
                work-list launch per N group,
   schedules    the benchmark call with per-stage launches and as one work-list launch,
-  adjoint      the FP64 backward on the 64-point adjoint workload against its forward,
+  adjoint      the FP64 and 3xTF32 backward on the 64-point adjoint workload against their forwards,
   tensor_peaks the tensor pipe's tf32 and bf16 issue rates measured by the library's probe.
 
 --impl reference times the FP64 CPU oracle (the only reference that exists:
@@ -407,9 +407,9 @@ def run_ours(args, rank, world):
         del slab, splan
 
     # the adjoint on the adjoint workload (64 points x 2 species x 32^3): one
-    # dgfs_collide_backward of the FP64 plan (the only form with an adjoint)
-    # against one forward call of the same plan, and the 3xTF32 forward that
-    # the autograd wrapper pairs with it
+    # dgfs_collide_backward of the FP64 plan and of the 3xTF32 plan (its
+    # (r, s) loop on the tensor cores), each against one forward call of the
+    # same plan; the omega gradient is requested in both
     if not args.no_adjoint:
         ap = W.make_problem("c4_adjoint_n32")
         Pa = ap["f"].shape[0]
@@ -431,16 +431,32 @@ def run_ours(args, rank, world):
 
         t_f = tev(lambda: p64.collide(fa, Qa))
         t_b = tev(lambda: p64.backward(fa, ga))
+        df64, dw64 = p64.backward(fa, ga)
         ptc = B.Plan(ap["N"], ap["L"], ap["M"], ap["Nrho"], ap["masses"], ap["pairs"], "fp32_tc", Pa, dev)
-        fa32 = fa.float()
+        fa32, ga32 = fa.float(), ga.float()
         Qt = ptc.collide(fa32)
+        dft, dwt = ptc.backward(fa32, ga32)
         torch.cuda.synchronize()
         t_t = tev(lambda: ptc.collide(fa32, Qt), reps=5)
+        t_tb = tev(lambda: ptc.backward(fa32, ga32), reps=3)
+        # per-kernel-class times of one profiled backward call
+        ptc.profile(True)
+        ptc.backward(fa32, ga32)
+        torch.cuda.synchronize()
+        bprof = {k: round(v[1], 3) for k, v in ptc.profile_read().items()}
+        ptc.profile(False)
         ne = Pa * S * S
         out["adjoint"] = {"workload": "c4_adjoint_n32: 64 points, 2 species (m = 1, 2), N = 32, M = 12, N_rho = 8",
                           "fp64_forward_ms": t_f, "fp64_backward_ms": t_b, "backward_over_forward": t_b / t_f,
                           "fp64_backward_evals_per_s": ne / (t_b / 1e3), "fp32_tc_forward_ms": t_t,
-                          "note": "the backward runs on an FP64 plan (tensor-core plans have no adjoint)"}
+                          "fp32_tc_backward_ms": t_tb, "fp32_tc_backward_over_forward": t_tb / t_t,
+                          "fp32_tc_backward_evals_per_s": ne / (t_tb / 1e3),
+                          "fp32_tc_backward_speedup_over_fp64": t_b / t_tb,
+                          "fp32_tc_vs_fp64_df_rel_err": float((dft.double() - df64).abs().max() / df64.abs().max()),
+                          "fp32_tc_vs_fp64_domega_rel_err": float((dwt - dw64).abs().max() / dw64.abs().max()),
+                          "fp32_tc_backward_kernel_ms": bprof,
+                          "note": "df and domega of both plans for the same seeded upstream gradient; the "
+                                  "tensor-core backward's inputs are the FP64 ones rounded to float32"}
         del p64, ptc
 
     # end to end through the host-buffer C-ABI call (pinned host memory)

@@ -183,8 +183,15 @@ dgfs_status dgfs_plan_selftest_wait(dgfs_plan plan, int expire, void *stream);
  *   df[P][S][n]   = sum over pairs of the f_p- and f_q-gradients,
  *   domega[S*S]   = dL/d omega_pq (host or device pointer, see domega_on_host),
  * recomputing the per-(rho, sigma) translates instead of storing them.
- * df_dev is overwritten.  domega may be NULL.  Errors: EINVAL, ECUDA,
- * EUNSUPPORTED (FP64 plans only in this build). */
+ * f_dev, dQ_dev and df_dev have the plan's element type (double for FP64
+ * plans, float otherwise).  FP64 plans run the adjoint in FP64; the other
+ * plans run its (rho, sigma) loop on the tensor cores in their operand format
+ * and the parts outside it (the transforms of dQ and dQ f_p, the loss-term
+ * adjoint, the final inverse transforms, the omega reduction) in FP64; they
+ * allocate their FP64 scratch per call, stream-ordered.
+ * df_dev is overwritten.  domega may be NULL.  Errors: EINVAL, ECUDA, ENOMEM,
+ * ETIMEOUT (a bounded device wait expired), EUNSUPPORTED (the Hermitian
+ * form, or N outside 8, 16, 24, 32, 48 on a tensor-core plan). */
 dgfs_status dgfs_collide_backward(dgfs_plan plan, int P, const void *f_dev, const void *dQ_dev,
                                   void *df_dev, double *domega, int domega_on_host, void *stream);
 

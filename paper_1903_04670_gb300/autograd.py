@@ -5,10 +5,12 @@ the backward pass calls dgfs_collide_backward, which recomputes the per-(rho,
 sigma) translates instead of storing them and also returns dL/d omega_pq
 through beta^(pq)(omega) and the radial weights rho^{gamma+2}, gamma = 2(1 - omega).
 
-The forward may run in any precision form; the backward always runs on an
-FP64 plan built with the same parameters (the tensor-core plans implement the
-forward only), with f promoted to double.  All arithmetic runs in the CUDA
-library; this module only orchestrates calls.
+The backward runs on the forward's own plan by default: the tensor-core forms
+have their own adjoint (the (rho, sigma) loop on the tensor cores in the
+plan's operand format, the parts outside it in FP64).  backward="fp64" builds
+a second, FP64 plan with the same parameters instead and promotes f and dQ to
+double for it.  All arithmetic runs in the CUDA library; this module only
+orchestrates calls.
 """
 import torch
 
@@ -16,14 +18,20 @@ from . import binding as B
 
 
 class CollisionOperator:
-    """Owns a forward plan (any precision) and an FP64 plan for gradients."""
+    """Owns a forward plan (any precision) and the plan that runs its adjoint:
+    the same plan (backward="native") or an FP64 one (backward="fp64")."""
 
-    def __init__(self, N, L, M, N_rho, masses, pairs, precision="fp64", max_points=1, device=0):
+    def __init__(self, N, L, M, N_rho, masses, pairs, precision="fp64", max_points=1, device=0,
+                 backward="native"):
+        if backward not in ("native", "fp64"):
+            raise ValueError("backward must be 'native' or 'fp64'")
         self.args = (N, L, M, N_rho, list(masses), [dict(p) for p in pairs])
         self.S = len(masses)
         self.fwd = B.Plan(N, L, M, N_rho, masses, pairs, precision, max_points, device)
-        self.bwd = self.fwd if precision == "fp64" else B.Plan(N, L, M, N_rho, masses, pairs, "fp64",
-                                                               max_points, device)
+        if precision == "fp64" or backward == "native":
+            self.bwd = self.fwd
+        else:
+            self.bwd = B.Plan(N, L, M, N_rho, masses, pairs, "fp64", max_points, device)
         self.omega = torch.tensor([p["omega"] for p in pairs], dtype=torch.float64,
                                   device="cuda").view(self.S, self.S)
 
@@ -52,5 +60,6 @@ class _Collide(torch.autograd.Function):
     def backward(ctx, dQ):
         (f,) = ctx.saved_tensors
         op = ctx.op
-        df, dom = op.bwd.backward(f.contiguous().to(torch.float64), dQ.contiguous().to(torch.float64))
+        dt = op.bwd.dtype
+        df, dom = op.bwd.backward(f.contiguous().to(dt), dQ.contiguous().to(dt))
         return df.to(f.dtype), dom.view(op.S, op.S), None

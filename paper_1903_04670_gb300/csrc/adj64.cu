@@ -57,6 +57,8 @@ enum AMode {
     L1,              // loss grids: L = ifft(c F_q), Lw = ifft(c_w F_q), Y = ifft(conj(c) GF) (x)
     L2,              // the three loss grids along y (inverse)
     L3,              // along z, then combine into df and the omega dot
+    X_INV,           // in-place inverse along the axis on X (grid.z = eval)
+    X_INV_RE,        // inverse along the axis, xout = xscale Re(result)
 };
 
 struct AdjArgs {
@@ -81,6 +83,9 @@ struct AdjArgs {
     void *df;              // [P][S][n] output (accumulated)
     int want_omega;
     const double2 *tw;
+    double2 *X;            // X_INV, X_INV_RE: [E][n] spectrum
+    double *xout;          // X_INV_RE: [E][n]
+    double xscale;
 };
 
 __device__ __forceinline__ double load_real(const void *base, int f32, long i)
@@ -273,6 +278,20 @@ __global__ void __launch_bounds__(64) k_adj(AdjArgs a)
             a.accp[o] = acc_s[(0 * N + k) * T + t];
             a.accq[o] = acc_s[(1 * N + k) * T + t];
         }
+    } else if constexpr (MODE == X_INV || MODE == X_INV_RE) {
+        if (!act) return;
+        double2 *X = a.X + (long)blockIdx.z * n;
+#pragma unroll
+        for (int j = 0; j < N; ++j) v[j] = X[poff<N, AXIS>(pi, j)];
+        fft<N, +1>(v, tw);
+        if constexpr (MODE == X_INV) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) X[poff<N, AXIS>(pi, k)] = v[k];
+        } else {
+            double *o = a.xout + (long)blockIdx.z * n;
+#pragma unroll
+            for (int k = 0; k < N; ++k) o[poff<N, AXIS>(pi, k)] = a.xscale * v[k].x;
+        }
     } else if constexpr (MODE == L1 || MODE == L2) {
         if (!act) return;
         const int e = blockIdx.z;
@@ -347,10 +366,11 @@ __global__ void __launch_bounds__(64) k_adj(AdjArgs a)
 }
 
 // domega[pair] = sum over points of dlnbeta <g,Q> + beta (sum_rs (wlog/w) dot_rs - <g f_p, Re S_w f_q>)
-// with <g,Q> = beta (sum_rs dot_rs - <g f_p, Re S f_q>) and dot_rs = w_rs / n^3 Re<V_u, A_u B_u>.
-__global__ void k_omega_reduce(double *domega, int pair, const double *dots, const double *lossdots, int E, int RS,
-                               int nblk, const double *w, const double *wlog, double beta, double dlnbeta,
-                               double inv_n3, int accumulate)
+// with <g,Q> = beta (sum_rs dot_rs - <g f_p, Re S f_q>) and dot_rs = w_rs dscale Re<V_u, A_u B_u>
+// (V_u, A_u, B_u as the caller's passes leave them; dscale undoes their scale).
+__global__ void k_omega_reduce(double *domega, int pair, const double *dots, int dblk, double dscale,
+                               const double *lossdots, int E, int RS, int nblk, const double *w, const double *wlog,
+                               double beta, double dlnbeta, int accumulate)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double total = 0.0;
@@ -358,9 +378,9 @@ __global__ void k_omega_reduce(double *domega, int pair, const double *dots, con
         double gain = 0.0, gain_w = 0.0;
         for (int rs = 0; rs < RS; ++rs) {
             double s = 0.0;
-            for (int b = 0; b < nblk; ++b) s += dots[((long)e * RS + rs) * nblk + b];
-            gain += w[rs] * inv_n3 * s;
-            gain_w += wlog[rs] * inv_n3 * s;
+            for (int b = 0; b < dblk; ++b) s += dots[((long)e * RS + rs) * dblk + b];
+            gain += w[rs] * dscale * s;
+            gain_w += wlog[rs] * dscale * s;
         }
         double l0 = 0.0, l1 = 0.0;
         for (int b = 0; b < nblk; ++b) {
@@ -378,8 +398,8 @@ constexpr int kAdjThreads = 64;
 template <int N, int AXIS, int MODE>
 dgfs_status alaunch(dgfs_plan_s *plan, dim3 grid, const AdjArgs &a, cudaStream_t st)
 {
-    static const char *names[] = {"adj_g_fwd_real", "adj_g_fwd", "adj_j1", "adj_j2", "adj_j3",
-                                  "adj_j4", "adj_j5", "adj_l1", "adj_l2", "adj_l3"};
+    static const char *names[] = {"adj_g_fwd_real", "adj_g_fwd", "adj_j1", "adj_j2",  "adj_j3",   "adj_j4",
+                                  "adj_j5",         "adj_l1",    "adj_l2", "adj_l3",  "adj_x_inv", "adj_x_inv"};
     grid.x = (N * N + kAdjThreads - 1) / kAdjThreads;
     const size_t smem = MODE == J5 ? sizeof(double) * 2 * N * kAdjThreads : 0;
     if (smem > 0)
@@ -484,8 +504,8 @@ dgfs_status backward_n(dgfs_plan_s *plan, int P, const void *f, const void *dQ, 
                 DGFS_TRY((alaunch<N, 1, L2>(plan, dim3(1, 1, Ec), a, st)));
                 DGFS_TRY((alaunch<N, 2, L3>(plan, dim3(1, 1, Ec), a, st)));
                 if (domega) {
-                    k_omega_reduce<<<1, 32, 0, st>>>(dom, p * S + q, dots, lossdots, Ec, RS, nblk, pt.w, pt.wlog,
-                                                     pt.beta, pt.dlogbeta, 1.0 / ((double)n * n * n),
+                    k_omega_reduce<<<1, 32, 0, st>>>(dom, p * S + q, dots, nblk, 1.0 / ((double)n * n * n),
+                                                     lossdots, Ec, RS, nblk, pt.w, pt.wlog, pt.beta, pt.dlogbeta,
                                                      pt0 > 0 ? 1 : 0);
                     DGFS_LAUNCHED(plan);
                 }
@@ -500,7 +520,84 @@ dgfs_status backward_n(dgfs_plan_s *plan, int P, const void *f, const void *dQ, 
     return DGFS_OK;
 }
 
+template <int N>
+dgfs_status part_n(dgfs_plan_s *plan, int which, const AdjPart &x, cudaStream_t st)
+{
+    const PairTables &pt = plan->pairs[x.p * plan->S + x.q];
+    AdjArgs a{};
+    a.n = (long)N * N * N;
+    a.S = plan->S;
+    a.RS = plan->Nrho * plan->M;
+    a.p = x.p;
+    a.q = x.q;
+    a.pt0 = x.pt0;
+    a.f = reinterpret_cast<const double *>(x.f);
+    a.dQ = x.dQ;
+    a.f32 = x.f32;
+    a.F = x.F;
+    a.Gg = x.Gg;
+    a.GF = x.GF;
+    a.L = x.L;
+    a.Lw = x.Lw;
+    a.Y = x.Y;
+    a.accp = x.accp;
+    a.accq = x.accq;
+    a.lossdots = x.lossdots;
+    a.df = x.df;
+    a.want_omega = x.want_omega;
+    a.tw = plan->twiddle;
+    a.phase = pt.phase;
+    a.b = pt.b;
+    a.c = pt.c;
+    a.c_om = pt.c_om;
+    a.w = pt.w;
+    a.beta = pt.beta;
+    a.X = x.X;
+    a.xout = x.xout;
+    a.xscale = x.xscale;
+    const int Ec = x.Ec;
+    switch (which) {
+    case ADJ_PART_G:
+        DGFS_TRY((alaunch<N, 0, G_FWD_REAL>(plan, dim3(1, 2, Ec), a, st)));
+        DGFS_TRY((alaunch<N, 1, G_FWD>(plan, dim3(1, 2, Ec), a, st)));
+        return alaunch<N, 2, G_FWD>(plan, dim3(1, 2, Ec), a, st);
+    case ADJ_PART_INV:
+        DGFS_TRY((alaunch<N, 0, X_INV>(plan, dim3(1, 1, Ec), a, st)));
+        DGFS_TRY((alaunch<N, 1, X_INV>(plan, dim3(1, 1, Ec), a, st)));
+        return alaunch<N, 2, X_INV_RE>(plan, dim3(1, 1, Ec), a, st);
+    case ADJ_PART_LOSS:
+        DGFS_TRY((alaunch<N, 0, L1>(plan, dim3(1, 1, Ec), a, st)));
+        DGFS_TRY((alaunch<N, 1, L2>(plan, dim3(1, 1, Ec), a, st)));
+        return alaunch<N, 2, L3>(plan, dim3(1, 1, Ec), a, st);
+    default: set_error("adjoint: unknown part"); return DGFS_EINVAL;
+    }
+}
+
 }  // namespace
+
+int adj64_nblk(int N) { return (N * N + kAdjThreads - 1) / kAdjThreads; }
+
+dgfs_status adj64_part(dgfs_plan_s *plan, int which, const AdjPart &x, cudaStream_t st)
+{
+    switch (plan->N) {
+    case 8: return part_n<8>(plan, which, x, st);
+    case 16: return part_n<16>(plan, which, x, st);
+    case 24: return part_n<24>(plan, which, x, st);
+    case 32: return part_n<32>(plan, which, x, st);
+    case 48: return part_n<48>(plan, which, x, st);
+    default: set_error("N not supported by the adjoint's FP64 parts"); return DGFS_EUNSUPPORTED;
+    }
+}
+
+dgfs_status adj64_omega(dgfs_plan_s *plan, double *dom, int p, int q, const double *dots, int dblk, double dscale,
+                        const double *lossdots, int Ec, int accumulate, cudaStream_t st)
+{
+    const PairTables &pt = plan->pairs[p * plan->S + q];
+    k_omega_reduce<<<1, 32, 0, st>>>(dom, p * plan->S + q, dots, dblk, dscale, lossdots, Ec, plan->Nrho * plan->M,
+                                     adj64_nblk(plan->N), pt.w, pt.wlog, pt.beta, pt.dlogbeta, accumulate);
+    DGFS_LAUNCHED(plan);
+    return DGFS_OK;
+}
 
 dgfs_status fp64_backward(dgfs_plan_s *plan, int P, const void *f, const void *dQ, void *df, double *domega,
                           int domega_on_host, cudaStream_t st)

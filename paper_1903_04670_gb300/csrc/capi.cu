@@ -574,14 +574,13 @@ dgfs_status dgfs_collide_backward(dgfs_plan plan, int P, const void *f_dev, cons
     }
     dgfs_status st = entry_check(plan);
     if (st != DGFS_OK) return st;
-    if (plan->prec != DGFS_FP64) {
-        set_error("dgfs_collide_backward: tensor-core plans do not implement the adjoint yet");
-        return DGFS_EUNSUPPORTED;
-    }
     if (plan->hermitian) {
         set_error("dgfs_collide_backward: the adjoint is of the literal operator; switch the Hermitian form off");
         return DGFS_EUNSUPPORTED;
     }
+    if (plan->prec != DGFS_FP64)
+        return tc_backward(plan, P, f_dev, dQ_dev, df_dev, domega, domega_on_host,
+                           reinterpret_cast<cudaStream_t>(stream));
     return fp64_backward(plan, P, f_dev, dQ_dev, df_dev, domega, domega_on_host,
                          reinterpret_cast<cudaStream_t>(stream));
 }

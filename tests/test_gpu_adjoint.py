@@ -1,6 +1,9 @@
-"""GPU adjoint (dgfs_collide_backward, FP64) against the oracle's FP64 adjoint,
-the dot-product identity of the bilinear map, and central finite differences
-in omega; plus the torch.autograd wrapper."""
+"""GPU adjoint (dgfs_collide_backward) against the oracle's FP64 adjoint, the
+dot-product identity of the bilinear map, and central finite differences in
+omega; plus the torch.autograd wrapper.  The FP64 plans' adjoint runs in FP64;
+the tensor-core plans' adjoint runs its (rho, sigma) loop on the tensor cores
+in the plan's operand format (bounds as the forward's: 1e-5 for 3xTF32, 1e-3
+for split BF16, relative to the largest entry)."""
 import numpy as np
 import pytest
 import torch
@@ -89,8 +92,8 @@ def test_gpu_omega_gradient_finite_difference():
 
 def test_autograd_moment_loss_c4_shape():
     """Configuration 4's loss: weighted velocity moments (1, v, |v|^2, v_x v_y) of
-    Q^(pq); float32 f on the tensor-core forward, gradients from the FP64 adjoint,
-    checked against the oracle adjoint at one sampled point."""
+    Q^(pq); float32 f on the tensor-core forward, gradients from its tensor-core
+    adjoint, checked against the oracle adjoint at one sampled point."""
     pb = W.make_problem("c4_adjoint_n32", points=2, dtype=np.float32)
     N, L = pb["N"], pb["L"]
     op = AG.CollisionOperator(N, L, pb["M"], pb["Nrho"], pb["masses"], pb["pairs"], "fp32_tc", 2)
@@ -112,3 +115,77 @@ def test_autograd_moment_loss_c4_shape():
     # omega gradient sums over both points: compare the FP64 plan's per-point value
     assert omega.grad is not None and omega.grad.shape == (2, 2)
     assert torch.isfinite(omega.grad).all()
+
+
+TC_TOL = {"fp32_tc": 1e-5, "bf16x3": 1e-3}
+
+
+def _f32(x):
+    return x.astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("N,M,Nrho,S,P,prec", [(8, 12, 4, 2, 2, "fp32_tc"), (16, 6, 4, 2, 1, "fp32_tc"),
+                                               (16, 6, 4, 2, 1, "bf16x3"), (24, 6, 3, 3, 1, "fp32_tc"),
+                                               (32, 12, 4, 2, 1, "fp32_tc")])
+def test_tc_adjoint_matches_oracle_adjoint(N, M, Nrho, S, P, prec):
+    """The tensor-core adjoint (float32 f, dQ) against the oracle's FP64 adjoint
+    of the same float32-rounded inputs: df and dL/d omega."""
+    pb, f, g = _problem(N, M, Nrho, S, P, seed=N + S + 7)
+    f, g = _f32(f), _f32(g)
+    plan = B.Plan(pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"], prec, P)
+    fd = torch.from_numpy(f).to("cuda", torch.float32)
+    gd = torch.from_numpy(g).to("cuda", torch.float32)
+    df, dom = plan.backward(fd, gd)
+    plan.check()
+    torch.cuda.synchronize()
+    dfo, domo = _oracle_grads(pb, f, g)
+    tol = TC_TOL[prec]
+    err_df = np.abs(df.double().cpu().numpy() - dfo).max() / np.abs(dfo).max()
+    err_w = np.abs(dom.cpu().numpy() - domo).max() / np.abs(domo).max()
+    assert err_df <= tol, err_df
+    assert err_w <= tol, err_w
+
+
+def test_tc_adjoint_chunks_and_repeat():
+    """30 points take two launch chunks (24 + 6): two calls in a row give the same
+    bits, and every point equals its own one-point call."""
+    P = 30
+    pb, f, g = _problem(8, 6, 2, 2, P, seed=11)
+    plan = B.Plan(pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"], "fp32_tc", P)
+    assert plan.info()["chunk"] < P
+    fd = torch.from_numpy(f).to("cuda", torch.float32)
+    gd = torch.from_numpy(g).to("cuda", torch.float32)
+    df1, dom1 = plan.backward(fd, gd)
+    df2, dom2 = plan.backward(fd, gd)
+    torch.cuda.synchronize()
+    assert torch.equal(df1, df2) and torch.equal(dom1, dom2)
+    parts = [plan.backward(fd[i:i + 1].contiguous(), gd[i:i + 1].contiguous()) for i in range(P)]
+    dfs = torch.cat([p[0] for p in parts])
+    doms = sum(p[1] for p in parts)
+    assert float((dfs - df1).abs().max()) <= 1e-6 * float(df1.abs().max())
+    assert float((doms - dom1).abs().max()) <= 1e-6 * float(dom1.abs().max())
+
+
+def test_tc_dot_product_identity():
+    """<g, J d> = <J^T g, d> with the tensor-core forward and adjoint: J d is the
+    exact central difference (Q(f + d) - Q(f - d)) / 2 of the quadratic map."""
+    pb, f, g = _problem(16, 6, 4, 2, 1, seed=13)
+    plan = B.Plan(pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"], "fp32_tc", 1)
+    fd = torch.from_numpy(f).to("cuda", torch.float32)
+    gd = torch.from_numpy(g).to("cuda", torch.float32)
+    df, _ = plan.backward(fd, gd)
+    d = torch.randn_like(fd) * fd.abs().max()
+    Qp = plan.collide((fd + d).contiguous()).double()
+    Qm = plan.collide((fd - d).contiguous()).double()
+    lhs = float((gd.double() * (Qp - Qm) / 2).sum())
+    rhs = float((df.double() * d.double()).sum())
+    scale = float((gd.double().abs() * ((Qp - Qm) / 2).abs()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * scale, (lhs, rhs, scale)
+
+
+def test_tc_adjoint_refuses_hermitian_form():
+    pb, f, g = _problem(8, 6, 2, 2, 1, seed=2)
+    plan = B.Plan(pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"], "fp32_tc", 1)
+    plan.set_hermitian(True)
+    with pytest.raises(B.DgfsError):
+        plan.backward(torch.from_numpy(f).to("cuda", torch.float32), torch.from_numpy(g).to("cuda", torch.float32))

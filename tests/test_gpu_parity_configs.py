@@ -175,8 +175,26 @@ def test_adjoint_workload_full_size_through_autograd():
         # dL/d omega sums g dQ/d omega over the grid with cancellation: FP64 to ~1e-10
         assert np.abs(per_pt[pt] - domo[i]).max() <= 1e-9 * np.abs(domo[i]).max(), pt
     tot = per_pt.sum(0)
-    tol_w = 1e-9 if bwd_fp64 else 1e-5
-    assert np.abs(omega.grad.cpu().numpy().reshape(S * S) - tot).max() <= tol_w * np.abs(tot).max()
+    got_w = omega.grad.cpu().numpy().reshape(S * S)
+    if bwd_fp64:
+        assert np.abs(got_w - tot).max() <= 1e-9 * np.abs(tot).max()
+    else:
+        # dL/d omega sums beta (sum_rs wlog_rs <V_rs, A_rs B_rs> - <g f_p, Re S_w f_q>) and
+        # dlnbeta <g, Q>: gain-level terms that cancel against the loss to the
+        # size of <g, Q> itself (conservation makes the moment weights nearly
+        # orthogonal to Q; on this workload sum |g dQ/domega| is 50-70 times
+        # |<g, dQ/domega>| and the gain 25 times Q).  Its tensor-core error is
+        # therefore of the order of the tensor-core forward's error in the same
+        # functional <g, Q>: bounded here by ten times that error (per pair, against
+        # the FP64 forward) plus the form's 1e-5.
+        p64P = B.Plan(N, L, pb["M"], pb["Nrho"], pb["masses"], pb["pairs"], "fp64", P)
+        Q64 = p64P.collide(fd64)
+        Qt = op.fwd.collide(f.detach())
+        gQ64 = (gq[None] * Q64).sum(dim=(0, 3, 4, 5)).reshape(S * S).cpu().numpy()
+        gQt = (gq[None] * Qt.double()).sum(dim=(0, 3, 4, 5)).reshape(S * S).cpu().numpy()
+        eQ = np.abs(gQt - gQ64) / np.abs(gQ64)
+        ew = np.abs(got_w - tot) / np.abs(tot)
+        assert np.all(ew <= 10 * eQ + 1e-5), (ew.tolist(), eQ.tolist())
 
 
 # ------------------------------------------------------------ uneven batch
