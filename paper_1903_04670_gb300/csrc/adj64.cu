@@ -61,6 +61,8 @@ enum AMode {
     X_INV_RE,        // inverse along the axis, xout = xscale Re(result)
 };
 
+constexpr int kAdjMaxPairs = 9;
+
 struct AdjArgs {
     long n;
     int S, p, q, pt0, RS;
@@ -86,6 +88,11 @@ struct AdjArgs {
     double2 *X;            // X_INV, X_INV_RE: [E][n] spectrum
     double *xout;          // X_INV_RE: [E][n]
     double xscale;
+    // G_FWD_REAL and L1 over several pairs: grid.z = pair slot k * Ec + e, the
+    // slot's pair (pk[k], qk[k]) and tables; every [E][n] buffer is indexed by grid.z
+    int Ec;
+    int pk[kAdjMaxPairs], qk[kAdjMaxPairs];
+    const double2 *ck[kAdjMaxPairs], *comk[kAdjMaxPairs];
 };
 
 __device__ __forceinline__ double load_real(const void *base, int f32, long i)
@@ -121,12 +128,12 @@ __global__ void __launch_bounds__(64) k_adj(AdjArgs a)
     double2 v[N];
 
     if constexpr (MODE == G_FWD_REAL) {
-        // grid.y: 0 -> g, 1 -> g . f_p ; grid.z = eval
-        const int e = blockIdx.z, pt = a.pt0 + e;
+        // grid.y: 0 -> g, 1 -> g . f_p ; grid.z = (pair slot, eval)
+        const int k = blockIdx.z / a.Ec, e = blockIdx.z % a.Ec, pt = a.pt0 + e;
         if (!act) return;
-        const long qb = (((long)pt * a.S + a.p) * a.S + a.q) * n;
-        const long fb = ((long)pt * a.S + a.p) * n;
-        double2 *X = (blockIdx.y == 0 ? a.Gg : a.GF) + (long)e * n;
+        const long qb = (((long)pt * a.S + a.pk[k]) * a.S + a.qk[k]) * n;
+        const long fb = ((long)pt * a.S + a.pk[k]) * n;
+        double2 *X = (blockIdx.y == 0 ? a.Gg : a.GF) + (long)blockIdx.z * n;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             const long o = poff<N, AXIS>(pi, j);
@@ -294,10 +301,11 @@ __global__ void __launch_bounds__(64) k_adj(AdjArgs a)
         }
     } else if constexpr (MODE == L1 || MODE == L2) {
         if (!act) return;
-        const int e = blockIdx.z;
+        const int e = blockIdx.z, k = blockIdx.z / a.Ec;
         double2 *dst[3] = {a.L + (long)e * n, a.Lw + (long)e * n, a.Y + (long)e * n};
-        const double2 *Fq = a.F + ((long)(a.pt0 + e) * a.S + a.q) * n;
+        const double2 *Fq = a.F + ((long)(a.pt0 + e % a.Ec) * a.S + a.qk[k]) * n;
         const double2 *Gf = a.GF + (long)e * n;
+        const double2 *cc = a.ck[k], *cw = a.comk[k];
 #pragma unroll
         for (int which = 0; which < 3; ++which) {
             if (which == 1 && !a.want_omega) continue;
@@ -305,7 +313,7 @@ __global__ void __launch_bounds__(64) k_adj(AdjArgs a)
             for (int j = 0; j < N; ++j) {
                 const long o = poff<N, AXIS>(pi, j);
                 if constexpr (MODE == L1) {
-                    v[j] = which == 0 ? cmul(a.c[o], Fq[o]) : which == 1 ? cmul(a.c_om[o], Fq[o]) : cmulc(Gf[o], a.c[o]);
+                    v[j] = which == 0 ? cmul(cc[o], Fq[o]) : which == 1 ? cmul(cw[o], Fq[o]) : cmulc(Gf[o], cc[o]);
                 } else {
                     v[j] = dst[which][o];
                 }
@@ -368,32 +376,29 @@ __global__ void __launch_bounds__(64) k_adj(AdjArgs a)
 // domega[pair] = sum over points of dlnbeta <g,Q> + beta (sum_rs (wlog/w) dot_rs - <g f_p, Re S_w f_q>)
 // with <g,Q> = beta (sum_rs dot_rs - <g f_p, Re S f_q>) and dot_rs = w_rs dscale Re<V_u, A_u B_u>
 // (V_u, A_u, B_u as the caller's passes leave them; dscale undoes their scale).
-__global__ void k_omega_reduce(double *domega, int pair, const double *dots, int dblk, double dscale,
-                               const double *lossdots, int E, int RS, int nblk, const double *w, const double *wlog,
-                               double beta, double dlnbeta, int accumulate)
+__global__ void __launch_bounds__(256) k_omega_reduce(double *domega, int pair, const double *dots, int dblk,
+                                                      double dscale, const double *lossdots, int E, int RS, int nblk,
+                                                      const double *w, const double *wlog, double beta, double dlnbeta,
+                                                      int accumulate)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double total = 0.0;
-    for (int e = 0; e < E; ++e) {
-        double gain = 0.0, gain_w = 0.0;
-        for (int rs = 0; rs < RS; ++rs) {
-            double s = 0.0;
-            for (int b = 0; b < dblk; ++b) s += dots[((long)e * RS + rs) * dblk + b];
-            gain += w[rs] * dscale * s;
-            gain_w += wlog[rs] * dscale * s;
-        }
-        double l0 = 0.0, l1 = 0.0;
-        for (int b = 0; b < nblk; ++b) {
-            l0 += lossdots[((long)e * 2 + 0) * nblk + b];
-            l1 += lossdots[((long)e * 2 + 1) * nblk + b];
-        }
-        const double gQ = beta * (gain - l0);
-        total += dlnbeta * gQ + beta * (gain_w - l1);
+    // the sum is linear in every dot: each thread takes a share of the terms
+    // with its weight, then one block reduction
+    double v = 0.0;
+    const long nd = dots ? (long)E * RS * dblk : 0;  // null: no gain terms in this call
+    for (long i = threadIdx.x; i < nd; i += blockDim.x) {
+        const int rs = (int)((i / dblk) % RS);
+        v += (dlnbeta * beta * w[rs] + beta * wlog[rs]) * dscale * dots[i];
     }
-    domega[pair] = accumulate ? domega[pair] + total : total;
+    for (long i = threadIdx.x; lossdots && i < (long)E * nblk; i += blockDim.x) {
+        const long e = i / nblk, b = i % nblk;
+        v -= dlnbeta * beta * lossdots[(e * 2 + 0) * nblk + b] + beta * lossdots[(e * 2 + 1) * nblk + b];
+    }
+    const double total = block_sum(v);
+    if (threadIdx.x == 0) domega[pair] = accumulate ? domega[pair] + total : total;
 }
 
 constexpr int kAdjThreads = 64;
+template <int N> constexpr int adj64_nblk_n() { return (N * N + kAdjThreads - 1) / kAdjThreads; }
 
 template <int N, int AXIS, int MODE>
 dgfs_status alaunch(dgfs_plan_s *plan, dim3 grid, const AdjArgs &a, cudaStream_t st)
@@ -489,9 +494,14 @@ dgfs_status backward_n(dgfs_plan_s *plan, int P, const void *f, const void *dQ, 
             a.c_om = pt.c_om;
             a.w = pt.w;
             a.beta = pt.beta;
+            a.pk[0] = p;
+            a.qk[0] = q;
+            a.ck[0] = pt.c;
+            a.comk[0] = pt.c_om;
             for (int pt0 = 0; pt0 < P; pt0 += E) {
                 const int Ec = std::min(E, P - pt0);
                 a.pt0 = pt0;
+                a.Ec = Ec;
                 DGFS_TRY((alaunch<N, 0, G_FWD_REAL>(plan, dim3(1, 2, Ec), a, st)));
                 DGFS_TRY((alaunch<N, 1, G_FWD>(plan, dim3(1, 2, Ec), a, st)));
                 DGFS_TRY((alaunch<N, 2, G_FWD>(plan, dim3(1, 2, Ec), a, st)));
@@ -504,7 +514,7 @@ dgfs_status backward_n(dgfs_plan_s *plan, int P, const void *f, const void *dQ, 
                 DGFS_TRY((alaunch<N, 1, L2>(plan, dim3(1, 1, Ec), a, st)));
                 DGFS_TRY((alaunch<N, 2, L3>(plan, dim3(1, 1, Ec), a, st)));
                 if (domega) {
-                    k_omega_reduce<<<1, 32, 0, st>>>(dom, p * S + q, dots, nblk, 1.0 / ((double)n * n * n),
+                    k_omega_reduce<<<1, 256, 0, st>>>(dom, p * S + q, dots, nblk, 1.0 / ((double)n * n * n),
                                                      lossdots, Ec, RS, nblk, pt.w, pt.wlog, pt.beta, pt.dlogbeta,
                                                      pt0 > 0 ? 1 : 0);
                     DGFS_LAUNCHED(plan);
@@ -523,52 +533,70 @@ dgfs_status backward_n(dgfs_plan_s *plan, int P, const void *f, const void *dQ, 
 template <int N>
 dgfs_status part_n(dgfs_plan_s *plan, int which, const AdjPart &x, cudaStream_t st)
 {
-    const PairTables &pt = plan->pairs[x.p * plan->S + x.q];
     AdjArgs a{};
     a.n = (long)N * N * N;
     a.S = plan->S;
     a.RS = plan->Nrho * plan->M;
-    a.p = x.p;
-    a.q = x.q;
     a.pt0 = x.pt0;
+    a.Ec = x.Ec;
     a.f = reinterpret_cast<const double *>(x.f);
     a.dQ = x.dQ;
     a.f32 = x.f32;
     a.F = x.F;
-    a.Gg = x.Gg;
-    a.GF = x.GF;
-    a.L = x.L;
-    a.Lw = x.Lw;
-    a.Y = x.Y;
-    a.accp = x.accp;
-    a.accq = x.accq;
-    a.lossdots = x.lossdots;
     a.df = x.df;
     a.want_omega = x.want_omega;
     a.tw = plan->twiddle;
-    a.phase = pt.phase;
-    a.b = pt.b;
-    a.c = pt.c;
-    a.c_om = pt.c_om;
-    a.w = pt.w;
-    a.beta = pt.beta;
     a.X = x.X;
     a.xout = x.xout;
     a.xscale = x.xscale;
-    const int Ec = x.Ec;
+    if (x.npairs < 1 || x.npairs > kAdjMaxPairs) {
+        set_error("adjoint: bad pair count");
+        return DGFS_EINVAL;
+    }
+    for (int k = 0; k < x.npairs; ++k) {
+        const PairTables &pt = plan->pairs[x.pairs[k]];
+        a.pk[k] = x.pairs[k] / plan->S;
+        a.qk[k] = x.pairs[k] % plan->S;
+        a.ck[k] = pt.c;
+        a.comk[k] = pt.c_om;
+    }
+    const unsigned slots = (unsigned)(x.npairs * x.Ec);
+    const long en = (long)x.Ec * a.n;  // one pair slot of an [E][n] buffer
     switch (which) {
     case ADJ_PART_G:
-        DGFS_TRY((alaunch<N, 0, G_FWD_REAL>(plan, dim3(1, 2, Ec), a, st)));
-        DGFS_TRY((alaunch<N, 1, G_FWD>(plan, dim3(1, 2, Ec), a, st)));
-        return alaunch<N, 2, G_FWD>(plan, dim3(1, 2, Ec), a, st);
+        a.Gg = x.Gg;
+        a.GF = x.GF;
+        DGFS_TRY((alaunch<N, 0, G_FWD_REAL>(plan, dim3(1, 2, slots), a, st)));
+        DGFS_TRY((alaunch<N, 1, G_FWD>(plan, dim3(1, 2, slots), a, st)));
+        return alaunch<N, 2, G_FWD>(plan, dim3(1, 2, slots), a, st);
     case ADJ_PART_INV:
-        DGFS_TRY((alaunch<N, 0, X_INV>(plan, dim3(1, 1, Ec), a, st)));
-        DGFS_TRY((alaunch<N, 1, X_INV>(plan, dim3(1, 1, Ec), a, st)));
-        return alaunch<N, 2, X_INV_RE>(plan, dim3(1, 1, Ec), a, st);
+        // x.Ec grids in X, no pairs involved
+        DGFS_TRY((alaunch<N, 0, X_INV>(plan, dim3(1, 1, x.Ec), a, st)));
+        DGFS_TRY((alaunch<N, 1, X_INV>(plan, dim3(1, 1, x.Ec), a, st)));
+        return alaunch<N, 2, X_INV_RE>(plan, dim3(1, 1, x.Ec), a, st);
     case ADJ_PART_LOSS:
-        DGFS_TRY((alaunch<N, 0, L1>(plan, dim3(1, 1, Ec), a, st)));
-        DGFS_TRY((alaunch<N, 1, L2>(plan, dim3(1, 1, Ec), a, st)));
-        return alaunch<N, 2, L3>(plan, dim3(1, 1, Ec), a, st);
+        a.GF = x.GF;
+        a.L = x.L;
+        a.Lw = x.Lw;
+        a.Y = x.Y;
+        DGFS_TRY((alaunch<N, 0, L1>(plan, dim3(1, 1, slots), a, st)));
+        DGFS_TRY((alaunch<N, 1, L2>(plan, dim3(1, 1, slots), a, st)));
+        // the combine adds into df[p] and df[q]: one pair per launch
+        for (int k = 0; k < x.npairs; ++k) {
+            const PairTables &pt = plan->pairs[x.pairs[k]];
+            AdjArgs b = a;
+            b.p = a.pk[k];
+            b.q = a.qk[k];
+            b.beta = pt.beta;
+            b.L = x.L + k * en;
+            b.Lw = x.Lw + k * en;
+            b.Y = x.Y + k * en;
+            b.accp = x.accp + 2 * k * en;
+            b.accq = x.accp + (2 * k + 1) * en;
+            b.lossdots = x.lossdots + (long)k * x.Ec * 2 * adj64_nblk_n<N>();
+            DGFS_TRY((alaunch<N, 2, L3>(plan, dim3(1, 1, x.Ec), b, st)));
+        }
+        return DGFS_OK;
     default: set_error("adjoint: unknown part"); return DGFS_EINVAL;
     }
 }
@@ -589,12 +617,22 @@ dgfs_status adj64_part(dgfs_plan_s *plan, int which, const AdjPart &x, cudaStrea
     }
 }
 
-dgfs_status adj64_omega(dgfs_plan_s *plan, double *dom, int p, int q, const double *dots, int dblk, double dscale,
-                        const double *lossdots, int Ec, int accumulate, cudaStream_t st)
+dgfs_status adj64_omega_gain(dgfs_plan_s *plan, double *dom, int p, int q, const double *dots, double dscale, int Ec,
+                             int accumulate, cudaStream_t st)
 {
     const PairTables &pt = plan->pairs[p * plan->S + q];
-    k_omega_reduce<<<1, 32, 0, st>>>(dom, p * plan->S + q, dots, dblk, dscale, lossdots, Ec, plan->Nrho * plan->M,
-                                     adj64_nblk(plan->N), pt.w, pt.wlog, pt.beta, pt.dlogbeta, accumulate);
+    k_omega_reduce<<<1, 256, 0, st>>>(dom, p * plan->S + q, dots, 1, dscale, nullptr, Ec, plan->Nrho * plan->M,
+                                      adj64_nblk(plan->N), pt.w, pt.wlog, pt.beta, pt.dlogbeta, accumulate);
+    DGFS_LAUNCHED(plan);
+    return DGFS_OK;
+}
+
+dgfs_status adj64_omega_loss(dgfs_plan_s *plan, double *dom, int p, int q, const double *lossdots, int Ec,
+                             cudaStream_t st)
+{
+    const PairTables &pt = plan->pairs[p * plan->S + q];
+    k_omega_reduce<<<1, 256, 0, st>>>(dom, p * plan->S + q, nullptr, 1, 0.0, lossdots, Ec, plan->Nrho * plan->M,
+                                      adj64_nblk(plan->N), pt.w, pt.wlog, pt.beta, pt.dlogbeta, 1);
     DGFS_LAUNCHED(plan);
     return DGFS_OK;
 }

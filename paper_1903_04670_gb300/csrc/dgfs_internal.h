@@ -150,24 +150,32 @@ dgfs_status fp64_backward(dgfs_plan_s *plan, int P, const void *f, const void *d
                           double *domega, int domega_on_host, cudaStream_t st);
 dgfs_status fp64_forward(dgfs_plan_s *plan, int P, const void *f, double2 *F, cudaStream_t st);
 // adj64.cu: the parts of the adjoint outside its (r, s) loop, in FP64, for one
-// species pair and chunk of points (also used by the tensor-core adjoint)
+// chunk of points [pt0, pt0 + Ec) and a list of species pairs (also used by the
+// tensor-core adjoint).  Buffers hold one [Ec][n] slot per listed pair, in list
+// order (accp: two slots per pair, the f_p then the f_q sum).
 struct AdjPart {
-    int p = 0, q = 0, pt0 = 0, Ec = 0, f32 = 1, want_omega = 0;
+    int pt0 = 0, Ec = 0, f32 = 1, want_omega = 0;
+    int npairs = 1;
+    int pairs[9] = {0};                      // p S + q of each listed pair
     const void *f = nullptr, *dQ = nullptr;  // [P][S][n], [P][S][S][n]
     void *df = nullptr;                      // [P][S][n], accumulated
     const double2 *F = nullptr;              // [P][S][n] fft3(f)
-    double2 *Gg = nullptr, *GF = nullptr, *L = nullptr, *Lw = nullptr, *Y = nullptr;  // [E][n]
-    double *accp = nullptr, *accq = nullptr;  // [E][n] gain sums of the f_p, f_q gradients (scale n^3)
-    double *lossdots = nullptr;               // [E][2][adj64_nblk(N)]
-    double2 *X = nullptr;                     // ADJ_PART_INV: [E][n] spectrum (overwritten)
-    double *xout = nullptr;                   // ADJ_PART_INV: [E][n] = xscale Re ifft3_u(X)
+    double2 *Gg = nullptr, *GF = nullptr, *L = nullptr, *Lw = nullptr, *Y = nullptr;  // [pairs][Ec][n]
+    double *accp = nullptr;                   // [pairs][2][Ec][n] gain sums of the f_p, f_q gradients (scale n^3)
+    double *lossdots = nullptr;               // [pairs][Ec][2][adj64_nblk(N)]
+    double2 *X = nullptr;                     // ADJ_PART_INV: [Ec][n] spectra (Ec counts grids here)
+    double *xout = nullptr;                   // ADJ_PART_INV: [Ec][n] = xscale Re ifft3_u(X)
     double xscale = 1.0;
 };
 enum { ADJ_PART_G = 0, ADJ_PART_INV = 1, ADJ_PART_LOSS = 2 };
 int adj64_nblk(int N);
 dgfs_status adj64_part(dgfs_plan_s *plan, int which, const AdjPart &x, cudaStream_t st);
-dgfs_status adj64_omega(dgfs_plan_s *plan, double *dom, int p, int q, const double *dots, int dblk, double dscale,
-                        const double *lossdots, int Ec, int accumulate, cudaStream_t st);
+// dL/d omega_pq (dom[p S + q]): the gain terms from per-(point, r, s) dots [Ec][RS] of
+// dscale^-1 Re<V, A B> (set, or added when accumulate), and the loss terms (added)
+dgfs_status adj64_omega_gain(dgfs_plan_s *plan, double *dom, int p, int q, const double *dots, double dscale, int Ec,
+                             int accumulate, cudaStream_t st);
+dgfs_status adj64_omega_loss(dgfs_plan_s *plan, double *dom, int p, int q, const double *lossdots, int Ec,
+                             cudaStream_t st);
 // tcadj.cu: the adjoint of a tensor-core plan
 dgfs_status tc_backward(dgfs_plan_s *plan, int P, const void *f, const void *dQ, void *df, double *domega,
                         int domega_on_host, cudaStream_t st);

@@ -352,19 +352,19 @@ dgfs_status backward_n(dgfs_plan_s *plan, int P, const void *f, const void *dQ, 
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_b_adj<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_c<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::C));
 
-    // per call: F [P][S][n] | Gg, GF, L, Lw, Y, ACC [E][n] (complex FP64) | accp, accq [E][n] |
-    //           dots [E][RS] | lossdots [E][2][lblk] | dom [S*S]
-    const size_t bytes = sizeof(double2) * ((size_t)P * S * n + 6 * (size_t)E * n) +
-                         sizeof(double) * (2 * (size_t)E * n + (size_t)E * RS + 2 * (size_t)E * lblk + S * S);
+    // per call: F [P][S][n] | Gg, GF, L, Lw, Y [S*S][E][n], ACC [S*S][2][E][n] (complex FP64) |
+    //           acc [S*S][2][E][n] | dots [E][RS] | lossdots [S*S][E][2][lblk] | dom [S*S]
+    const long SS = (long)S * S, En = (long)E * n;
+    const size_t bytes = sizeof(double2) * ((size_t)P * S * n + 7 * SS * En) +
+                         sizeof(double) * (2 * SS * En + (size_t)E * RS + 2 * SS * E * lblk + SS);
     void *own = nullptr;
     DGFS_CUDA(dev_malloc_async(&own, bytes, st));
     double2 *F = reinterpret_cast<double2 *>(own);
-    double2 *Gg = F + (long)P * S * n, *GF = Gg + (long)E * n, *Lb = GF + (long)E * n, *Lw = Lb + (long)E * n;
-    double2 *Y = Lw + (long)E * n, *ACC = Y + (long)E * n;
-    double *accp = reinterpret_cast<double *>(ACC + (long)E * n), *accq = accp + (long)E * n;
-    double *dots = accq + (long)E * n, *lossdots = dots + (long)E * RS, *dom = lossdots + 2L * E * lblk;
+    double2 *Gg = F + (long)P * S * n, *GF = Gg + SS * En, *Lb = GF + SS * En, *Lw = Lb + SS * En;
+    double2 *Y = Lw + SS * En, *ACC = Y + SS * En;
+    double *acc = reinterpret_cast<double *>(ACC + 2 * SS * En);
+    double *dots = acc + 2 * SS * En, *lossdots = dots + (long)E * RS, *dom = lossdots + 2 * SS * E * lblk;
 
-    dgfs_status status = DGFS_OK;
     auto run = [&]() -> dgfs_status {
         DGFS_CUDA(cudaMemsetAsync(df, 0, sizeof(float) * (size_t)P * S * n, st));
         DGFS_TRY(fp64_forward(plan, P, f, F, st));
@@ -373,32 +373,32 @@ dgfs_status backward_n(dgfs_plan_s *plan, int P, const void *f, const void *dQ, 
         const int RSB = (RS + rpb - 1) / rpb;
         constexpr int G = kRows / N;
         const dim3 gA(ts->groups_a, RS, 2), gB(ts->groups_b, RS);
-        for (int p = 0; p < S; ++p)
-            for (int q = 0; q < S; ++q) {
-                const long pq = p * S + q;
-                for (int pt0 = 0; pt0 < P; pt0 += E) {
-                    const int Ec = std::min(E, P - pt0);
-                    AdjPart x;
-                    x.p = p;
-                    x.q = q;
-                    x.pt0 = pt0;
-                    x.Ec = Ec;
-                    x.f32 = 1;
-                    x.want_omega = domega ? 1 : 0;
-                    x.f = f;
-                    x.dQ = dQ;
-                    x.df = df;
-                    x.F = F;
-                    x.Gg = Gg;
-                    x.GF = GF;
-                    x.L = Lb;
-                    x.Lw = Lw;
-                    x.Y = Y;
-                    x.accp = accp;
-                    x.accq = accq;
-                    x.lossdots = lossdots;
-                    // G = D g, D(g f_p)
-                    DGFS_TRY(adj64_part(plan, ADJ_PART_G, x, st));
+        for (int pt0 = 0; pt0 < P; pt0 += E) {
+            const int Ec = std::min(E, P - pt0);
+            const long ecn = (long)Ec * n;  // one pair slot of this chunk's buffers
+            AdjPart x;
+            x.pt0 = pt0;
+            x.Ec = Ec;
+            x.f32 = 1;
+            x.want_omega = domega ? 1 : 0;
+            x.npairs = (int)SS;
+            for (int k = 0; k < SS; ++k) x.pairs[k] = k;
+            x.f = f;
+            x.dQ = dQ;
+            x.df = df;
+            x.F = F;
+            x.Gg = Gg;
+            x.GF = GF;
+            x.L = Lb;
+            x.Lw = Lw;
+            x.Y = Y;
+            x.accp = acc;
+            x.lossdots = lossdots;
+            // G = D g and D(g f_p) of every pair
+            DGFS_TRY(adj64_part(plan, ADJ_PART_G, x, st));
+            for (int p = 0; p < S; ++p)
+                for (int q = 0; q < S; ++q) {
+                    const long pq = p * S + q;
                     TcArgs a = job_args(plan, f, p, q, pt0, Ec);
                     a.collapse_M = 1;
                     a.rsb = RSB;
@@ -411,10 +411,10 @@ dgfs_status backward_n(dgfs_plan_s *plan, int P, const void *f, const void *dQ, 
                     DGFS_LAUNCHED(plan);
                     {
                         ProfScope ps(plan, "tc_adj_stage_z", st);
-                        k_stage_z<N, FMT><<<gC, kRows * NPipes<N, FMT>::C, SM::C, st>>>(a, Gg);
+                        k_stage_z<N, FMT><<<gC, kRows * NPipes<N, FMT>::C, SM::C, st>>>(a, Gg + pq * ecn);
                     }
                     DGFS_LAUNCHED(plan);
-                    DGFS_CUDA(cudaMemsetAsync(dots, 0, sizeof(double) * (size_t)Ec * RS, st));
+                    if (domega) DGFS_CUDA(cudaMemsetAsync(dots, 0, sizeof(double) * (size_t)Ec * RS, st));
                     {
                         ProfScope ps(plan, "tc_adj_stage_b", st);
                         k_stage_b_adj<N, FMT><<<gB, kRows * NPipes<N, FMT>::B, SM::B, st>>>(a, dots);
@@ -432,25 +432,34 @@ dgfs_status backward_n(dgfs_plan_s *plan, int P, const void *f, const void *dQ, 
                         DGFS_LAUNCHED(plan);
                         {
                             ProfScope ps(plan, "tc_adj_sum", st);
-                            k_sum_partials_d<<<nblk((long)Ec * n, 256), 256, 0, st>>>(ACC, w.QGp, RSB, n, Ec);
+                            k_sum_partials_d<<<nblk(ecn, 256), 256, 0, st>>>(ACC + (pq * 2 + side) * ecn, w.QGp, RSB,
+                                                                              n, Ec);
                         }
                         DGFS_LAUNCHED(plan);
-                        // acc = n Re ifft3_u(sum): the FP64 adjoint's scale (n^3 times the gain sum);
-                        // the stage outputs carry n (V from the unnormalised conjugate transform)
-                        AdjPart xi = x;
-                        xi.X = ACC;
-                        xi.xout = side == 0 ? accp : accq;
-                        xi.xscale = (double)n;
-                        DGFS_TRY(adj64_part(plan, ADJ_PART_INV, xi, st));
                     }
-                    // loss-term adjoint and df += beta (accp / n^3 - ...), per species
-                    DGFS_TRY(adj64_part(plan, ADJ_PART_LOSS, x, st));
-                    // dots hold n Re<V, A B> per (point, r, s)
-                    if (domega)
-                        DGFS_TRY(adj64_omega(plan, dom, p, q, dots, 1, 1.0 / (double)n, lossdots, Ec, pt0 > 0 ? 1 : 0,
-                                             st));
+                    // dots hold n Re<V, A B> per (point, r, s); the reduction waits for
+                    // the loss dots of this pair below
+                    if (domega) {
+                        // keep this pair's dots: the next pair's stage B overwrites the buffer
+                        DGFS_TRY(adj64_omega_gain(plan, dom, p, q, dots, 1.0 / (double)n, Ec, pt0 > 0 ? 1 : 0, st));
+                    }
                 }
-            }
+            // acc = n Re ifft3_u(sum) of every pair and side: the FP64 adjoint's scale (n^3
+            // times the gain sum); the stage outputs carry n (V from the unnormalised
+            // conjugate transform)
+            AdjPart xi = x;
+            xi.Ec = (int)(2 * SS * Ec);
+            xi.X = ACC;
+            xi.xout = acc;
+            xi.xscale = (double)n;
+            DGFS_TRY(adj64_part(plan, ADJ_PART_INV, xi, st));
+            // loss-term adjoint and df += beta (acc / n^3 - ...), per species
+            DGFS_TRY(adj64_part(plan, ADJ_PART_LOSS, x, st));
+            if (domega)
+                for (int k = 0; k < SS; ++k)
+                    DGFS_TRY(adj64_omega_loss(plan, dom, (int)(k / S), (int)(k % S),
+                                              lossdots + (long)k * Ec * 2 * lblk, Ec, st));
+        }
         if (domega) {
             DGFS_CUDA(cudaMemcpyAsync(domega, dom, sizeof(double) * S * S,
                                       domega_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
@@ -458,7 +467,7 @@ dgfs_status backward_n(dgfs_plan_s *plan, int P, const void *f, const void *dQ, 
         }
         return DGFS_OK;
     };
-    status = run();
+    const dgfs_status status = run();
     const cudaError_t fe = dev_free_async(own, st);
     if (status == DGFS_OK && fe != cudaSuccess) return cuda_status(fe, "dgfs_collide_backward");
     return status;
