@@ -411,14 +411,11 @@ def run_ours(args, rank, world):
     # (r, s) loop on the tensor cores), each against one forward call of the
     # same plan; the omega gradient is requested in both
     if not args.no_adjoint:
-        ap = W.make_problem("c4_adjoint_n32")
+        ap = W.make_problem("c4_adjoint_n32", points=args.adjoint_points)
         Pa = ap["f"].shape[0]
-        p64 = B.Plan(ap["N"], ap["L"], ap["M"], ap["Nrho"], ap["masses"], ap["pairs"], "fp64", Pa, dev)
+        aforms = args.adjoint_forms.split(",")
         fa = torch.from_numpy(ap["f"]).to("cuda", torch.float64)
         ga = torch.from_numpy(np.random.default_rng(4).normal(size=(Pa, S, S) + fa.shape[2:])).to("cuda")
-        Qa = p64.collide(fa)
-        p64.backward(fa, ga)
-        torch.cuda.synchronize()
 
         def tev(fn, reps=2):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -429,35 +426,24 @@ def run_ours(args, rank, world):
             e1.synchronize()
             return e0.elapsed_time(e1) / reps
 
-        t_f = tev(lambda: p64.collide(fa, Qa))
-        t_b = tev(lambda: p64.backward(fa, ga))
-        df64, dw64 = p64.backward(fa, ga)
-        ptc = B.Plan(ap["N"], ap["L"], ap["M"], ap["Nrho"], ap["masses"], ap["pairs"], "fp32_tc", Pa, dev)
-        fa32, ga32 = fa.float(), ga.float()
-        Qt = ptc.collide(fa32)
-        dft, dwt = ptc.backward(fa32, ga32)
-        torch.cuda.synchronize()
-        t_t = tev(lambda: ptc.collide(fa32, Qt), reps=5)
-        t_tb = tev(lambda: ptc.backward(fa32, ga32), reps=3)
-        # per-kernel-class times of one profiled backward call
-        ptc.profile(True)
-        ptc.backward(fa32, ga32)
-        torch.cuda.synchronize()
-        bprof = {k: round(v[1], 3) for k, v in ptc.profile_read().items()}
-        ptc.profile(False)
-        ne = Pa * S * S
-        out["adjoint"] = {"workload": "c4_adjoint_n32: 64 points, 2 species (m = 1, 2), N = 32, M = 12, N_rho = 8",
-                          "fp64_forward_ms": t_f, "fp64_backward_ms": t_b, "backward_over_forward": t_b / t_f,
-                          "fp64_backward_evals_per_s": ne / (t_b / 1e3), "fp32_tc_forward_ms": t_t,
-                          "fp32_tc_backward_ms": t_tb, "fp32_tc_backward_over_forward": t_tb / t_t,
-                          "fp32_tc_backward_evals_per_s": ne / (t_tb / 1e3),
-                          "fp32_tc_backward_speedup_over_fp64": t_b / t_tb,
-                          "fp32_tc_vs_fp64_df_rel_err": float((dft.double() - df64).abs().max() / df64.abs().max()),
-                          "fp32_tc_vs_fp64_domega_rel_err": float((dwt - dw64).abs().max() / dw64.abs().max()),
-                          "fp32_tc_backward_kernel_ms": bprof,
-                          "note": "df and domega of both plans for the same seeded upstream gradient; the "
-                                  "tensor-core backward's inputs are the FP64 ones rounded to float32"}
-        del p64, ptc
+        adj = {"workload": "c4_adjoint_n32: %d points, 2 species (m = 1, 2), N = 32, M = 12, N_rho = 8" % Pa}
+        df64 = None
+        if "fp64" in aforms:
+            p64 = B.Plan(ap["N"], ap["L"], ap["M"], ap["Nrho"], ap["masses"], ap["pairs"], "fp64", Pa, dev)
+            Qa = p64.collide(fa)
+            p64.backward(fa, ga)
+            torch.cuda.synchronize()
+            t_f = tev(lambda: p64.collide(fa, Qa))
+            t_b = tev(lambda: p64.backward(fa, ga))
+            df64, dw64 = p64.backward(fa, ga)
+            del p64
+            adj.update({"fp64_forward_ms": t_f, "fp64_backward_ms": t_b, "backward_over_forward": t_b / t_f,
+                        "fp64_backward_evals_per_s": Pa * S * S / (t_b / 1e3)})
+        if "fp32_tc" in aforms:
+            adj.update(_tc_adjoint(ap, Pa, S, dev, fa, ga, tev, df64, dw64 if df64 is not None else None))
+        if "fp64_backward_ms" in adj and "fp32_tc_backward_ms" in adj:
+            adj["fp32_tc_backward_speedup_over_fp64"] = adj["fp64_backward_ms"] / adj["fp32_tc_backward_ms"]
+        out["adjoint"] = adj
 
     # end to end through the host-buffer C-ABI call (pinned host memory)
     if not args.no_e2e:
@@ -808,6 +794,37 @@ def run_reference(args, rank, world):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def _tc_adjoint(ap, Pa, S, dev, fa, ga, tev, df64, dw64):
+    """The 3xTF32 plan's backward on the adjoint workload: its time against its
+    forward, the per-kernel times of one profiled call, and (given the FP64
+    plan's result) the relative differences of df and dL/d omega."""
+    import torch
+    from paper_1903_04670_gb300 import binding as B
+    ptc = B.Plan(ap["N"], ap["L"], ap["M"], ap["Nrho"], ap["masses"], ap["pairs"], "fp32_tc", Pa, dev)
+    fa32, ga32 = fa.float(), ga.float()
+    Qt = ptc.collide(fa32)
+    dft, dwt = ptc.backward(fa32, ga32)
+    torch.cuda.synchronize()
+    t_t = tev(lambda: ptc.collide(fa32, Qt), reps=5)
+    t_tb = tev(lambda: ptc.backward(fa32, ga32), reps=3)
+    # per-kernel-class times of one profiled backward call
+    ptc.profile(True)
+    ptc.backward(fa32, ga32)
+    torch.cuda.synchronize()
+    bprof = {k: round(v[1], 3) for k, v in ptc.profile_read().items()}
+    ptc.profile(False)
+    ne = Pa * S * S
+    out = {"fp32_tc_forward_ms": t_t, "fp32_tc_backward_ms": t_tb, "fp32_tc_backward_over_forward": t_tb / t_t,
+           "fp32_tc_backward_evals_per_s": ne / (t_tb / 1e3), "fp32_tc_backward_kernel_ms": bprof}
+    if df64 is not None:
+        out.update({"fp32_tc_vs_fp64_df_rel_err": float((dft.double() - df64).abs().max() / df64.abs().max()),
+                    "fp32_tc_vs_fp64_domega_rel_err": float((dwt - dw64).abs().max() / dw64.abs().max()),
+                    "note": "df and domega of both plans for the same seeded upstream gradient; the "
+                            "tensor-core backward's inputs are the FP64 ones rounded to float32"})
+    del ptc
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -827,6 +844,10 @@ def main():
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--points", type=int, default=None,
                     help="evaluate only the first POINTS spatial points (small cases for profiling)")
+    ap.add_argument("--adjoint-points", type=int, default=None,
+                    help="points of the adjoint workload (default: all 64; small cases for profiling)")
+    ap.add_argument("--adjoint-forms", default="fp64,fp32_tc",
+                    help="plans whose backward the adjoint section times: fp64, fp32_tc or both")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 

@@ -17,7 +17,9 @@
 //                              as the conjugate of the forward DFT image)
 //   stage B adjoint (here):    X = F_x W, A = T+_x A', B = T-_x B';
 //                              dot_rs += Re sum X A B  (= n Re<V, A B>, for d/d omega),
-//                              H_p = F_x conj(B X), H_q = F_x conj(A X)
+//                              H_p = F_x conj(B X), H_q = F_x conj(A X); a
+//                              same-species pair reads B' from A' at the reflected
+//                              direction, as the forward's stage B
 //   stage C (forward kernel) with the table w_rs conj(phi_rs(k)) in place of
 //                              w_rs b_rs: the (r, s) sums of both gradients
 // The parts outside the (r, s) loop (D g, D(g f_p), the loss-term adjoint, the
@@ -132,11 +134,15 @@ __global__ void __launch_bounds__(kRows *NPipes<N, FMT>::C, 1) k_stage_z(TcArgs 
 //   X = F_x W,  A = T+_x A',  B = T-_x B'          (three contractions)
 //   dot_rs(e) += Re sum_x X A B
 //   H_p = F_x conj(B X)  -> written over W (a.H)
-//   H_q = F_x conj(A X)  -> written over A' (a.Ap)
+//   H_q = F_x conj(A X)  -> written over B' (a.Bq)
 // Every item reads its pencils before it writes the same pencils, and no other
-// item touches them, so the outputs can overwrite the inputs.
-template <int N, int FMT>
-__device__ __forceinline__ bool k_stage_b_adj_body(const TcArgs &a, double *dots, const uint3 bid, const uint3 gdim)
+// item touches them, so the outputs can overwrite the inputs.  A same-species
+// pair (SH) reads B' from A' at the reflected direction bmap[rs] (stage A then
+// computes the A side only, as in the forward); A' is only read here, and its
+// B' buffer is free for H_q.
+template <int N, int FMT, bool SH>
+__device__ __forceinline__ bool k_stage_b_adj_body(const TcArgs &a, double *dots, const uint16_t *bmap,
+                                                   const uint3 bid, const uint3 gdim)
 {
     using SM = Smem<N, FMT>;
     constexpr int NP = NPipes<N, FMT>::B, NT = SM::NT, AB = SM::AB, IC = SM::IC;
@@ -216,7 +222,7 @@ __device__ __forceinline__ bool k_stage_b_adj_body(const TcArgs &a, double *dots
         if (!ok) break;
         // A = T+_x A' (region 1)
         stage_pencil(pa_raw);
-        load_pencil(pa_raw, a.Bq + gbase, valid);
+        load_pencil(pa_raw, (SH ? a.Ap + ((long)bmap[rs] - rs) * n : a.Bq) + gbase, valid);
         ok = contract(NO, 0);
         if (!ok) break;
         // B = T-_x B' (region 2)
@@ -271,7 +277,7 @@ __device__ __forceinline__ bool k_stage_b_adj_body(const TcArgs &a, double *dots
         }
         ok = contract(2 * NO, 2);  // H_q = F_x P_q
         if (!ok) break;
-        store_out(a.Ap + gbase - (t & 1), valid);
+        store_out(a.Bq + gbase - (t & 1), valid);
         // this warp's pencils belong to one (point, r, s)
         if (!valid) dot = 0.f;
 #pragma unroll
@@ -282,10 +288,11 @@ __device__ __forceinline__ bool k_stage_b_adj_body(const TcArgs &a, double *dots
     return ok;
 }
 
-template <int N, int FMT>
-__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1) k_stage_b_adj(TcArgs a, double *dots)
+template <int N, int FMT, bool SH>
+__global__ void __launch_bounds__(kRows *NPipes<N, FMT>::B, 1)
+    k_stage_b_adj(TcArgs a, double *dots, const uint16_t *bmap)
 {
-    k_stage_b_adj_body<N, FMT>(a, dots, blockIdx, dim3(gridDim.x, gridDim.y, gridDim.z));
+    k_stage_b_adj_body<N, FMT, SH>(a, dots, bmap, blockIdx, dim3(gridDim.x, gridDim.y, gridDim.z));
 }
 
 // out[side][rs][k] = conj(phi_side,x(kx) phi_side,y(ky) phi_side,z(kz)) in FP32, from
@@ -321,6 +328,8 @@ __global__ void k_sum_partials_d(double2 *acc, const float2 *QGp, int rsb, long 
     acc[i] = make_double2(sx, sy);
 }
 
+constexpr int kZBlock = 8;  // (r, s) per stage Z pipeline
+
 dgfs_status ensure_adjmul(dgfs_plan_s *plan, TcState *ts, cudaStream_t st)
 {
     if (ts->adjmul) return DGFS_OK;
@@ -349,7 +358,10 @@ dgfs_status backward_n(dgfs_plan_s *plan, int P, const void *f, const void *dQ, 
     DGFS_TRY(ensure_adjmul(plan, ts, st));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_a<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::A));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_z<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::C));
-    DGFS_CUDA(cudaFuncSetAttribute(k_stage_b_adj<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B));
+    DGFS_CUDA(
+        cudaFuncSetAttribute(k_stage_b_adj<N, FMT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B));
+    DGFS_CUDA(
+        cudaFuncSetAttribute(k_stage_b_adj<N, FMT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::B));
     DGFS_CUDA(cudaFuncSetAttribute(k_stage_c<N, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::C));
 
     // per call: F [P][S][n] | Gg, GF, L, Lw, Y [S*S][E][n], ACC [S*S][2][E][n] (complex FP64) |
@@ -372,7 +384,7 @@ dgfs_status backward_n(dgfs_plan_s *plan, int P, const void *f, const void *dQ, 
         const int rsb = std::min(ts->rsb, RS), rpb = (RS + rsb - 1) / rsb;
         const int RSB = (RS + rpb - 1) / rpb;
         constexpr int G = kRows / N;
-        const dim3 gA(ts->groups_a, RS, 2), gB(ts->groups_b, RS);
+        const dim3 gB(ts->groups_b, RS);
         for (int pt0 = 0; pt0 < P; pt0 += E) {
             const int Ec = std::min(E, P - pt0);
             const long ecn = (long)Ec * n;  // one pair slot of this chunk's buffers
@@ -400,6 +412,8 @@ dgfs_status backward_n(dgfs_plan_s *plan, int P, const void *f, const void *dQ, 
                 for (int q = 0; q < S; ++q) {
                     const long pq = p * S + q;
                     TcArgs a = job_args(plan, f, p, q, pt0, Ec);
+                    const Share sh = job_share(plan, p, q);
+                    const dim3 gA(ts->groups_a, RS, sh.on ? 1 : 2);
                     a.collapse_M = 1;
                     a.rsb = RSB;
                     a.rs_per_block = rpb;
@@ -410,20 +424,29 @@ dgfs_status backward_n(dgfs_plan_s *plan, int P, const void *f, const void *dQ, 
                     }
                     DGFS_LAUNCHED(plan);
                     {
+                        // stage Z's (r, s) are independent (no accumulation): blocks of
+                        // kZBlock, so that its grid fills the SMs at a few points too
+                        TcArgs z = a;
+                        z.rs_per_block = std::min(kZBlock, RS);
+                        z.rsb = (RS + z.rs_per_block - 1) / z.rs_per_block;
+                        const dim3 gZ((N + G - 1) / G, (z.rsb + NPipes<N, FMT>::C - 1) / NPipes<N, FMT>::C, Ec);
                         ProfScope ps(plan, "tc_adj_stage_z", st);
-                        k_stage_z<N, FMT><<<gC, kRows * NPipes<N, FMT>::C, SM::C, st>>>(a, Gg + pq * ecn);
+                        k_stage_z<N, FMT><<<gZ, kRows * NPipes<N, FMT>::C, SM::C, st>>>(z, Gg + pq * ecn);
                     }
                     DGFS_LAUNCHED(plan);
                     if (domega) DGFS_CUDA(cudaMemsetAsync(dots, 0, sizeof(double) * (size_t)Ec * RS, st));
                     {
                         ProfScope ps(plan, "tc_adj_stage_b", st);
-                        k_stage_b_adj<N, FMT><<<gB, kRows * NPipes<N, FMT>::B, SM::B, st>>>(a, dots);
+                        if (sh.on)
+                            k_stage_b_adj<N, FMT, true><<<gB, kRows * NPipes<N, FMT>::B, SM::B, st>>>(a, dots, sh.bmap);
+                        else
+                            k_stage_b_adj<N, FMT, false><<<gB, kRows * NPipes<N, FMT>::B, SM::B, st>>>(a, dots, nullptr);
                     }
                     DGFS_LAUNCHED(plan);
-                    // the two (r, s) sums: H_p (in H) with conj(phi+), H_q (in A') with conj(phi-)
+                    // the two (r, s) sums: H_p (in H) with conj(phi+), H_q (in B') with conj(phi-)
                     for (int side = 0; side < 2; ++side) {
                         TcArgs c = a;
-                        c.H = side == 0 ? w.H : w.Ap;
+                        c.H = side == 0 ? w.H : w.Bq;
                         c.b32 = ts->adjmul + (pq * 2 + side) * (long)RS * n;
                         {
                             ProfScope ps(plan, "tc_stage_c", st);

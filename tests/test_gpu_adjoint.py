@@ -189,3 +189,24 @@ def test_tc_adjoint_refuses_hermitian_form():
     plan.set_hermitian(True)
     with pytest.raises(B.DgfsError):
         plan.backward(torch.from_numpy(f).to("cuda", torch.float32), torch.from_numpy(g).to("cuda", torch.float32))
+
+
+def test_tc_adjoint_tf32_and_collapsed_plans():
+    """A single-product TF32 plan's adjoint stays near the 3xTF32 one (TF32 keeps
+    about 11 bits per operand), and a VHS plan with the sigma collapse switched on
+    (a forward-only variant) gives the same adjoint bits as without it."""
+    pb, f, g = _problem(16, 6, 4, 2, 1, seed=17, alpha=1.0)
+    args = (pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"])
+    fd = torch.from_numpy(f).to("cuda", torch.float32)
+    gd = torch.from_numpy(g).to("cuda", torch.float32)
+    ref = B.Plan(*args, "fp32_tc", 1)
+    df3, dw3 = ref.backward(fd, gd)
+    tf = B.Plan(*args, "tf32", 1)
+    df1, dw1 = tf.backward(fd, gd)
+    col = B.Plan(*args, "fp32_tc", 1)
+    col.set_collapse(True)
+    dfc, dwc = col.backward(fd, gd)
+    torch.cuda.synchronize()
+    assert float((df1 - df3).abs().max()) <= 2e-2 * float(df3.abs().max())
+    assert float((dw1 - dw3).abs().max()) <= 2e-2 * float(dw3.abs().max())
+    assert torch.equal(dfc, df3) and torch.equal(dwc, dw3)
