@@ -126,10 +126,13 @@ def _f32(x):
 
 @pytest.mark.parametrize("N,M,Nrho,S,P,prec", [(8, 12, 4, 2, 2, "fp32_tc"), (16, 6, 4, 2, 1, "fp32_tc"),
                                                (16, 6, 4, 2, 1, "bf16x3"), (24, 6, 3, 3, 1, "fp32_tc"),
-                                               (32, 12, 4, 2, 1, "fp32_tc")])
+                                               (32, 12, 4, 2, 1, "fp32_tc"), (48, 6, 2, 2, 1, "fp32_tc"),
+                                               (48, 6, 2, 2, 1, "bf16x3")])
 def test_tc_adjoint_matches_oracle_adjoint(N, M, Nrho, S, P, prec):
     """The tensor-core adjoint (float32 f, dQ) against the oracle's FP64 adjoint
-    of the same float32-rounded inputs: df and dL/d omega."""
+    of the same float32-rounded inputs: df and dL/d omega.  N = 48 runs one
+    pipeline per CTA, whose stage B images do not fit next to the data and are
+    reloaded per contraction."""
     pb, f, g = _problem(N, M, Nrho, S, P, seed=N + S + 7)
     f, g = _f32(f), _f32(g)
     plan = B.Plan(pb["N"], pb["L"], pb["M"], pb["Nrho"], pb["masses"], pb["pairs"], prec, P)
