@@ -7,7 +7,8 @@ collective on the data path; the read-only tables are built on every rank.
 This mirrors the paper's linear domain decomposition of spatial elements
 (Sec. 3.3.2) without its trace exchange, which belongs to the DG streaming
 term, not to the operator.  Collectives are used only for timing (MAX over
-ranks) and, optionally, for gathering results.
+ranks), optionally for gathering results, and in the sharded adjoint for the
+omega gradient, a sum over all points.
 """
 import torch
 import torch.distributed as dist
@@ -48,6 +49,21 @@ def gather_shards(local, P, rank, world):
         out.append(parts[r][: b - a])
     return torch.cat(out, dim=0)
 
+
+
+def backward_sharded(backward, f_local, dQ_local):
+    """Adjoint of a point-sharded collision call.
+
+    backward(f, dQ) -> (df, domega) is a plan's backward (binding.Plan.backward)
+    or anything with its contract.  Each rank runs it on its own block of
+    points: df stays with the rank (it has the rank's points), while
+    dL/d omega_pq, a sum over all points of the bilinear map's omega
+    derivative, is summed over the ranks (one all_reduce of S*S values, the
+    only collective of the sharded adjoint)."""
+    df, dom = backward(f_local, dQ_local)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(dom, op=dist.ReduceOp.SUM)
+    return df, dom
 
 # ------------------------------------------------- DG slab split over ranks
 def element_range(Ne, rank, world):

@@ -1,8 +1,9 @@
 """The multi-rank paths on CPU: gloo ranks each evaluate their contiguous
 block of points (with the oracle as the per-rank compute, since the CPU has no
 GPU) and the gathered result equals the single-process result bit for bit;
-the timing reduction takes the MAX over ranks; a DG slab split over ranks with
-the trace halo exchange steps exactly like the undivided slab."""
+the timing reduction takes the MAX over ranks; the sharded adjoint keeps df per
+rank and sums dL/d omega over the ranks; a DG slab split over ranks with the
+trace halo exchange steps exactly like the undivided slab."""
 import os
 import socket
 
@@ -69,6 +70,69 @@ def test_two_gloo_ranks_equal_single_process(tmp_path):
     assert res["tmax"] == 2.0
     assert np.array_equal(res["Q"].numpy(), ref)
 
+
+
+ADJ = dict(N=8, L=4.0, M=6, Nrho=2, masses=(1.0, 2.0), P=5)
+
+
+def _adj_inputs():
+    from paper_1903_04670_gb300 import workloads as W
+    rng = np.random.default_rng(21)
+    S, N, P = len(ADJ["masses"]), ADJ["N"], ADJ["P"]
+    pairs = W.pair_params([0.72, 0.8], [1.0, 1.0], [1.0, 1.1])
+    f = rng.uniform(0.1, 1.0, size=(P, S, N, N, N))
+    g = rng.normal(size=(P, S, S, N, N, N))
+    return pairs, f, g
+
+
+def _oracle_backward(prob, S):
+    """A backward with the plan's contract, computed by the oracle (the CPU has no GPU)."""
+    def run(f, g):
+        f, g = f.numpy(), g.numpy()
+        df = np.zeros_like(f)
+        dom = np.zeros(S * S)
+        for pt in range(f.shape[0]):
+            for p in range(S):
+                for q in range(S):
+                    dp, dq, dw = prob.pair(p, q).adjoint(f[pt, p], f[pt, q], g[pt, p, q])
+                    df[pt, p] += dp
+                    df[pt, q] += dq
+                    dom[p * S + q] += dw
+        return torch.from_numpy(df), torch.from_numpy(dom)
+    return run
+
+
+def _adj_worker(rank, world, port, out_path):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle as O
+    O.set_threads(1)
+    pairs, f, g = _adj_inputs()
+    S = len(ADJ["masses"])
+    prob = O.Problem(ADJ["N"], ADJ["L"], ADJ["M"], ADJ["Nrho"], ADJ["masses"], pairs)
+    lo, hi = D.shard_range(ADJ["P"], rank, world)
+    df, dom = D.backward_sharded(_oracle_backward(prob, S), torch.from_numpy(f[lo:hi].copy()),
+                                 torch.from_numpy(g[lo:hi].copy()))
+    full = D.gather_shards(df, ADJ["P"], rank, world)
+    if rank == 0:
+        torch.save({"df": full, "dom": dom}, out_path)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sharded_adjoint_sums_omega_gradient_over_ranks(tmp_path):
+    out = str(tmp_path / "adj.pt")
+    mp.start_processes(_adj_worker, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
+    res = torch.load(out)
+    import oracle as O
+    pairs, f, g = _adj_inputs()
+    S = len(ADJ["masses"])
+    prob = O.Problem(ADJ["N"], ADJ["L"], ADJ["M"], ADJ["Nrho"], ADJ["masses"], pairs)
+    df, dom = D.backward_sharded(_oracle_backward(prob, S), torch.from_numpy(f), torch.from_numpy(g))
+    # df: the same per-point values, gathered; d omega: the two ranks' partial sums
+    assert torch.equal(res["df"], df)
+    assert float((res["dom"] - dom).abs().max()) <= 1e-13 * float(dom.abs().max())
 
 class _OracleBlock:
     """The operations dg_step_decomposed needs from a slab, done by the DG
