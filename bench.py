@@ -240,6 +240,8 @@ def run_ours(args, rank, world):
                       "evals_per_step": evals, "precision": main, "rs_per_eval": RS,
                       "l2": "flushed before every timed step (256 MiB write, outside the events)",
                       "launch_parameters": "dgfs_plan_autotune before timing" if not args.no_tune else "defaults",
+                      "launch": {k: int(info[k]) for k in ("chunk", "rs_blocks", "groups_a", "groups_b", "nterms")}
+                      if main != "fp64" else None,
                       "parallelism": "replicas: every rank evaluates its own 96 (point, pair) operators"}}
 
     peaks, src = _peaks()
