@@ -121,3 +121,43 @@ def test_dg_batch_and_graph_creation_unwind():
     assert _sweep(graph_create, lambda h: B.dgfs_graph_destroy(ctypes.c_void_p(h))) == 1
     plan.collide(f, Q)
     plan.check()
+
+
+def test_tc_backward_allocation_failure():
+    """The tensor-core backward allocates its k-space tables once per plan and its
+    FP64 scratch per call: a failure of either returns DGFS_ENOMEM, leaves no
+    scratch behind, and the next call gives the same result as an unhindered plan."""
+    N, L, M, Nrho = 8, 2.5, 6, 3
+    masses = [1.0, 2.0]
+    pairs = W.pair_params([0.81, 0.75], [1.0, 1.4], [1.0, 1.2])
+    rng = np.random.default_rng(9)
+    f = torch.from_numpy(np.stack([W.two_maxwellians(rng, N, L, m) for m in masses])[None]).to("cuda", torch.float32)
+    g = torch.from_numpy(rng.normal(size=(1, 2, 2, N, N, N))).to("cuda", torch.float32)
+    ref = B.Plan(N, L, M, Nrho, masses, pairs, "fp32_tc", 1)
+    df0, dw0 = ref.backward(f, g)
+    plan = B.Plan(N, L, M, Nrho, masses, pairs, "fp32_tc", 1)
+    torch.cuda.synchronize()
+    base = B.dgfs_debug_live_allocations()
+    df = torch.empty_like(f)
+    dom = torch.zeros(4, dtype=torch.float64, device="cuda")
+    # 1st allocation: the plan's conj(phi) tables
+    B.dgfs_debug_fail_alloc(1)
+    st = B.lib().dgfs_collide_backward(plan._h, 1, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                                       ctypes.c_void_p(df.data_ptr()), ctypes.c_void_p(dom.data_ptr()), 0, None)
+    B.dgfs_debug_fail_alloc(0)
+    torch.cuda.synchronize()
+    assert st == ENOMEM, B.dgfs_last_error()
+    assert B.dgfs_debug_live_allocations() == base
+    # 2nd allocation: the per-call scratch (the tables of the 1st stay with the plan)
+    B.dgfs_debug_fail_alloc(2)
+    st = B.lib().dgfs_collide_backward(plan._h, 1, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                                       ctypes.c_void_p(df.data_ptr()), ctypes.c_void_p(dom.data_ptr()), 0, None)
+    B.dgfs_debug_fail_alloc(0)
+    torch.cuda.synchronize()
+    assert st == ENOMEM, B.dgfs_last_error()
+    assert B.dgfs_debug_live_allocations() == base + 1
+    df1, dw1 = plan.backward(f, g)
+    plan.check()
+    torch.cuda.synchronize()
+    assert B.dgfs_debug_live_allocations() == base + 1
+    assert torch.equal(df1, df0) and torch.equal(dw1, dw0)
