@@ -61,7 +61,7 @@ enum AMode {
     X_INV_RE,        // inverse along the axis, xout = xscale Re(result)
 };
 
-constexpr int kAdjMaxPairs = 9;
+constexpr int kAdjMaxPairs = 16;  // S * S, S <= 4
 
 struct AdjArgs {
     long n;

@@ -156,7 +156,7 @@ dgfs_status fp64_forward(dgfs_plan_s *plan, int P, const void *f, double2 *F, cu
 struct AdjPart {
     int pt0 = 0, Ec = 0, f32 = 1, want_omega = 0;
     int npairs = 1;
-    int pairs[9] = {0};                      // p S + q of each listed pair
+    int pairs[16] = {0};                     // p S + q of each listed pair (S <= 4)
     const void *f = nullptr, *dQ = nullptr;  // [P][S][n], [P][S][S][n]
     void *df = nullptr;                      // [P][S][n], accumulated
     const double2 *F = nullptr;              // [P][S][n] fft3(f)

@@ -18,8 +18,8 @@ pytestmark = pytest.mark.gpu
 
 def _problem(N, M, Nrho, S, P, seed, alpha=1.3):
     rng = np.random.default_rng(seed)
-    masses = [1.0, 2.5, 0.7][:S]
-    pairs = W.pair_params([0.72, 0.8, 0.9][:S], [alpha, 1.0, 1.2][:S], [1.0, 1.1, 0.9][:S])
+    masses = [1.0, 2.5, 0.7, 1.6][:S]
+    pairs = W.pair_params([0.72, 0.8, 0.9, 0.75][:S], [alpha, 1.0, 1.2, 1.1][:S], [1.0, 1.1, 0.9, 1.05][:S])
     L = 0.5 * N
     f = np.stack([np.stack([W.two_maxwellians(rng, N, L, m) for m in masses]) for _ in range(P)])
     g = rng.normal(size=(P, S, S, N, N, N))
@@ -127,7 +127,7 @@ def _f32(x):
 @pytest.mark.parametrize("N,M,Nrho,S,P,prec", [(8, 12, 4, 2, 2, "fp32_tc"), (16, 6, 4, 2, 1, "fp32_tc"),
                                                (16, 6, 4, 2, 1, "bf16x3"), (24, 6, 3, 3, 1, "fp32_tc"),
                                                (32, 12, 4, 2, 1, "fp32_tc"), (48, 6, 2, 2, 1, "fp32_tc"),
-                                               (48, 6, 2, 2, 1, "bf16x3")])
+                                               (48, 6, 2, 2, 1, "bf16x3"), (8, 6, 2, 4, 2, "fp32_tc")])
 def test_tc_adjoint_matches_oracle_adjoint(N, M, Nrho, S, P, prec):
     """The tensor-core adjoint (float32 f, dQ) against the oracle's FP64 adjoint
     of the same float32-rounded inputs: df and dL/d omega.  N = 48 runs one
