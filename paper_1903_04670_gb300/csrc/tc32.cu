@@ -1259,27 +1259,34 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
 
     // Stage A runs on the plan's side stream: job k's stage A waits for job
     // k-1's stage B (the last reader of A', B'), so it overlaps job k-1's
-    // stage C; stage B waits for stage A.  The first stage A waits for the
+    // stage C; stage B waits for stage A.  With H double-buffered (hslots 2),
+    // stage B runs on a third stream and waits only for its stage A and for
+    // the stage C two jobs back (the last reader of its H slot), so that job
+    // k's stage B also runs beside job k-1's stage C; stage C and the partial
+    // sums stay on the caller's stream.  The first stage A waits for the
     // caller's stream at entry, and every side-stream launch is joined back
-    // through the stage B that consumes it (graph capture sees a closed fork).
+    // through the stage C that consumes it (graph capture sees a closed fork).
     // (serial when the plan's per-kernel profiler is on, so that every kernel's
     // event-bracketed time is its own)
     cudaStream_t sa = plan->prof ? st : ts->side;
     const bool fork = sa != st;
+    const int nh = fork ? ts->hslots : 1;
+    cudaStream_t sb = nh == 2 ? ts->side_b : st;
+    float2 *const Hslot[2] = {w.H, w.H2};
     if (fork) DGFS_CUDA(cudaEventRecord(ts->ev_entry, st));
-    bool first = true;
+    int job = 0;
     // forward transforms of f for the loss term (step 1 of Algorithm 2)
     DGFS_TRY(df_forward(plan, P, reinterpret_cast<const float *>(f), w.F, ts->tw_df, st));
     for (int p = 0; p < S; ++p)
         for (int q = 0; q < S; ++q) {
-            for (int pt0 = 0; pt0 < P; pt0 += E) {
+            for (int pt0 = 0; pt0 < P; pt0 += E, ++job) {
                 const int Ec = std::min(E, P - pt0);
-                const TcArgs a = job_args(plan, f, p, q, pt0, Ec);
+                TcArgs a = job_args(plan, f, p, q, pt0, Ec);
+                a.H = Hslot[job % nh];
                 const Share sh = job_share(plan, p, q);
                 dim3 gA, gB, gC;
                 job_grids<N, FMT>(plan, Ec, sh.on, gA, gB, gC);
-                if (fork) DGFS_CUDA(cudaStreamWaitEvent(sa, first ? ts->ev_entry : ts->ev_b, 0));
-                first = false;
+                if (fork) DGFS_CUDA(cudaStreamWaitEvent(sa, job == 0 ? ts->ev_entry : ts->ev_b, 0));
                 {
                     ProfScope ps(plan, "tc_stage_a", sa);
                     if (WsA<N, FMT>::OK && ts->ws_a == 1)
@@ -1292,17 +1299,19 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
                 DGFS_LAUNCHED(plan);
                 if (fork) {
                     DGFS_CUDA(cudaEventRecord(ts->ev_a, sa));
-                    DGFS_CUDA(cudaStreamWaitEvent(st, ts->ev_a, 0));
+                    DGFS_CUDA(cudaStreamWaitEvent(sb, ts->ev_a, 0));
                 }
+                if (nh == 2 && job >= 2) DGFS_CUDA(cudaStreamWaitEvent(sb, ts->ev_c[job % 2], 0));
                 {
-                    ProfScope ps(plan, "tc_stage_b", st);
+                    ProfScope ps(plan, "tc_stage_b", sb);
                     if (sh.on)
-                        k_stage_b_share<N, FMT, false><<<gB, kRows * NPipes<N, FMT>::B, SM::B, st>>>(a, sh.bmap);
+                        k_stage_b_share<N, FMT, false><<<gB, kRows * NPipes<N, FMT>::B, SM::B, sb>>>(a, sh.bmap);
                     else
-                        k_stage_b<N, FMT><<<gB, kRows * NPipes<N, FMT>::B, SM::B, st>>>(a);
+                        k_stage_b<N, FMT><<<gB, kRows * NPipes<N, FMT>::B, SM::B, sb>>>(a);
                 }
                 DGFS_LAUNCHED(plan);
-                if (fork) DGFS_CUDA(cudaEventRecord(ts->ev_b, st));
+                if (fork) DGFS_CUDA(cudaEventRecord(ts->ev_b, sb));
+                if (nh == 2) DGFS_CUDA(cudaStreamWaitEvent(st, ts->ev_b, 0));
                 {
                     ProfScope ps(plan, "tc_stage_c", st);
                     k_stage_c<N, FMT><<<gC, kRows * NPipes<N, FMT>::C, SM::C, st>>>(a);
@@ -1314,6 +1323,7 @@ dgfs_status collide_n(dgfs_plan_s *plan, int P, const void *f, void *Qout, cudaS
                                                                            w.QGp, RSB, n, pt0, Ec);
                 }
                 DGFS_LAUNCHED(plan);
+                if (nh == 2) DGFS_CUDA(cudaEventRecord(ts->ev_c[job % 2], st));
             }
         }
     // step 10 for every pair and point
@@ -1690,6 +1700,11 @@ dgfs_status tc_prepare(dgfs_plan_s *plan)
     DGFS_CUDA(cudaEventCreateWithFlags(&ts->ev_entry, cudaEventDisableTiming));
     DGFS_CUDA(cudaEventCreateWithFlags(&ts->ev_a, cudaEventDisableTiming));
     DGFS_CUDA(cudaEventCreateWithFlags(&ts->ev_b, cudaEventDisableTiming));
+    // H double-buffered where its second slot takes at most 2 GiB
+    ts->hslots = sizeof(float2) * (size_t)ts->chunk_max * RS * ((size_t)N * N * N) <= (size_t(2) << 30) ? 2 : 1;
+    DGFS_CUDA(cudaStreamCreateWithFlags(&ts->side_b, cudaStreamNonBlocking));
+    DGFS_CUDA(cudaEventCreateWithFlags(&ts->ev_c[0], cudaEventDisableTiming));
+    DGFS_CUDA(cudaEventCreateWithFlags(&ts->ev_c[1], cudaEventDisableTiming));
     // axes along which the design direction has no component: the translate
     // there is exp(i 0) = 1 in k-space, i.e. the identity, and is skipped
     {
@@ -1740,6 +1755,9 @@ void tc_release(dgfs_plan_s *plan)
     dev_free(ts->tw_df);
     dev_free(ts->adjmul);
     if (ts->side) cudaStreamDestroy(ts->side);
+    if (ts->side_b) cudaStreamDestroy(ts->side_b);
+    for (cudaEvent_t e : ts->ev_c)
+        if (e) cudaEventDestroy(e);
     if (ts->ev_entry) cudaEventDestroy(ts->ev_entry);
     if (ts->ev_a) cudaEventDestroy(ts->ev_a);
     if (ts->ev_b) cudaEventDestroy(ts->ev_b);
@@ -1753,8 +1771,9 @@ size_t tc_workspace_bytes(const dgfs_plan_s *plan)
     const long n = (long)plan->N * plan->N * plan->N;
     const long RS = (long)plan->Nrho * plan->M;
     const long E = ts ? ts->chunk_max : 1, RSB = ts ? ts->rsb_max : 1;
+    const long hs = ts ? ts->hslots : 1;
     return sizeof(float4) * ((long)plan->max_points * (plan->S + plan->S * plan->S) * n) +
-           sizeof(float2) * (3 * E * RS * n + E * RSB * n);
+           sizeof(float2) * ((2 + hs) * E * RS * n + E * RSB * n);
 }
 
 struct BatchPlan {

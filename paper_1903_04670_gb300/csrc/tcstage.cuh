@@ -50,6 +50,11 @@ struct TcState {
     int sms = 148;
     uint32_t *wl_ctr = nullptr;  // dependency counters of the work list
     size_t wl_words = 0;
+    // plain calls: 2 when H is double-buffered (stage B of job j + 1 on a third
+    // stream then runs beside stage C of job j, see collide_n)
+    int hslots = 1;
+    cudaStream_t side_b = nullptr;
+    cudaEvent_t ev_c[2] = {nullptr, nullptr};
     // adjoint (tcadj.cu): per pair [2 sides][RS][n] conj(phi_rs(k)) of the
     // transposed translates, built at the first backward call
     float2 *adjmul = nullptr;
@@ -860,11 +865,12 @@ unsigned nblk(long total, int t) { return (unsigned)((total + t - 1) / t); }
 
 // Workspace of a tensor-core plan:
 //   F [maxP][S][n] | QG [S*S][maxP][n] (complex double-floats, float4) | Ap, Bq, H [Emax][RS][n] f2 |
-//   QGp [Emax][RSBmax][n] f2
+//   QGp [Emax][RSBmax][n] f2 | H2 [Emax][RS][n] f2 (when H is double-buffered)
 struct TcWs {
     float4 *F, *QG;  // QG: pair p S + q at QG + (p S + q) qg_stride
     long qg_stride;
     float2 *Ap, *Bq, *H, *QGp;
+    float2 *H2;  // the second H slot (H itself when H is not double-buffered)
 };
 
 TcWs ws_of(const dgfs_plan_s *plan)
@@ -879,6 +885,7 @@ TcWs ws_of(const dgfs_plan_s *plan)
     w.Bq = w.Ap + (long)ts->chunk_max * RS * n;
     w.H = w.Bq + (long)ts->chunk_max * RS * n;
     w.QGp = w.H + (long)ts->chunk_max * RS * n;
+    w.H2 = ts->hslots == 2 ? w.QGp + (long)ts->chunk_max * ts->rsb_max * n : w.H;
     return w;
 }
 
