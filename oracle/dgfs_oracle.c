@@ -51,12 +51,12 @@
  * test of the adjoint, finite differences in omega, the loss term against an
  * independent quadrature of the truncated collision frequency for omega != 1
  * (pins the radial weight rho^{gamma+2}), moments of shifted Maxwellians
- * against their closed forms, and the VSS (alpha != 1) operator of Maxwell
+ * against their closed forms, the VSS (alpha != 1) operator of Maxwell
  * molecules through the closed-form relaxation rate of the traceless stress,
- * alone and relative to VHS, to its angular-quadrature error).  VSS at
- * omega != 1 is pinned only through its parts (the radial weight at alpha = 1,
- * the angular integral against direct quadrature) and equilibrium and
- * conservation trends.
+ * and the whole single-species operator at any omega and alpha through the
+ * closed-form linearised stress relaxation rate, 2e-4).  Unlike masses at
+ * omega != 1 are pinned through the parts (Krook-Wu covers unlike masses at
+ * omega = alpha = 1) and equilibrium and conservation trends.
  */
 #include <complex.h>
 #include <math.h>

@@ -1,0 +1,64 @@
+"""Pin of the whole single-species operator (Eq. 3 kernel at any omega and
+alpha, Algorithm 2): the linearised relaxation rate of the traceless stress
+against its closed form.
+
+Kernel B(|u|, t) = beta |u|^gamma (1 + t)^eta, gamma = 2(1 - omega),
+eta = alpha - 1, t = sigma . u^, u = v - v_*, post-collision velocity
+v' = (v + v_*)/2 + |u| sigma / 2 (equal masses).  For phi = v_x^2 - v_y^2 the
+sigma-average of phi(v') - phi(v) with weight (1 + t)^eta is
+-(lambda / 4)(u_x^2 - u_y^2) plus terms odd in u, with
+lambda = 3 pi int (1 + t)^eta (1 - t^2) dt = 3 pi 2^{alpha+2} / ((alpha+1)(alpha+2)),
+so that (weak form of Q(f, f))
+
+    <phi, Q(f, f)> = -(beta lambda / 4) int int f f_* |u|^gamma (u_x^2 - u_y^2) dv dv_*.
+
+For f = M (1 + eps phi), M = pi^{-3/2} exp(-|v|^2), the parts linear in eps are
+Gaussian integrals in the centre-of-mass and relative velocities:
+int int M M_* (phi + phi_*) |u|^gamma (u_x^2 - u_y^2) = (16/15) pi^{-1/2} 2^{gamma/2} Gamma((gamma+7)/2)
+and int M phi^2 = (8/15) pi^{-1/2} Gamma(7/2), so the linearised rate is
+
+    nu = -<phi, Q>_lin / <phi, f>_lin
+       = 3 pi beta 2^{alpha+1} / ((alpha+1)(alpha+2)) * 2^{gamma/2} Gamma((gamma+7)/2) / Gamma(7/2).
+
+The test takes the linear parts exactly as the odd part in eps of two
+evaluations, f = M (1 +- eps phi) (which also cancels Q(M, M), nonzero in the
+discrete operator).  beta comes from the oracle; its own formula is pinned by
+Bird's cross-section test.  What this pins: the radial weight rho^{gamma+2}
+and the truncation radius (through the gamma dependence), the VSS angular
+factor and its exponent sign, the design and radial quadratures, the phases
+and the normalisation of Algorithm 2 together, at the omega and alpha of the
+paper-shaped workloads.  Measured: within 4e-5 at N = 24 (L = 7) and 1.2e-6 at
+N = 32 (L = 8) for all five (omega, alpha) below; bound 2e-4 at N = 24."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+N, L, M, NRHO, EPS = 24, 7.0, 12, 12, 0.05
+
+
+def _closed_form(beta, omega, alpha):
+    gamma = 2.0 * (1.0 - omega)
+    return (3.0 * math.pi * beta * 2.0 ** (alpha + 1) / ((alpha + 1.0) * (alpha + 2.0)) * 2.0 ** (gamma / 2.0) *
+            math.gamma((gamma + 7.0) / 2.0) / math.gamma(3.5))
+
+
+@pytest.mark.parametrize("omega,alpha", [(1.0, 1.0), (0.81, 1.0), (0.5, 1.0), (0.75, 1.4), (0.81, 0.8)])
+def test_linearised_stress_rate_matches_closed_form(omega, alpha):
+    h = 2 * L / N
+    c = -L + (np.arange(N) + 0.5) * h
+    cx, cy, cz = np.meshgrid(c, c, c, indexing="ij")
+    Mx = np.exp(-(cx ** 2 + cy ** 2 + cz ** 2)) / np.pi ** 1.5
+    phi = cx ** 2 - cy ** 2
+    pair = O.Problem(N, L, M, NRHO, [1.0], [dict(omega=omega, alpha=alpha, d=1.0)]).pair(0, 0)
+    num = den = 0.0
+    for sgn in (1.0, -1.0):
+        f = Mx * (1.0 + sgn * EPS * phi)
+        Q, _ = pair.collide(f, f)
+        num += sgn * float((phi * Q).sum())
+        den += sgn * float((phi * f).sum())
+    nu = -num / den
+    want = _closed_form(pair.beta, omega, alpha)
+    assert abs(nu / want - 1.0) <= 2e-4, (omega, alpha, nu, want)
