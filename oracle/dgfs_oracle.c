@@ -54,9 +54,9 @@
  * against their closed forms, the VSS (alpha != 1) operator of Maxwell
  * molecules through the closed-form relaxation rate of the traceless stress,
  * and the whole single-species operator at any omega and alpha through the
- * closed-form linearised stress relaxation rate, 2e-4).  Unlike masses at
- * omega != 1 are pinned through the parts (Krook-Wu covers unlike masses at
- * omega = alpha = 1) and equilibrium and conservation trends.
+ * closed-form linearised stress relaxation rate, 2e-4, and the unlike-mass
+ * pair operator through the closed-form linearised stress responses to a
+ * perturbation of either species, 5e-5).
  */
 #include <complex.h>
 #include <math.h>
